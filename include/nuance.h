@@ -1,0 +1,213 @@
+/*
+ * nuance on GB300: C ABI of the transit-search hot path.
+ *
+ * Method: Garcia et al., "nuance: Efficient detection of planets transiting
+ * active stars" (arXiv:2402.06835).  The library computes
+ *   - the linear search of Sect. 2.2: for every trial epoch t0 and duration D,
+ *     the generalised least-squares fit (Eq. ls) of a transit template that is
+ *     the last column of the design matrix (Eq. linear_model), under the fixed
+ *     Gaussian-process covariance Sigma, returning the depth, its variance and
+ *     the log-likelihood gain of Eq. linear_search_ll over the transit-free
+ *     model;
+ *   - the periodic search of Sect. 2.3-2.4: the combination of those single
+ *     events with Eq. result (biased estimates of Eq. sigma_delta) on a phase
+ *     grid, the argmax of Eq. phi0 and the periodogram Q(P) = Delta / sigma.
+ *
+ * Conventions for every call:
+ *   - Arrays named *_dev are DEVICE pointers owned by the caller; arrays named
+ *     *_host are host pointers read during the call only.  All times,
+ *     durations and periods are in days.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL for
+ *     the legacy default stream) and is asynchronous unless stated.
+ *   - The return value is a nu_status; on anything but NU_OK a message is
+ *     available from nu_last_error() in the calling thread.  Argument errors
+ *     are detected on the host before any work is enqueued.  Errors that only
+ *     the device can see (a non-positive pivot of the factor, unsorted times,
+ *     a wait that ran out) are written to a status word that the next
+ *     synchronising call (nu_factor_info, nu_batch_search) reads back.
+ *   - The library keeps no global state except the thread-local error
+ *     message; a nu_factor may be used from any thread but not concurrently.
+ */
+#ifndef NUANCE_GB300_H
+#define NUANCE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NU_OK = 0,
+    NU_EINVAL = 1,    /* bad argument: shape, order, range, null pointer       */
+    NU_ENOTPD = 2,    /* covariance not positive definite (pivot <= 0 or NaN)  */
+    NU_ECUDA = 3,     /* a CUDA runtime call failed                            */
+    NU_ENOMEM = 4,    /* device allocation failed                              */
+    NU_ETIMEOUT = 5   /* a bounded device wait ran out                         */
+} nu_status;
+
+typedef enum {
+    NU_FP64 = 0,      /* every step in IEEE binary64                           */
+    NU_MIXED = 1      /* FP64 factor and prefix bases; FP32 window recursion,
+                         window sums and GLS with compensated accumulation;
+                         FP32 fold with FP64 epoch arithmetic                   */
+} nu_precision;
+
+typedef enum {
+    NU_BOX = 0,       /* -1 for t0 - D/2 <= t < t0 + D/2, else 0 (Sect. 2.1:
+                         "normalized box-shaped transit")                        */
+    NU_TRAPEZOID = 1  /* total width D, linear ingress and egress of width
+                         ingress_frac*D, flat bottom -1; not in the paper (its
+                         Sect. 4.4 names other base templates as a prospect)     */
+} nu_template;
+
+/* Covariance terms.  kind and parameters:
+ *   NU_TERM_SHO      p = {sigma, omega, Q}: Appendix A, k(0) = sigma^2;
+ *                    all three damping regimes (Q <, =, > 1/2) are accepted.
+ *   NU_TERM_EXP      p = {sigma, ell}: sigma^2 exp(-|tau|/ell), Sect. 3.2.
+ *   NU_TERM_ROTATION p = {sigma, period, Q0, dQ, f}: the two SHO terms of
+ *                    Sect. 3.2 (Q1 = 1/2+Q0+dQ, omega1 = 4 pi Q1/(P sqrt(4Q1^2-1)),
+ *                    S1 = sigma^2/((1+f) omega1 Q1); Q2 = 1/2+Q0, omega2 = 2 omega1,
+ *                    S2 = f sigma^2/((1+f) omega2 Q2)), with sigma_j^2 = S_j omega_j Q_j.
+ * The total state dimension (2 per SHO, 2 per EXP, 4 per ROTATION) must be
+ * at most 8. */
+enum { NU_TERM_SHO = 0, NU_TERM_EXP = 1, NU_TERM_ROTATION = 2 };
+typedef struct {
+    int kind;
+    double p[5];
+} nu_term;
+
+typedef struct nu_factor nu_factor;   /* opaque; owns library device memory */
+
+/* Factor the covariance and prepare the per-sample vectors of the search.
+ *
+ * Defines Sigma = diag(diag_var) + sum of terms (Sect. 2.1, App. A, Sect. 3.2)
+ * on the sample times t, factors it as L diag(D) L^T (the celerite-type
+ * quasiseparable factorisation the paper uses through tinygp, here in its
+ * state-space form), and computes, for the transit-free model y ~ N(X w, Sigma):
+ * Sigma^-1 X after Sigma-orthonormalising the columns of X, the null fit and
+ * its residual z0 = Sigma^-1 (y - X w_null), ln|Sigma| and the null
+ * log-likelihood of Eq. linear_search_ll.
+ *
+ *   t_dev         (n) strictly increasing sample times (checked on device)
+ *   diag_var_dev  (n) white-noise variance per sample, > 0 recommended
+ *   terms_host    (n_terms) covariance terms, see nu_term
+ *   X_dev         column-major n x k design matrix (column c at X_dev + c*n);
+ *                 may be NULL when k == 0.  0 <= k <= 4.
+ *   y_dev         (n) observed flux
+ *   out           receives a new factor; release it with nu_factor_free.
+ * The input arrays are copied; they may be freed once the call returns
+ * (after the stream has reached this point).  Asynchronous: a non-positive
+ * pivot or unsorted t is reported by nu_factor_info.
+ * Errors: NU_EINVAL (n < 2, k outside 0..4, bad term, state dimension > 8,
+ * null pointer), NU_ENOMEM, NU_ECUDA. */
+nu_status nu_gp_factor(const double* t_dev, const double* diag_var_dev, int64_t n,
+                       const nu_term* terms_host, int n_terms,
+                       const double* X_dev, int k, const double* y_dev,
+                       void* stream, nu_factor** out);
+
+/* Synchronise with the factor's stream and read its scalars: ln|Sigma|, the
+ * null log-likelihood (Eq. linear_search_ll without the transit column) and,
+ * when the factor failed, the first sample index at fault (else -1).
+ * Any pointer may be NULL.  Returns the factor's device status
+ * (NU_OK, NU_ENOTPD for a pivot <= 0 or NaN, NU_EINVAL for unsorted t). */
+nu_status nu_factor_info(const nu_factor* f, double* logdet, double* lnL_null,
+                         int64_t* first_bad_index);
+
+/* Number of samples and columns of X of a factor (host-side, no sync). */
+int64_t nu_factor_size(const nu_factor* f, int* k);
+
+/* Release a factor and its device memory (synchronises its stream). */
+void nu_factor_free(nu_factor* f);
+
+/* Linear search (Sect. 2.2) on the grid t0s x Ds.
+ *
+ * For every duration index j and epoch index i the template m(t0_i, D_j) is
+ * appended to X and Eq. ls is solved: depth = last weight, var = last diagonal
+ * entry of (X'^T Sigma^-1 X')^-1, dlnl = ln L(t0, D) - ln L_null = depth^2 /
+ * (2 var) (Eq. linear_search_ll).  Outputs are [n_D][n_t0] row-major
+ * (duration-major), FP64 when prec == NU_FP64 and FP32 when NU_MIXED.  A
+ * window with no sample, or whose template lies in the span of X, gives NaN
+ * in all three outputs.
+ *
+ *   f             factor from nu_gp_factor (its samples define the windows)
+ *   t0s_dev       (n_t0) trial epochs, any order
+ *   Ds_host       (n_D) trial durations, > 0
+ *   tmpl, ingress_frac  template and, for NU_TRAPEZOID, 0 < ingress_frac <= 0.5
+ *   depth_dev, var_dev, dlnl_dev  outputs as above (double* or float*)
+ * Errors: NU_EINVAL (null pointer, n_t0 < 1, n_D < 1, D <= 0, bad template),
+ * NU_ENOMEM, NU_ECUDA. */
+nu_status nu_linear_search(const nu_factor* f, const double* t0s_dev, int64_t n_t0,
+                           const double* Ds_host, int n_D, nu_template tmpl,
+                           double ingress_frac, nu_precision prec, void* stream,
+                           void* depth_dev, void* var_dev, void* dlnl_dev);
+
+/* Periodic search (Sect. 2.3-2.4) over trial periods.
+ *
+ * Inputs are the linear-search products on the grid t0s x Ds (layout and
+ * element type as produced by nu_linear_search with the same prec).  t0s must
+ * be sorted ascending.  For each period P: phases phi_j = j/n_phi with
+ * n_phi = ceil(P/phase_step); epochs T = t0s[0] + (phi_j + k) P for k >= 0
+ * and T <= t0s[n_t0-1]; each single event is linearly interpolated in time
+ * between the bracketing grid epochs (largest i with t0_i <= T, and i+1) from
+ * (depth, sqrt(var), dlnl), and dropped if it has no right neighbour, if the
+ * two epochs are more than gap_factor*phase_step apart, or if a node is
+ * non-finite.  The events of a (phase, duration) cell are combined with
+ * Eq. result using the biased estimates of Eq. sigma_delta and the gains as
+ * ln L_k; the cell maximising ln P (first in duration-major, then phase order)
+ * is Eq. phi0's argmax.
+ *
+ *   phase_step    > 0, or 0 for the median spacing of t0s (computed on the
+ *                 host from a copy of t0s; this synchronises the stream)
+ *   gap_factor    > 0 (1.5 is the default reading)
+ *   outputs (n_P each): Q = Delta/sigma, T0 = t0s[0] + phi0*P, D_idx (int32,
+ *   -1 when no cell has an epoch), depth Delta, sigma, lnP.  A period with no
+ *   valid cell gets Q = 0, lnP = -inf and NaN for the others.
+ * Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
+                             const double* Ds_host, int n_D,
+                             const void* depth_dev, const void* var_dev,
+                             const void* dlnl_dev, nu_precision prec,
+                             const double* periods_dev, int64_t n_P,
+                             double phase_step, double gap_factor, void* stream,
+                             double* Q_dev, double* T0_dev, int32_t* D_idx_dev,
+                             double* depth_out_dev, double* sigma_out_dev,
+                             double* lnP_dev);
+
+/* Batched survey search: factor, linear search (box template, t0s = the
+ * sample times of each curve) and periodic search for n_lc light curves of
+ * uneven length packed back to back, launched as one graph on `stream`.
+ *
+ *   offsets_host  (n_lc+1) start of each curve in the packed arrays
+ *   t_dev, y_dev, diag_var_dev  packed samples
+ *   terms_host, n_terms_host    terms of curve c are terms_host[tb_c ...],
+ *                 tb_c = sum of n_terms_host[0..c-1]
+ *   k             1 or 2: X = [1] or [1, t] per curve
+ *   Ds_host (n_D), periods_dev (n_P): shared grids
+ *   phase_step    > 0 (shared by all curves)
+ *   outputs, [n_lc][n_P] each: Q, T0, D_idx, depth, sigma, lnP (as in
+ *   nu_periodic_search); status_host (n_lc) per-curve factor status.
+ * Synchronises the stream before returning (the statuses are host data).
+ * Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
+nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
+                          const double* t_dev, const double* y_dev,
+                          const double* diag_var_dev, const nu_term* terms_host,
+                          const int* n_terms_host, int k,
+                          const double* Ds_host, int n_D,
+                          const double* periods_dev, int64_t n_P,
+                          double phase_step, nu_precision prec, void* stream,
+                          double* Q_dev, double* T0_dev, int32_t* D_idx_dev,
+                          double* depth_out_dev, double* sigma_out_dev,
+                          double* lnP_dev, int* status_host);
+
+/* Message of the last failed call in this thread ("" if none). */
+const char* nu_last_error(void);
+
+/* Library version string. */
+const char* nu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUANCE_GB300_H */
