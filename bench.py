@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the nuance hot path on GB300 (one JSON line on rank 0).
+
+A step is one full pass of the hot path over one light curve of the workload:
+nu_gp_factor (covariance factor and null fit), nu_linear_search (every
+(t0, D) template) and nu_periodic_search (every trial period), inputs resident
+in HBM.  Default workload: one TESS-sector-shaped light curve, N = 19 440 with
+a 1-day mid-sector gap, 10 durations (20 min - 3 h), 20 000 periods
+(0.2 - 13.5 d), FP64.  The same sector with 16 durations in mixed precision is
+measured beside it ("mixed").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the CPU oracle (dense FP64 covariance, one GLS per
+template, literal Eq. result fold) is timed on the host cores on bounded
+samples of the same workload and extrapolated to a full step.
+Multi-GPU (torchrun): every rank searches its own replica (independent light
+curves, no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_06835_gb300 import synth  # noqa: E402
+
+METRIC = "linear-search (t0,D) fits/s + period trials/s, %HBM roofline, mixed vs FP64"
+MEASURED_FP64_TFLOPS = 1.197   # DFMA microbenchmark on this machine's GB300 (2 DFMA/clk/SM)
+FOLD_FLOPS_PER_VISIT = 55.0    # 25 in pass 1 + 30 in pass 2 (one log per visit)
+FLUSH_BYTES = 512 << 20        # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sector_19440")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mixed-workload", default="sector_19440_16d")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def fold_visits(t0s, periods, dt, n_D):
+    """Exact number of epoch evaluations (per pass) of one periodic search."""
+    span = t0s[-1] - t0s[0]
+    total = 0
+    for P in periods:
+        n_phi = int(np.ceil(P / dt))
+        phi = np.arange(n_phi) / n_phi
+        K = np.floor((span - phi * P) / P).astype(np.int64) + 1
+        total += int(K[K > 0].sum())
+    return total * n_D
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our pipeline
+class Pipeline:
+    def __init__(self, api, torch, lc, Ds, periods, precision, dev):
+        self.api, self.torch = api, torch
+        f64 = torch.float64
+        self.t = torch.as_tensor(lc.t, dtype=f64, device=dev)
+        self.y = torch.as_tensor(lc.y, dtype=f64, device=dev)
+        self.dv = torch.as_tensor(lc.diag_var, dtype=f64, device=dev)
+        self.X = torch.as_tensor(lc.X, dtype=f64, device=dev)
+        self.t0s = self.t
+        self.periods = torch.as_tensor(periods, dtype=f64, device=dev)
+        self.Ds = [float(d) for d in Ds]
+        self.terms = lc.terms
+        self.precision = precision
+        self.dt = float(np.median(np.diff(lc.t)))
+        self.n_templates = len(lc.t) * len(Ds)
+        self.n_periods = len(periods)
+
+    def step(self, events=None):
+        api = self.api
+        if events:
+            events[0].record()
+        f = api.nu_gp_factor(self.t, self.dv, self.terms, self.X, self.y)
+        if events:
+            events[1].record()
+        d, v, l = api.nu_linear_search(f, self.t0s, self.Ds, precision=self.precision)
+        if events:
+            events[2].record()
+        res = api.nu_periodic_search(self.t0s, self.Ds, d, v, l, self.periods,
+                                     precision=self.precision, phase_step=self.dt)
+        if events:
+            events[3].record()
+        f.free()
+        return res
+
+
+def time_pipeline(pipe, torch, steps, warmup, flush):
+    for _ in range(warmup):
+        pipe.step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k + 1)                       # evict L2 between timed steps
+        pipe.step(ev[k])
+    torch.cuda.synchronize()
+    stages = np.array([[ev[k][s].elapsed_time(ev[k][s + 1]) for s in range(3)]
+                       for k in range(steps)])
+    return stages                                 # (steps, 3) ms
+
+
+def run_e2e(pipe, api, torch, lc, steps):
+    """Same step through the public API with inputs from pinned host memory,
+    outputs read back to the host, copies inside the timed region."""
+    f64 = torch.float64
+    host = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=f64).pin_memory()
+            for k, v in (("t", lc.t), ("y", lc.y), ("dv", lc.diag_var), ("X", lc.X),
+                         ("P", pipe.periods.cpu().numpy()))}
+    dev = {k: torch.empty_like(v, device="cuda") for k, v in host.items()}
+    nP = pipe.n_periods
+    out_host = torch.empty((5, nP), dtype=f64).pin_memory()
+    idx_host = torch.empty(nP, dtype=torch.int32).pin_memory()
+    bi = sum(v.numel() * v.element_size() for v in host.values())
+    bo = out_host.numel() * 8 + idx_host.numel() * 4
+
+    def one():
+        for k in host:
+            dev[k].copy_(host[k], non_blocking=True)
+        f = api.nu_gp_factor(dev["t"], dev["dv"], pipe.terms, dev["X"], dev["y"])
+        d, v, l = api.nu_linear_search(f, dev["t"], pipe.Ds, precision=pipe.precision)
+        r = api.nu_periodic_search(dev["t"], pipe.Ds, d, v, l, dev["P"],
+                                   precision=pipe.precision, phase_step=pipe.dt)
+        out_host.copy_(torch.stack([r["Q"], r["T0"], r["depth"], r["sigma"], r["lnP"]]),
+                       non_blocking=True)
+        idx_host.copy_(r["D_idx"], non_blocking=True)
+        f.free()
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return ms, bi, bo
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample(lc, Ds, periods, n_templates=256, n_periods=8, seed=0):
+    """Time the oracle on a bounded sample and extrapolate to one full step."""
+    from oracle import linear, periodic
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    model = linear.DenseModel(lc.t, lc.y, lc.diag_var, lc.terms, lc.X)
+    t_setup = time.perf_counter() - t0
+    n = len(lc.t)
+    pairs = [(int(rng.integers(0, len(Ds))), int(rng.integers(0, n)))
+             for _ in range(n_templates)]
+    t0 = time.perf_counter()
+    d, v, l = linear.sampled_linear_search(model, lc.t, Ds, pairs)
+    t_lin = (time.perf_counter() - t0) / n_templates
+    # fold on a synthetic grid of the right shape (values do not change the work)
+    g = dict(depth=rng.normal(0, 1e-3, (len(Ds), n)), var=rng.uniform(1e-8, 4e-8, (len(Ds), n)),
+             dlnl=rng.uniform(0, 5, (len(Ds), n)))
+    sel = rng.choice(len(periods), size=n_periods, replace=False)
+    dt = float(np.median(np.diff(lc.t)))
+    t0 = time.perf_counter()
+    periodic.periodic_search(lc.t, g["depth"], g["var"], g["dlnl"], np.asarray(periods)[sel], dt)
+    t_per = (time.perf_counter() - t0) / n_periods
+    total = t_setup + t_lin * n * len(Ds) + t_per * len(periods)
+    return dict(t_setup=t_setup, t_template=t_lin, t_period=t_per, total_s=total,
+                sample=f"dense Sigma factor once ({t_setup:.1f} s), {n_templates} random "
+                       f"templates, {n_periods} random periods; extrapolated to "
+                       f"{n * len(Ds)} templates + {len(periods)} periods")
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+# ---------------------------------------------------------------- main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = synth.WORKLOADS[args.workload]()
+    lc = w.curves[0]
+    n_templates = len(lc.t) * len(w.durations)
+    config = {"workload": f"{args.workload}: N={len(lc.t)} (2-min cadence, gaps), "
+                          f"{len(w.durations)} durations, {len(w.periods)} periods, "
+                          f"t0 = every sample, X=[1,t], rotation GP (2 SHO, J=4)",
+              "n_templates": n_templates, "n_periods": len(w.periods),
+              "precision": args.precision, "l2": "flushed (512 MB write) between timed steps"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        s = oracle_sample(lc, w.durations, w.periods, n_templates=64, n_periods=2)
+        for _ in range(args.warmup):
+            pass
+        per_step = []
+        for k in range(args.steps):
+            r = oracle_sample(lc, w.durations, w.periods, n_templates=64, n_periods=2, seed=k + 1)
+            per_step.append(r["total_s"])
+        tot = statistics.median(per_step)
+        val = n_templates / tot
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": val, "unit": "(t0,D) fits/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "period_trials_per_s": len(w.periods) / tot,
+            "cpu_baseline": {"value": val, "unit": "(t0,D) fits/s", "cores": blas_threads(),
+                             "kind": "oracle", "sample": s["sample"]},
+            "e2e": {"value": val, "unit": "(t0,D) fits/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2402_06835_gb300 import api
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    pipe = Pipeline(api, torch, lc, w.durations, w.periods, args.precision, dev)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    # warm up outside the sampler, then time
+    for _ in range(args.warmup):
+        pipe.step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    n0 = api.launch_count()
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.4)
+    t_wall0 = time.perf_counter()
+    stages = time_pipeline(pipe, torch, args.steps, 0, flush)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    launches = api.launch_count() - n0
+    ms = float(stages.sum(axis=1).mean())
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    stage_ms = stages.mean(axis=0)
+    value = world * n_templates / (ms / 1e3)
+
+    # dominant kernel: the fold (k_fold), FP64 pipe-bound in FP64 mode
+    visits = fold_visits(lc.t, w.periods, pipe.dt, len(w.durations))
+    fold_ms = float(stage_ms[2])
+    fold_tflops = visits * FOLD_FLOPS_PER_VISIT / (fold_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_fold (nu_periodic_search)", "bound": "alu",
+                "achieved": fold_tflops, "peak": MEASURED_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": fold_tflops / MEASURED_FP64_TFLOPS, "traffic": None,
+                "peak_source": "measured FP64 DFMA peak (microbenchmark, of measured)",
+                "algorithmic": f"{visits} visits x {FOLD_FLOPS_PER_VISIT:.0f} FP64 flops"}
+    out = {"metric": METRIC, "value": value, "unit": "(t0,D) fits/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+           "config": config, "period_trials_per_s": world * len(w.periods) / (ms / 1e3),
+           "stages_ms": {"factor": float(stage_ms[0]), "linear_search": float(stage_ms[1]),
+                         "periodic_search": float(stage_ms[2])},
+           "linear_search_fits_per_s": n_templates / ((stage_ms[0] + stage_ms[1]) / 1e3),
+           "fold_visits_per_s": visits / (fold_ms / 1e3),
+           "gpu_launches": int(launches), "wall_s_timed": t_wall, "clocks": clocks,
+           "roofline": roofline}
+
+    if not args.no_e2e:
+        try:
+            e2e_ms, bi, bo = run_e2e(pipe, api, torch, lc, max(1, args.steps))
+            out["e2e"] = {"value": world * n_templates / (e2e_ms / 1e3), "unit": "(t0,D) fits/s",
+                          "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                          "ms_per_step": e2e_ms}
+        except Exception as exc:      # report, do not hide
+            out["e2e"] = {"error": repr(exc)}
+
+    if not args.no_mixed and args.precision == "fp64":
+        try:
+            wm = synth.WORKLOADS[args.mixed_workload]()
+            lm = wm.curves[0]
+            pm = Pipeline(api, torch, lm, wm.durations, wm.periods, "mixed", dev)
+            for _ in range(args.warmup):
+                pm.step()
+            sm = time_pipeline(pm, torch, args.steps, 0, flush)
+            msm = float(sm.sum(axis=1).mean())
+            sms = sm.mean(axis=0)
+            ntm = len(lm.t) * len(wm.durations)
+            out["mixed"] = {"workload": args.mixed_workload, "ms_per_step": msm,
+                            "value": world * ntm / (msm / 1e3), "unit": "(t0,D) fits/s",
+                            "period_trials_per_s": world * len(wm.periods) / (msm / 1e3),
+                            "stages_ms": {"factor": float(sms[0]), "linear_search": float(sms[1]),
+                                          "periodic_search": float(sms[2])}}
+        except Exception as exc:
+            out["mixed"] = {"error": repr(exc)}
+
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            s = oracle_sample(lc, w.durations, w.periods)
+            out["cpu_baseline"] = {"value": n_templates / s["total_s"], "unit": "(t0,D) fits/s",
+                                   "cores": blas_threads(), "kind": "oracle",
+                                   "sample": s["sample"],
+                                   "period_trials_per_s": len(w.periods) / s["total_s"]}
+        except Exception as exc:
+            out["cpu_baseline"] = {"error": repr(exc)}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

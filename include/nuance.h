@@ -117,7 +117,11 @@ nu_status nu_factor_info(const nu_factor* f, double* logdet, double* lnL_null,
 /* Number of samples and columns of X of a factor (host-side, no sync). */
 int64_t nu_factor_size(const nu_factor* f, int* k);
 
-/* Release a factor and its device memory (synchronises its stream). */
+/* Release a factor.  Its device memory is returned stream-ordered on the
+ * factor's stream (no host synchronisation): work already enqueued on that
+ * stream completes first.  Work that used the factor on another stream must
+ * be complete (or ordered before this call's point on the factor's stream)
+ * before the call. */
 void nu_factor_free(nu_factor* f);
 
 /* Linear search (Sect. 2.2) on the grid t0s x Ds.
@@ -162,7 +166,9 @@ nu_status nu_linear_search(const nu_factor* f, const double* t0s_dev, int64_t n_
  *   gap_factor    > 0 (1.5 is the default reading)
  *   outputs (n_P each): Q = Delta/sigma, T0 = t0s[0] + phi0*P, D_idx (int32,
  *   -1 when no cell has an epoch), depth Delta, sigma, lnP.  A period with no
- *   valid cell gets Q = 0, lnP = -inf and NaN for the others.
+ *   valid cell gets Q = 0, lnP = -inf and NaN for the others; a period that
+ *   is not finite and > 0, or that gives more than 1e9 epochs or phases,
+ *   gets NaN everywhere and D_idx = -1 (and costs no work).
  * Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
 nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
                              const double* Ds_host, int n_D,
@@ -202,6 +208,10 @@ nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
 
 /* Message of the last failed call in this thread ("" if none). */
 const char* nu_last_error(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all threads, all devices); for launch accounting in benchmarks. */
+uint64_t nu_launch_count(void);
 
 /* Library version string. */
 const char* nu_version(void);

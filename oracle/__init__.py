@@ -19,10 +19,6 @@ and scipy's LAPACK routines as the only library steps:
                 phase grid, the combination of Eq. result with the biased
                 estimates of Eq. sigma_delta, the argmax of Eq. phi0 and
                 Q(P) = Delta/sigma.
-* ``semisep``   a second, sequential FP64 reference for long light curves
-                (the state-space recursion of the same covariance), used only
-                where the dense matrix does not fit; it is pinned to ``gp`` +
-                ``linear`` on sizes where both run.
 
 Nothing here shares code with the CUDA sources; the two meet only through the
 seeded inputs of ``paper_2402_06835_gb300.synth``.

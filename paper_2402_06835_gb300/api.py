@@ -1,0 +1,231 @@
+"""Thin Python binding of the C ABI in include/nuance.h (marshalling only).
+
+Every function here checks shapes and dtypes, passes device pointers and the
+current CUDA stream to the library and returns torch tensors that the library
+filled.  All arithmetic of the search runs in the CUDA library; there is no
+CPU path.  Importing this module loads ``_build/libnuance_gb300.so`` and
+raises ImportError if it has not been built (``python -m
+paper_2402_06835_gb300.build`` or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+NU_OK, NU_EINVAL, NU_ENOTPD, NU_ECUDA, NU_ENOMEM, NU_ETIMEOUT = range(6)
+NU_FP64, NU_MIXED = 0, 1
+NU_BOX, NU_TRAPEZOID = 0, 1
+NU_TERM_SHO, NU_TERM_EXP, NU_TERM_ROTATION = 0, 1, 2
+
+_STATUS_NAMES = {0: "NU_OK", 1: "NU_EINVAL", 2: "NU_ENOTPD", 3: "NU_ECUDA",
+                 4: "NU_ENOMEM", 5: "NU_ETIMEOUT"}
+_PREC = {"fp64": NU_FP64, "mixed": NU_MIXED}
+_TMPL = {"box": NU_BOX, "trapezoid": NU_TRAPEZOID}
+
+
+class NuanceError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+
+
+class nu_term(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("p", ctypes.c_double * 5)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(
+            f"CUDA library {path} not built; run `python -m "
+            "paper_2402_06835_gb300.build` (needs nvcc for sm_103a)")
+    lib = ctypes.CDLL(path)
+    P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.nu_gp_factor.argtypes = [P, P, I64, ctypes.POINTER(nu_term), I, P, I, P, P,
+                                 ctypes.POINTER(P)]
+    lib.nu_factor_info.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D),
+                                   ctypes.POINTER(I64)]
+    lib.nu_factor_size.argtypes = [P, ctypes.POINTER(I)]
+    lib.nu_factor_size.restype = I64
+    lib.nu_factor_free.argtypes = [P]
+    lib.nu_factor_free.restype = None
+    lib.nu_linear_search.argtypes = [P, P, I64, P, I, I, D, I, P, P, P, P]
+    lib.nu_periodic_search.argtypes = [P, I64, P, I, P, P, P, I, P, I64, D, D, P,
+                                       P, P, P, P, P, P]
+    lib.nu_batch_search.argtypes = [I, P, P, P, P, ctypes.POINTER(nu_term), P, I, P, I,
+                                    P, I64, D, I, P, P, P, P, P, P, P, P]
+    lib.nu_last_error.restype = ctypes.c_char_p
+    lib.nu_version.restype = ctypes.c_char_p
+    lib.nu_launch_count.restype = ctypes.c_uint64
+    for name in ("nu_gp_factor", "nu_factor_info", "nu_linear_search",
+                 "nu_periodic_search", "nu_batch_search"):
+        getattr(lib, name).restype = I
+    return lib
+
+
+LIB = _load()
+
+
+def _check(status, what):
+    if status != NU_OK:
+        raise NuanceError(status, f"{what}: {LIB.nu_last_error().decode()}")
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x, name, dtype=torch.float64):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype} (got {x.dtype})")
+    return x.contiguous()
+
+
+def _p(x):
+    return ctypes.c_void_p(x.data_ptr()) if x is not None else ctypes.c_void_p(0)
+
+
+def make_terms(terms):
+    """[(kind, params), ...] -> ctypes array of nu_term."""
+    arr = (nu_term * max(1, len(terms)))()
+    for i, (kind, params) in enumerate(terms):
+        arr[i].kind = int(kind)
+        vals = list(params) + [0.0] * (5 - len(params))
+        for j in range(5):
+            arr[i].p[j] = float(vals[j])
+    return arr
+
+
+class Factor:
+    """Owner of a nu_factor handle (library device memory)."""
+
+    def __init__(self, handle, n, k, keep, stream):
+        self._h = handle
+        self.n = n
+        self.k = k
+        self._keep = keep        # caller tensors read asynchronously
+        self.stream = stream
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("factor already freed")
+        return self._h
+
+    def info(self):
+        """Synchronising read of (status, logdet, lnL_null, first_bad)."""
+        ld, ln, fb = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        st = LIB.nu_factor_info(self.handle, ctypes.byref(ld), ctypes.byref(ln),
+                                ctypes.byref(fb))
+        return dict(status=st, logdet=ld.value, lnL_null=ln.value,
+                    first_bad=fb.value,
+                    message=LIB.nu_last_error().decode() if st else "")
+
+    def free(self):
+        if self._h is not None:
+            LIB.nu_factor_free(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def nu_gp_factor(t, diag_var, terms, X, y, stream=None):
+    """Factor Sigma and prepare the search vectors (see nu_gp_factor in the header).
+
+    t, diag_var, y: (N,) float64 CUDA tensors; X: (N, k) float64 or None.
+    """
+    t = _dev(t, "t")
+    diag_var = _dev(diag_var, "diag_var")
+    y = _dev(y, "y")
+    n = t.numel()
+    if diag_var.numel() != n or y.numel() != n:
+        raise ValueError("t, diag_var and y must have the same length")
+    if X is None or X.numel() == 0:
+        k, Xc = 0, None
+    else:
+        X = _dev(X, "X")
+        if X.dim() != 2 or X.shape[0] != n:
+            raise ValueError("X must be (N, k)")
+        k = X.shape[1]
+        Xc = X.t().contiguous()                 # column-major (k, N)
+    tm = make_terms(terms)
+    h = ctypes.c_void_p()
+    sp = _stream_ptr(stream)
+    st = LIB.nu_gp_factor(_p(t), _p(diag_var), n, tm, len(terms), _p(Xc), k, _p(y),
+                          sp, ctypes.byref(h))
+    _check(st, "nu_gp_factor")
+    return Factor(h, n, k, (t, diag_var, y, Xc), stream)
+
+
+def nu_factor_info(factor):
+    return factor.info()
+
+
+def nu_linear_search(factor, t0s, Ds, template="box", ingress_frac=0.1,
+                     precision="fp64", stream=None, out=None):
+    """Linear search (Sect. 2.2).  Returns (depth, var, dlnl), each (n_D, n_t0)."""
+    t0s = _dev(t0s, "t0s")
+    Ds = [float(d) for d in (Ds.tolist() if hasattr(Ds, "tolist") else Ds)]
+    n_D, n_t0 = len(Ds), t0s.numel()
+    prec = _PREC[precision]
+    dt = torch.float64 if prec == NU_FP64 else torch.float32
+    if out is None:
+        out = tuple(torch.empty((n_D, n_t0), dtype=dt, device=t0s.device)
+                    for _ in range(3))
+    for o in out:
+        if o.dtype != dt or o.numel() != n_D * n_t0 or not o.is_contiguous():
+            raise ValueError("output tensors must be contiguous (n_D, n_t0) of the "
+                             "precision's dtype")
+    Ds_arr = (ctypes.c_double * n_D)(*Ds)
+    st = LIB.nu_linear_search(factor.handle, _p(t0s), n_t0, Ds_arr, n_D,
+                              _TMPL[template], float(ingress_frac), prec,
+                              _stream_ptr(stream), _p(out[0]), _p(out[1]), _p(out[2]))
+    _check(st, "nu_linear_search")
+    return out
+
+
+def nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision="fp64",
+                       phase_step=0.0, gap_factor=1.5, stream=None):
+    """Periodic search (Sect. 2.3-2.4).  Returns a dict of (n_P,) tensors."""
+    t0s = _dev(t0s, "t0s")
+    periods = _dev(periods, "periods")
+    prec = _PREC[precision]
+    dt = torch.float64 if prec == NU_FP64 else torch.float32
+    depth, var, dlnl = (_dev(a, nm, dt) for a, nm in
+                        ((depth, "depth"), (var, "var"), (dlnl, "dlnl")))
+    n_D = depth.shape[0] if depth.dim() == 2 else len(Ds)
+    n_P = periods.numel()
+    dev = t0s.device
+    res = {name: torch.empty(n_P, dtype=torch.float64, device=dev)
+           for name in ("Q", "T0", "depth", "sigma", "lnP")}
+    res["D_idx"] = torch.empty(n_P, dtype=torch.int32, device=dev)
+    Ds_l = [float(d) for d in (Ds.tolist() if hasattr(Ds, "tolist") else Ds)]
+    Ds_arr = (ctypes.c_double * max(1, len(Ds_l)))(*Ds_l)
+    st = LIB.nu_periodic_search(_p(t0s), t0s.numel(), Ds_arr, n_D, _p(depth), _p(var),
+                                _p(dlnl), prec, _p(periods), n_P, float(phase_step),
+                                float(gap_factor), _stream_ptr(stream), _p(res["Q"]),
+                                _p(res["T0"]), _p(res["D_idx"]), _p(res["depth"]),
+                                _p(res["sigma"]), _p(res["lnP"]))
+    _check(st, "nu_periodic_search")
+    return res
+
+
+def launch_count():
+    """Kernels launched by the library so far (all threads)."""
+    return int(LIB.nu_launch_count())
+
+
+def version():
+    return LIB.nu_version().decode()

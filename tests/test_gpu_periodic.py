@@ -1,0 +1,128 @@
+"""GPU parity of the periodic search (Sect. 2.3-2.4) against the oracle fold.
+
+The fold's inputs are single-event grids computed by the oracle (or drawn at
+random by the seeded generator for full-size shapes); both sides fold the
+same grid.  ln P of the best cell is unique and is compared directly; when
+the GPU's argmax cell differs from the oracle's (a near-tie), the oracle is
+evaluated at the GPU's cell and must give the same maximum and Q.
+"""
+import numpy as np
+import pytest
+
+from oracle import linear, periodic
+from paper_2402_06835_gb300 import synth
+from parity import FP64_TOL, MIXED_SNR_ABS, periodic_compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2402_06835_gb300 import api  # noqa: E402
+
+
+def cu(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def c1_grid():
+    w = synth.single_2048()
+    lc = w.curves[0]
+    ora = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t,
+                               w.durations)
+    return w, lc, ora
+
+
+def _gpu_fold(t0s, Ds, grid, periods, precision, phase_step=0.0):
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    res = api.nu_periodic_search(cu(t0s), Ds, cu(grid["depth"], dt), cu(grid["var"], dt),
+                                 cu(grid["dlnl"], dt), cu(periods), precision=precision,
+                                 phase_step=phase_step)
+    return {k: v.cpu().numpy() for k, v in res.items()}
+
+
+def test_fold_fp64_single_2048(c1_grid):
+    w, lc, g = c1_grid
+    dt = periodic.median_spacing(lc.t)
+    ora = periodic.periodic_search(lc.t, g["depth"], g["var"], g["dlnl"], w.periods, dt)
+    gpu = _gpu_fold(lc.t, w.durations, g, w.periods, "fp64")
+    wl, wq, differ = periodic_compare(gpu, ora, lc.t, g["depth"], g["var"], g["dlnl"],
+                                      w.periods, dt, FP64_TOL, FP64_TOL,
+                                      periodic.fold_period)
+    print(f"single_2048 fold fp64: lnP err {wl:.2e}, Q err {wq:.2e}, argmax ties {differ}")
+    b_o = periodic.best(ora, w.periods)
+    b_g = int(np.argmax(np.where(np.isfinite(gpu["Q"]), gpu["Q"], -np.inf)))
+    assert abs(w.periods[b_g] - b_o["period"]) < 1e-12 or differ > 0
+
+
+def test_fold_mixed_single_2048(c1_grid):
+    w, lc, g = c1_grid
+    dt = periodic.median_spacing(lc.t)
+    ora = periodic.periodic_search(lc.t, g["depth"], g["var"], g["dlnl"], w.periods, dt)
+    gpu = _gpu_fold(lc.t, w.durations, g, w.periods, "mixed")
+    wl, wq, differ = periodic_compare(gpu, ora, lc.t, g["depth"], g["var"], g["dlnl"],
+                                      w.periods, dt, 1e-4, MIXED_SNR_ABS,
+                                      periodic.fold_period, max_reeval=1000, q_abs=True)
+    print(f"single_2048 fold mixed: lnP err {wl:.2e}, Q abs err {wq:.2e}, ties {differ}")
+
+
+def test_end_to_end_single_2048_recovers_injection(c1_grid):
+    w, lc, g = c1_grid
+    f = api.nu_gp_factor(cu(lc.t), cu(lc.diag_var), lc.terms, cu(lc.X), cu(lc.y))
+    d, v, l = api.nu_linear_search(f, cu(lc.t), w.durations)
+    res = api.nu_periodic_search(cu(lc.t), w.durations, d, v, l, cu(w.periods))
+    Q = res["Q"].cpu().numpy()
+    p = int(np.argmax(Q))
+    inj = lc.injected["period"]
+    # best period at the injected one or a simple alias
+    ratios = np.array([1.0, 0.5, 2.0])
+    assert np.min(np.abs(w.periods[p] / inj - ratios)) < 0.02, (w.periods[p], inj)
+
+
+def test_fold_gaps_edges_and_explicit_step():
+    """Random grid with a gap and NaN holes; explicit phase step."""
+    rng = np.random.default_rng(17)
+    t0s = np.concatenate([np.arange(700), np.arange(900, 1500)]) * synth.CADENCE_DAYS
+    n = len(t0s)
+    g = dict(depth=rng.normal(0, 1e-3, (3, n)), var=rng.uniform(1e-8, 5e-8, (3, n)),
+             dlnl=rng.uniform(0, 8, (3, n)))
+    g["depth"][1, 100:110] = np.nan
+    g["var"][2, 650:720] = np.nan
+    periods = np.linspace(0.05, 1.9, 257)
+    dt = synth.CADENCE_DAYS
+    ora = periodic.periodic_search(t0s, g["depth"], g["var"], g["dlnl"], periods, dt)
+    gpu = _gpu_fold(t0s, np.ones(3), g, periods, "fp64", phase_step=dt)
+    periodic_compare(gpu, ora, t0s, g["depth"], g["var"], g["dlnl"], periods, dt,
+                     FP64_TOL, FP64_TOL, periodic.fold_period)
+
+
+def test_fold_no_valid_cell():
+    t0s = np.arange(50) * synth.CADENCE_DAYS
+    nan = np.full((1, 50), np.nan)
+    g = dict(depth=nan, var=nan, dlnl=nan)
+    gpu = _gpu_fold(t0s, np.ones(1), g, np.array([0.02, 0.03]), "fp64")
+    assert np.all(gpu["Q"] == 0.0) and np.all(gpu["D_idx"] == -1)
+    assert np.all(np.isneginf(gpu["lnP"]))
+
+
+@pytest.mark.slow
+def test_fold_fp64_sector_shape_sampled_periods():
+    """Full sector shape (19 440 epochs with a 1-day gap, 10 durations, 20 000
+    periods) on a seeded random grid; the oracle checks 40 sampled periods."""
+    w = synth.sector_19440()
+    t0s = w.curves[0].t
+    n = len(t0s)
+    rng = np.random.default_rng(5)
+    g = dict(depth=rng.normal(0, 5e-4, (10, n)), var=rng.uniform(2e-8, 9e-8, (10, n)),
+             dlnl=rng.uniform(0, 6, (10, n)))
+    gpu = _gpu_fold(t0s, w.durations, g, w.periods, "fp64")
+    dt = periodic.median_spacing(t0s)
+    sel = np.concatenate([[0, 1, len(w.periods) - 1], rng.integers(0, len(w.periods), 37)])
+    ora = periodic.periodic_search(t0s, g["depth"], g["var"], g["dlnl"], w.periods[sel], dt)
+    gsel = {k: v[sel] for k, v in gpu.items()}
+    wl, wq, differ = periodic_compare(gsel, ora, t0s, g["depth"], g["var"], g["dlnl"],
+                                      w.periods[sel], dt, FP64_TOL, FP64_TOL,
+                                      periodic.fold_period)
+    print(f"sector fold fp64 sampled: lnP err {wl:.2e}, Q err {wq:.2e}, ties {differ}")
