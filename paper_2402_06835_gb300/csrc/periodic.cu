@@ -24,6 +24,37 @@
 
 namespace nu {
 
+// ------------------------------------------------------------------ helpers
+// Reciprocals from the hardware approximation refined by Newton-Raphson
+// (y <- y (2 - x y), each step doubling the correct bits); x > 0 finite.
+__device__ __forceinline__ double rcp64(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+__device__ __forceinline__ float rcp32(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_32(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Node record of the single-event grid: depth, sigma = sqrt(var) (NaN when
+// any of depth/var/gain is not finite or var <= 0), gain, and ig = 1/(gap to
+// the next epoch) (NaN when there is no next epoch or the gap exceeds the
+// limit).  Interpolating with a NaN anywhere yields a NaN sigma, which is how
+// an epoch is dropped.
+template <typename T> struct __align__(4 * sizeof(T)) Node4 {
+    T d, s, l, ig;
+};
+
 struct FoldGeom {
     const double* t0s;
     int64_t n_t0;
@@ -35,17 +66,6 @@ struct FoldGeom {
     const int* bucket;  // bucket[b] = #{i : t0_i <= t_ref + b*dt}
     int64_t n_bucket;
 };
-
-// largest i with t0[i] <= T (T >= t0[0]), exact
-__device__ __forceinline__ int64_t bracket(const FoldGeom& g, double T) {
-    int64_t b = (int64_t)floor((T - g.t_ref) * g.inv_dt);
-    b = b < 0 ? 0 : (b >= g.n_bucket ? g.n_bucket - 1 : b);
-    int64_t i = (int64_t)g.bucket[b] - 1;
-    if (i < 0) i = 0;
-    while (i + 1 < g.n_t0 && g.t0s[i + 1] <= T) ++i;
-    while (i > 0 && g.t0s[i] > T) --i;
-    return i;
-}
 
 __global__ void k_buckets(const double* __restrict__ t0s, int64_t n_t0, double t_ref,
                           double dt, int64_t n_bucket, int* __restrict__ bucket) {
@@ -60,12 +80,69 @@ __global__ void k_buckets(const double* __restrict__ t0s, int64_t n_t0, double t
     bucket[b] = (int)lo;
 }
 
+// Per-(duration, epoch) node records for the exact path.
 template <typename T>
-__global__ void k_sqrt(const T* __restrict__ var, T* __restrict__ sig, int64_t n) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void k_nodes(const T* __restrict__ depth, const T* __restrict__ var,
+                        const T* __restrict__ gain, const double* __restrict__ t0s,
+                        int64_t n_t0, int n_D, double gap_max, Node4<T>* __restrict__ nodes) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= n_t0 * (int64_t)n_D) return;
+    const int64_t i = gid % n_t0;
+    const T d = depth[gid], v = var[gid], l = gain[gid];
+    Node4<T> r;
+    r.d = d;
+    r.l = l;
+    r.s = (isfinite(d) && isfinite(v) && isfinite(l) && v > T(0)) ? sqrt(v) : T(NAN);
+    T ig = T(NAN);
+    if (i + 1 < n_t0) {
+        const double gap = t0s[i + 1] - t0s[i];
+        if (gap <= gap_max && gap > 0.0) ig = (T)(1.0 / gap);
+    }
+    r.ig = ig;
+    nodes[gid] = r;
+}
+
+// Regular-grid test for the slot path: every epoch within 1e-3 slot of
+// t_ref + s*dt with strictly increasing slots.  slot_of[i] = s.
+__global__ void k_slots(const double* __restrict__ t0s, int64_t n_t0, double t_ref,
+                        double inv_dt, int* __restrict__ slot_of, int* __restrict__ irregular) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_t0) return;
+    const double u = (t0s[i] - t_ref) * inv_dt;
+    const double s = rint(u);
+    bool bad = !(fabs(u - s) <= 1e-3) || !(s >= 0.0) || s > 2.0e9;
+    if (i > 0) {
+        const double up = rint((t0s[i - 1] - t_ref) * inv_dt);
+        bad = bad || !(s > up);
+    }
+    slot_of[i] = bad ? -1 : (int)s;
+    if (bad) atomicExch(irregular, 1);
+}
+
+// Slot records (mixed path): node values placed at their slot, NaN sigma in
+// empty slots.  One thread per (duration, epoch); slots were cleared to NaN.
+__global__ void k_slot_fill(const float* __restrict__ depth, const float* __restrict__ var,
+                            const float* __restrict__ gain, const int* __restrict__ slot_of,
+                            int64_t n_t0, int n_D, int64_t n_slots,
+                            Node4<float>* __restrict__ rec) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= n_t0 * (int64_t)n_D) return;
+    const int64_t d = gid / n_t0, i = gid - d * n_t0;
+    const int s = slot_of[i];
+    if (s < 0 || s >= n_slots) return;
+    const float dd = depth[gid], v = var[gid], l = gain[gid];
+    Node4<float> r;
+    r.d = dd;
+    r.l = l;
+    r.s = (isfinite(dd) && isfinite(v) && isfinite(l) && v > 0.f) ? sqrtf(v) : NAN;
+    r.ig = 0.f;
+    rec[d * n_slots + s] = r;
+}
+
+__global__ void k_fill_nan(Node4<float>* rec, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const T v = var[i];
-    sig[i] = v > T(0) ? sqrt(v) : T(NAN);
+    rec[i] = Node4<float>{NAN, NAN, NAN, 0.f};
 }
 
 template <typename T> struct KSum {
@@ -98,100 +175,30 @@ __device__ __forceinline__ bool better(const Best& a, const Best& b) {
     return a.cell < b.cell;
 }
 
-template <typename T>
-__device__ __forceinline__ bool event(const FoldGeom& g, const T* __restrict__ dep,
-                                      const T* __restrict__ sig, const T* __restrict__ gl,
-                                      double Tk, T& dk, T& sk2, T& lk) {
-    const int64_t i = bracket(g, Tk);
-    if (i > g.n_t0 - 2) return false;
-    const double ta = g.t0s[i], tb = g.t0s[i + 1];
-    const double gap = tb - ta;
-    if (!(gap <= g.gap_max)) return false;
-    const double w = (Tk - ta) / gap;
-    const T da = dep[i], db = dep[i + 1], sa = sig[i], sb = sig[i + 1];
-    const T la = gl[i], lb = gl[i + 1];
-    if (!(isfinite(da) && isfinite(db) && isfinite(sa) && isfinite(sb) && isfinite(la) &&
-          isfinite(lb)))
-        return false;
-    const T wl = (T)(1.0 - w), wr = (T)w;
-    dk = wl * da + wr * db;
-    const T s = wl * sa + wr * sb;
-    sk2 = s * s;
-    lk = wl * la + wr * lb;
-    return true;
+__device__ __forceinline__ void write_best(const Best& b, int64_t p, int64_t n_phi, double t_ref,
+                                           double P, double* Q_out, double* T0_out,
+                                           int* Didx_out, double* dep_out, double* sig_out,
+                                           double* lnp_out) {
+    if (b.cell == LLONG_MAX) {
+        Q_out[p] = 0.0;
+        T0_out[p] = NAN;
+        Didx_out[p] = -1;
+        dep_out[p] = NAN;
+        sig_out[p] = NAN;
+        lnp_out[p] = -INFINITY;
+    } else {
+        const int d = (int)(b.cell / n_phi);
+        const int64_t j = b.cell - (int64_t)d * n_phi;
+        Q_out[p] = b.depth / b.sigma;
+        T0_out[p] = __dadd_rn(t_ref, __dmul_rn((double)j / (double)n_phi, P));
+        Didx_out[p] = d;
+        dep_out[p] = b.depth;
+        sig_out[p] = b.sigma;
+        lnp_out[p] = b.lnp;
+    }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_fold(FoldGeom g, const T* __restrict__ depth, const T* __restrict__ sig,
-       const T* __restrict__ gain, int n_D, const double* __restrict__ periods,
-       int64_t n_P, double* __restrict__ Q_out, double* __restrict__ T0_out,
-       int* __restrict__ Didx_out, double* __restrict__ dep_out,
-       double* __restrict__ sig_out, double* __restrict__ lnp_out) {
-    const int64_t p = blockIdx.x;
-    if (p >= n_P) return;
-    const double P = periods[p];
-    // a period must be finite, > 0 and give at most 1e9 epochs and phases;
-    // anything else is reported as NaN with no cell (and does no work)
-    if (!(P > 0.0) || !isfinite(P) || (g.t_last - g.t_ref) / P > 1.0e9 ||
-        P / g.dt > 1.0e9) {
-        if (threadIdx.x == 0) {
-            Q_out[p] = NAN;
-            T0_out[p] = NAN;
-            Didx_out[p] = -1;
-            dep_out[p] = NAN;
-            sig_out[p] = NAN;
-            lnp_out[p] = NAN;
-        }
-        return;
-    }
-    const int64_t n_phi = (int64_t)ceil(P / g.dt);
-    const int64_t n_cells = n_phi * n_D;
-    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
-    for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
-        const int d = (int)(cell / n_phi);
-        const int64_t j = cell - (int64_t)d * n_phi;
-        const double phi = (double)j / (double)n_phi;
-        const T* dp = depth + (int64_t)d * g.n_t0;
-        const T* sp = sig + (int64_t)d * g.n_t0;
-        const T* lp = gain + (int64_t)d * g.n_t0;
-        KSum<T> s_inv, s_d, s_l;
-        s_inv.init();
-        s_d.init();
-        s_l.init();
-        int K = 0;
-        for (int64_t k = 0;; ++k) {
-            const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
-            if (Tk > g.t_last) break;
-            T dk, sk2, lk;
-            if (!event<T>(g, dp, sp, lp, Tk, dk, sk2, lk)) continue;
-            const T iv = T(1) / sk2;
-            s_inv.add(iv);
-            s_d.add(dk * iv);
-            s_l.add(lk);
-            ++K;
-        }
-        if (K == 0) continue;
-        const T s2 = T(1) / s_inv.s;
-        const T Dl = s2 * s_d.s;
-        KSum<T> pen;
-        pen.init();
-        for (int64_t k = 0;; ++k) {
-            const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
-            if (Tk > g.t_last) break;
-            T dk, sk2, lk;
-            if (!event<T>(g, dp, sp, lp, Tk, dk, sk2, lk)) continue;
-            const T den = sk2 + s2;
-            const T r = dk - Dl;
-            // ln s_k^2 - ln(sigma^2 + s_k^2) = -ln(1 + sigma^2 / s_k^2)
-            pen.add(-log1p(s2 / sk2) + r * r / den);
-        }
-        const double lnp = (double)s_l.s - 0.5 * (double)pen.s;
-        if (!(lnp == lnp)) continue;   // NaN never selected
-        Best cand{lnp, (long long)cell, (double)Dl, sqrt((double)s2)};
-        if (better(cand, best)) best = cand;
-    }
-    // block argmax
+__device__ __forceinline__ Best block_argmax(Best best) {
     __shared__ Best sh[256];
     sh[threadIdx.x] = best;
     __syncthreads();
@@ -200,26 +207,312 @@ k_fold(FoldGeom g, const T* __restrict__ depth, const T* __restrict__ sig,
             sh[threadIdx.x] = sh[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const Best b = sh[0];
-        if (b.cell == LLONG_MAX) {
-            Q_out[p] = 0.0;
-            T0_out[p] = NAN;
-            Didx_out[p] = -1;
-            dep_out[p] = NAN;
-            sig_out[p] = NAN;
-            lnp_out[p] = -INFINITY;
-        } else {
-            const int d = (int)(b.cell / n_phi);
-            const int64_t j = b.cell - (int64_t)d * n_phi;
-            Q_out[p] = b.depth / b.sigma;
-            T0_out[p] = __dadd_rn(g.t_ref, __dmul_rn((double)j / (double)n_phi, P));
-            Didx_out[p] = d;
-            dep_out[p] = b.depth;
-            sig_out[p] = b.sigma;
-            lnp_out[p] = b.lnp;
-        }
+    return sh[0];
+}
+
+__device__ __forceinline__ bool bad_period(double P, const FoldGeom& g) {
+    // a period must be finite, > 0 and give at most 1e9 epochs and phases
+    return !(P > 0.0) || !isfinite(P) || (g.t_last - g.t_ref) / P > 1.0e9 ||
+           P / g.dt > 1.0e9;
+}
+
+__device__ __forceinline__ void write_bad(int64_t p, double* Q_out, double* T0_out,
+                                          int* Didx_out, double* dep_out, double* sig_out,
+                                          double* lnp_out) {
+    Q_out[p] = NAN;
+    T0_out[p] = NAN;
+    Didx_out[p] = -1;
+    dep_out[p] = NAN;
+    sig_out[p] = NAN;
+    lnp_out[p] = NAN;
+}
+
+// ------------------------------------------------ exact path (FP64 epochs)
+// largest i with t0[i] <= T starting from a guess (exact)
+__device__ __forceinline__ int64_t bracket_from(const FoldGeom& g, double T, int64_t i) {
+    while (i + 1 < g.n_t0 && g.t0s[i + 1] <= T) ++i;
+    while (i > 0 && g.t0s[i] > T) --i;
+    return i;
+}
+
+__device__ __forceinline__ int64_t bracket_guess(const FoldGeom& g, double T) {
+    int64_t b = (int64_t)((T - g.t_ref) * g.inv_dt);
+    b = b < 0 ? 0 : (b >= g.n_bucket ? g.n_bucket - 1 : b);
+    const int64_t i = (int64_t)g.bucket[b] - 1;
+    return i < 0 ? 0 : i;
+}
+
+template <typename T> __device__ __forceinline__ T rcp_t(T x);
+template <> __device__ __forceinline__ double rcp_t<double>(double x) { return rcp64(x); }
+template <> __device__ __forceinline__ float rcp_t<float>(float x) { return rcp32(x); }
+
+// One single event at epoch Tk: interpolated depth, variance and gain.
+template <typename T>
+__device__ __forceinline__ bool event_exact(const FoldGeom& g, const Node4<T>* __restrict__ nd,
+                                            double Tk, int64_t& i, T& dk, T& sk2, T& lk) {
+    i = bracket_from(g, Tk, i);
+    if (i > g.n_t0 - 2) return false;
+    const Node4<T> a = nd[i];
+    const Node4<T> b = nd[i + 1];
+    const T w = (T)((Tk - g.t0s[i]) * (double)a.ig);   // NaN across a gap
+    const T s = a.s + w * (b.s - a.s);
+    if (isnan(s)) return false;
+    dk = a.d + w * (b.d - a.d);
+    lk = a.l + w * (b.l - a.l);
+    sk2 = s * s;
+    return true;
+}
+
+// Fixed-point (24.40) walk of the slot grid u = (T - t_ref)/dt used to guess
+// brackets; the decisions themselves are FP64 comparisons with T.
+struct SlotWalk {
+    unsigned long long u0, ustep;
+};
+__device__ __forceinline__ SlotWalk slot_walk(double phi, double R) {
+    const double SCALE = 1099511627776.0;   // 2^40
+    SlotWalk w;
+    const double a = phi * R * SCALE, b = R * SCALE;
+    w.u0 = a < 4.0e18 ? (unsigned long long)llrint(a) : 4000000000000000000ull;
+    w.ustep = b < 4.0e18 ? (unsigned long long)llrint(b) : 4000000000000000000ull;
+    return w;
+}
+__device__ __forceinline__ int64_t guess_at(const FoldGeom& g, unsigned long long u) {
+    int64_t b = (int64_t)(u >> 40);
+    b = b >= g.n_bucket ? g.n_bucket - 1 : b;
+    const int64_t i = (int64_t)g.bucket[b] - 1;
+    return i < 0 ? 0 : i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
+             const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
+             double* __restrict__ T0_out, int* __restrict__ Didx_out,
+             double* __restrict__ dep_out, double* __restrict__ sig_out,
+             double* __restrict__ lnp_out) {
+    const int64_t p = blockIdx.x;
+    if (p >= n_P) return;
+    const double P = periods[p];
+    if (bad_period(P, g)) {
+        if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
+        return;
     }
+    const int64_t n_phi = (int64_t)ceil(P / g.dt);
+    const int64_t n_cells = n_phi * n_D;
+    const double R = P * g.inv_dt;
+    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
+        const int d = (int)(cell / n_phi);
+        const int64_t j = cell - (int64_t)d * n_phi;
+        const double phi = (double)j / (double)n_phi;
+        const Node4<T>* nd = nodes + (int64_t)d * g.n_t0;
+        const SlotWalk sw = slot_walk(phi, R);
+        KSum<T> s_inv, s_d, s_l;
+        s_inv.init();
+        s_d.init();
+        s_l.init();
+        int K = 0;
+        unsigned long long u = sw.u0;
+        for (int64_t k = 0;; ++k, u += sw.ustep) {
+            const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
+            if (Tk > g.t_last) break;
+            T dk, sk2, lk;
+            int64_t i = guess_at(g, u);
+            if (!event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) continue;
+            const T iv = rcp_t<T>(sk2);
+            s_inv.add(iv);
+            s_d.add(dk * iv);
+            s_l.add(lk);
+            ++K;
+        }
+        if (K == 0) continue;
+        const T s2 = T(1) / s_inv.s;
+        const T Dl = s2 * s_d.s;
+        // second sum of Eq. result: ln s_k^2 - ln(sigma^2 + s_k^2) accumulated
+        // as the log of a product of ratios in [1/2, 1] (renormalised), plus
+        // (Delta_k - Delta)^2 / (s_k^2 + sigma^2)
+        KSum<T> quad;
+        quad.init();
+        double prod = 1.0;
+        int expo = 0, cnt = 0;
+        float lsum = 0.f;
+        u = sw.u0;
+        for (int64_t k = 0;; ++k, u += sw.ustep) {
+            const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
+            if (Tk > g.t_last) break;
+            T dk, sk2, lk;
+            int64_t i = guess_at(g, u);
+            if (!event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) continue;
+            const T den = sk2 + s2;
+            const T iden = rcp_t<T>(den);
+            const T r = dk - Dl;
+            quad.add(r * r * iden);
+            if (sizeof(T) == 8) {
+                prod *= (double)(sk2 * iden);
+                if ((++cnt & 255) == 0) {
+                    const int e = ((__double2hiint(prod) >> 20) & 0x7ff) - 1023;
+                    prod = __hiloint2double(__double2hiint(prod) - (e << 20),
+                                            __double2loint(prod));
+                    expo += e;
+                }
+            } else {
+                lsum += lg2_32((float)(sk2 * iden));
+            }
+        }
+        double logsum;
+        if (sizeof(T) == 8) logsum = log(prod) + (double)expo * 0.69314718055994530942;
+        else logsum = (double)lsum * 0.69314718055994530942;
+        const double lnp = (double)s_l.s - 0.5 * (logsum + (double)quad.s);
+        if (!(lnp == lnp)) continue;   // NaN never selected
+        Best cand{lnp, (long long)cell, (double)Dl, sqrt((double)s2)};
+        if (better(cand, best)) best = cand;
+    }
+    const Best b = block_argmax(best);
+    if (threadIdx.x == 0)
+        write_best(b, p, n_phi, g.t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
+}
+
+// ---------------------------------------- slot path (mixed, regular grids)
+// Epochs walk the slot grid in 24.40 fixed point: u = (T - t_ref)/dt =
+// (j/n_phi + k) P/dt.  The interval is (slot, slot+1) and the weight is the
+// fractional part; on a grid whose epochs sit on the slots this is the
+// exact interpolation up to the epochs' offsets from the slot centres.
+struct SlotEvent {
+    float d, s, l;
+};
+__device__ __forceinline__ SlotEvent slot_event(const Node4<float>* __restrict__ rd,
+                                                unsigned long long u) {
+    const int64_t s = (int64_t)(u >> 40);
+    const float w = (float)((unsigned)((u >> 16) & 0xffffffu)) * 5.9604644775390625e-8f;
+    const Node4<float> a = rd[s];
+    const Node4<float> b = rd[s + 1];
+    SlotEvent e;
+    e.s = a.s + w * (b.s - a.s);
+    e.d = a.d + w * (b.d - a.d);
+    e.l = a.l + w * (b.l - a.l);
+    return e;
+}
+
+struct SlotPass1 {
+    KSum<float> s_inv, s_d, s_l;
+    int K;
+    __device__ __forceinline__ void init() {
+        s_inv.init();
+        s_d.init();
+        s_l.init();
+        K = 0;
+    }
+    __device__ __forceinline__ void add(const SlotEvent& e) {
+        if (isnan(e.s)) return;
+        const float iv = rcp32(e.s * e.s);
+        s_inv.add(iv);
+        s_d.add(e.d * iv);
+        s_l.add(e.l);
+        ++K;
+    }
+};
+
+struct SlotPass2 {
+    KSum<float> quad;
+    float lsum;
+    float s2, Dl;
+    __device__ __forceinline__ void init(float s2_, float Dl_) {
+        quad.init();
+        lsum = 0.f;
+        s2 = s2_;
+        Dl = Dl_;
+    }
+    __device__ __forceinline__ void add(float dk, float sg) {
+        if (isnan(sg)) return;
+        const float sk2 = sg * sg;
+        const float iden = rcp32(sk2 + s2);
+        const float r = dk - Dl;
+        quad.add(r * r * iden);
+        lsum += lg2_32(sk2 * iden);
+    }
+};
+
+// Epochs walk the slot grid in 24.40 fixed point: u = (T - t_ref)/dt =
+// (j/n_phi + k) P/dt.  The interval is (slot, slot+1) and the weight is the
+// fractional part; on a grid whose epochs sit on the slots this is the
+// interpolation between the bracketing epochs up to their offsets from the
+// slot centres (checked to be below 1e-3 slot).  Cells with at most KC epochs
+// keep their events in registers for the second pass.
+template <int KC>
+__global__ void __launch_bounds__(256)
+k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, double dt,
+             double t_ref, double t_last, const double* __restrict__ periods, int64_t n_P,
+             double* __restrict__ Q_out, double* __restrict__ T0_out,
+             int* __restrict__ Didx_out, double* __restrict__ dep_out,
+             double* __restrict__ sig_out, double* __restrict__ lnp_out) {
+    const int64_t p = blockIdx.x;
+    if (p >= n_P) return;
+    const double P = periods[p];
+    FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
+    if (bad_period(P, gg)) {
+        if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
+        return;
+    }
+    const int64_t n_phi = (int64_t)ceil(P / dt);
+    const int64_t n_cells = n_phi * n_D;
+    const double R = P / dt;                                   // slots per period
+    const double SCALE = 1099511627776.0;                      // 2^40
+    const double ulast_d = (t_last - t_ref) / dt * SCALE;       // < 2^62 (host check)
+    const unsigned long long ulast = (unsigned long long)llrint(ulast_d);
+    const unsigned long long ustep =
+        R * SCALE < 4.0e18 ? (unsigned long long)llrint(R * SCALE) : 4000000000000000000ull;
+    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
+        const int d = (int)(cell / n_phi);
+        const int64_t j = cell - (int64_t)d * n_phi;
+        const double u0_d = ((double)j / (double)n_phi) * R * SCALE;
+        if (!(u0_d <= ulast_d)) continue;
+        const unsigned long long u0 = (unsigned long long)llrint(u0_d);
+        if (u0 > ulast) continue;
+        const int64_t kmax = (int64_t)((ulast - u0) / ustep) + 1;
+        const Node4<float>* rd = rec + (int64_t)d * n_slots;
+        SlotPass1 p1;
+        p1.init();
+        SlotPass2 p2;
+        if (kmax <= KC) {
+            float cd[KC], cs[KC];
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                cs[k] = NAN;
+                cd[k] = 0.f;
+                if (k < kmax) {
+                    const SlotEvent e = slot_event(rd, u0 + (unsigned long long)k * ustep);
+                    cd[k] = e.d;
+                    cs[k] = e.s;
+                    p1.add(e);
+                }
+            }
+            if (p1.K == 0) continue;
+            const float s2 = 1.0f / p1.s_inv.s;
+            p2.init(s2, s2 * p1.s_d.s);
+#pragma unroll
+            for (int k = 0; k < KC; ++k) p2.add(cd[k], cs[k]);
+        } else {
+            unsigned long long u = u0;
+            for (int64_t k = 0; k < kmax; ++k, u += ustep) p1.add(slot_event(rd, u));
+            if (p1.K == 0) continue;
+            const float s2 = 1.0f / p1.s_inv.s;
+            p2.init(s2, s2 * p1.s_d.s);
+            u = u0;
+            for (int64_t k = 0; k < kmax; ++k, u += ustep) {
+                const SlotEvent e = slot_event(rd, u);
+                p2.add(e.d, e.s);
+            }
+        }
+        const double lnp = (double)p1.s_l.s -
+                           0.5 * ((double)p2.lsum * 0.69314718055994530942 + (double)p2.quad.s);
+        if (!(lnp == lnp)) continue;
+        Best cand{lnp, (long long)cell, (double)p2.Dl, sqrt((double)p2.s2)};
+        if (better(cand, best)) best = cand;
+    }
+    const Best b = block_argmax(best);
+    if (threadIdx.x == 0)
+        write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
 }  // namespace nu
@@ -279,35 +572,78 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
     const double span_steps = (t_last - t_ref) / phase_step;
     if (span_steps > 1.0e9) return fail(NU_EINVAL, "nu_periodic_search: phase grid too fine");
     const int64_t n_bucket = (int64_t)span_steps + 2;
-    const size_t esz = prec == NU_FP64 ? sizeof(double) : sizeof(float);
+    const bool fp64 = prec == NU_FP64;
+    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+    const int64_t ngrid = n_t0 * (int64_t)n_D;
+    const int64_t n_slots = n_bucket + 2;          // slot records, NaN padded
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_nodes = al((size_t)ngrid * 4 * esz);
+    const size_t b_bucket = al((size_t)n_bucket * sizeof(int));
+    const size_t b_slot_of = al((size_t)n_t0 * sizeof(int));
+    const size_t b_flag = 256;
+    const size_t b_rec = fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>));
     pool_keep_memory();
-    void* scratch = nullptr;
-    const size_t sig_bytes = ((size_t)n_t0 * n_D * esz + 255) / 256 * 256;
-    e = cudaMallocAsync(&scratch, sig_bytes + n_bucket * sizeof(int), st);
+    char* scratch = nullptr;
+    e = cudaMallocAsync((void**)&scratch, b_nodes + b_bucket + b_slot_of + b_flag + b_rec, st);
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: cudaMallocAsync");
-    void* sig = scratch;
-    int* bucket = (int*)((char*)scratch + sig_bytes);
-    k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
-                                                    n_bucket, bucket);
-    FoldGeom g{t0s_dev, n_t0, t_ref, t_last, phase_step, 1.0 / phase_step,
-               gap_factor * phase_step, bucket, n_bucket};
-    const int64_t nsig = n_t0 * (int64_t)n_D;
-    if (prec == NU_FP64) {
-        k_sqrt<double><<<div_up(nsig, 256), 256, 0, st>>>((const double*)var_dev,
-                                                        (double*)sig, nsig);
-        k_fold<double><<<(unsigned)n_P, 256, 0, st>>>(
-            g, (const double*)depth_dev, (const double*)sig, (const double*)dlnl_dev, n_D,
-            periods_dev, n_P, Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
-            lnP_dev);
-    } else {
-        k_sqrt<float><<<div_up(nsig, 256), 256, 0, st>>>((const float*)var_dev,
-                                                       (float*)sig, nsig);
-        k_fold<float><<<(unsigned)n_P, 256, 0, st>>>(
-            g, (const float*)depth_dev, (const float*)sig, (const float*)dlnl_dev, n_D,
-            periods_dev, n_P, Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
-            lnP_dev);
+    void* nodes = scratch;
+    int* bucket = (int*)(scratch + b_nodes);
+    int* slot_of = (int*)(scratch + b_nodes + b_bucket);
+    int* flag = (int*)(scratch + b_nodes + b_bucket + b_slot_of);
+    Node4<float>* rec = (Node4<float>*)(scratch + b_nodes + b_bucket + b_slot_of + b_flag);
+    int launched = 0;
+    // the slot path needs a regular grid and a gap rule that only joins
+    // neighbouring slots (1 < gap_factor < 2)
+    bool use_slots = !fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span_steps < 4.0e6;
+    if (use_slots) {
+        int irregular = 0;
+        e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+        k_slots<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, 1.0 / phase_step,
+                                                  slot_of, flag);
+        ++launched;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&irregular, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(scratch, st);
+            return cuda_fail(e, "nu_periodic_search: slot test");
+        }
+        use_slots = irregular == 0;
     }
-    count_launches(3);
+    if (use_slots) {
+        const int64_t nrec = n_slots * n_D;
+        k_fill_nan<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec);
+        k_slot_fill<<<div_up(ngrid, 256), 256, 0, st>>>(
+            (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
+            n_t0, n_D, n_slots, rec);
+        k_fold_slots<8><<<(unsigned)n_P, 256, 0, st>>>(rec, n_slots, n_D, phase_step, t_ref,
+                                                      t_last, periods_dev, n_P, Q_dev, T0_dev,
+                                                      D_idx_dev, depth_out_dev, sigma_out_dev,
+                                                      lnP_dev);
+        launched += 3;
+    } else {
+        k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
+                                                        n_bucket, bucket);
+        FoldGeom g{t0s_dev, n_t0, t_ref, t_last, phase_step, 1.0 / phase_step,
+                   gap_factor * phase_step, bucket, n_bucket};
+        if (fp64) {
+            k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
+                t0s_dev, n_t0, n_D, g.gap_max, (Node4<double>*)nodes);
+            k_fold_exact<double><<<(unsigned)n_P, 256, 0, st>>>(
+                g, (const Node4<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+        } else {
+            k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
+                t0s_dev, n_t0, n_D, g.gap_max, (Node4<float>*)nodes);
+            k_fold_exact<float><<<(unsigned)n_P, 256, 0, st>>>(
+                g, (const Node4<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+        }
+        launched += 3;
+    }
+    count_launches(launched);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: launch");
     e = cudaFreeAsync(scratch, st);

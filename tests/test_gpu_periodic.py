@@ -126,3 +126,36 @@ def test_fold_fp64_sector_shape_sampled_periods():
                                       w.periods[sel], dt, FP64_TOL, FP64_TOL,
                                       periodic.fold_period)
     print(f"sector fold fp64 sampled: lnP err {wl:.2e}, Q err {wq:.2e}, ties {differ}")
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.3])
+def test_fold_mixed_gapped_and_irregular(jitter):
+    """Mixed precision on a gapped grid with NaN holes: the fixed-point slot
+    walk (regular epochs) and the exact FP64-epoch walk (jittered epochs)."""
+    rng = np.random.default_rng(23)
+    dt = synth.CADENCE_DAYS
+    t0s = np.concatenate([np.arange(900), np.arange(1100, 1900)]) * dt
+    t0s = t0s + jitter * dt * rng.uniform(-1, 1, len(t0s)) * (np.arange(len(t0s)) % 3 == 1)
+    n = len(t0s)
+    g = dict(depth=rng.normal(0, 1e-3, (4, n)), var=rng.uniform(1e-8, 5e-8, (4, n)),
+             dlnl=rng.uniform(0, 8, (4, n)))
+    g["depth"][2, 300:320] = np.nan
+    periods = np.concatenate([np.linspace(0.03, 1.0, 200), [2.3, 2.61, 3.9]])
+    ora = periodic.periodic_search(t0s, g["depth"], g["var"], g["dlnl"], periods, dt)
+    gpu = _gpu_fold(t0s, np.ones(4), g, periods, "mixed", phase_step=dt)
+    wl, wq, differ = periodic_compare(gpu, ora, t0s, g["depth"], g["var"], g["dlnl"],
+                                      periods, dt, 1e-4, MIXED_SNR_ABS, periodic.fold_period,
+                                      max_reeval=len(periods), q_abs=True)
+    print(f"mixed fold jitter={jitter}: lnP err {wl:.2e}, Q abs err {wq:.2e}, ties {differ}")
+
+
+def test_fold_invalid_periods_are_nan():
+    t0s = np.arange(200) * synth.CADENCE_DAYS
+    rng = np.random.default_rng(2)
+    g = dict(depth=rng.normal(0, 1e-3, (1, 200)), var=np.full((1, 200), 1e-8),
+             dlnl=rng.uniform(0, 2, (1, 200)))
+    periods = np.array([0.05, -1.0, np.nan, 1e-300, 0.07])
+    for prec in ("fp64", "mixed"):
+        gpu = _gpu_fold(t0s, np.ones(1), g, periods, prec, phase_step=synth.CADENCE_DAYS)
+        assert np.isnan(gpu["Q"][1:4]).all() and (gpu["D_idx"][1:4] == -1).all()
+        assert np.isfinite(gpu["Q"][[0, 4]]).all()
