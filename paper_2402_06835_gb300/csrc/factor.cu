@@ -14,10 +14,12 @@
 //   zero from sample n on contributes s_n^T G_n s_n to sum e^2 / D.
 // The null model (X alone) is solved through these: X^T Sigma^-1 X and
 // X^T Sigma^-1 y are dot products of forward innovations weighted by 1/D.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 
+#include "factor_ops.cuh"
 #include "nu_internal.cuh"
 #include "ss.cuh"
 
@@ -56,131 +58,6 @@ __global__ void k_transitions(const double* __restrict__ t, int64_t n, Blocks bl
         block_transition(bl.b[b], tau, f);
         Fi[4 * b] = f[0]; Fi[4 * b + 1] = f[1]; Fi[4 * b + 2] = f[2]; Fi[4 * b + 3] = f[3];
     }
-}
-
-// -------------------------------------------------------------- Riccati pass
-// One thread: the pivots and gains (sequential by nature).
-template <int NB>
-__global__ void k_riccati(int64_t n, Blocks bl, const double* __restrict__ diag_var,
-                          const double* __restrict__ F, double* __restrict__ kg,
-                          double* __restrict__ invD, double* __restrict__ Dpiv,
-                          long long* dstat) {
-    constexpr int J = Dims<NB>::J;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double Pinf_h[J];
-    double prior = 0.0;
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        Pinf_h[2 * b] = bl.b[b].sigma2;
-        Pinf_h[2 * b + 1] = 0.0;
-        prior += bl.b[b].sigma2;
-    }
-    double M[J][J];
-#pragma unroll
-    for (int r = 0; r < J; ++r)
-#pragma unroll
-        for (int c = 0; c < J; ++c) M[r][c] = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        double Mh[J];
-#pragma unroll
-        for (int r = 0; r < J; ++r) {
-            double s = M[r][0];
-#pragma unroll
-            for (int b = 1; b < NB; ++b) s += M[r][2 * b];
-            Mh[r] = s;
-        }
-        const double hMh = hdot<NB>(Mh);
-        const double D = (prior + diag_var[i]) - hMh;
-        if (!(D > 0.0) || !isfinite(D)) {
-            flag_bad(dstat, ST_ENOTPD, i);
-            return;
-        }
-        const double iD = 1.0 / D;
-        double kt[J];
-#pragma unroll
-        for (int r = 0; r < J; ++r) {
-            kt[r] = Pinf_h[r] - Mh[r];
-            kg[i * J + r] = kt[r] * iD;
-        }
-        invD[i] = iD;
-        Dpiv[i] = D;
-        if (i + 1 == n) break;
-        // M+ = M + kt kt^T / D, then M = F M+ F^T
-#pragma unroll
-        for (int r = 0; r < J; ++r)
-#pragma unroll
-            for (int c = 0; c < J; ++c) M[r][c] += kt[r] * kt[c] * iD;
-        const double* Fn = F + (i + 1) * NB * 4;
-        double T[J][J];
-#pragma unroll
-        for (int c = 0; c < J; ++c) {
-            double col[J], out[J];
-#pragma unroll
-            for (int r = 0; r < J; ++r) col[r] = M[r][c];
-            apply_F<NB>(Fn, col, out);
-#pragma unroll
-            for (int r = 0; r < J; ++r) T[r][c] = out[r];
-        }
-#pragma unroll
-        for (int r = 0; r < J; ++r) {
-            double out[J];
-            apply_F<NB>(Fn, T[r], out);
-#pragma unroll
-            for (int c = 0; c < J; ++c) M[r][c] = out[c];
-        }
-        // keep M exactly symmetric
-#pragma unroll
-        for (int r = 0; r < J; ++r)
-#pragma unroll
-            for (int c = r + 1; c < J; ++c) {
-                const double s = 0.5 * (M[r][c] + M[c][r]);
-                M[r][c] = s;
-                M[c][r] = s;
-            }
-    }
-}
-
-// ------------------------------------------------------ forward multi-solve
-// One thread: innovations of y and of the columns of X, and the weighted
-// cross products e_a^T D^-1 e_b (= a^T Sigma^-1 b).
-template <int NB>
-__global__ void k_forward(int64_t n, int k, const double* __restrict__ X,
-                          const double* __restrict__ y, const double* __restrict__ F,
-                          const double* __restrict__ kg, const double* __restrict__ invD,
-                          double* __restrict__ E, double* __restrict__ cross) {
-    constexpr int J = Dims<NB>::J;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int nr = k + 1;           // columns of X, then y
-    double s[NU_MAX_K + 1][J];
-    double acc[NU_MAX_K + 1][NU_MAX_K + 1];
-    for (int r = 0; r < nr; ++r) {
-        for (int c = 0; c < J; ++c) s[r][c] = 0.0;
-        for (int c = 0; c < nr; ++c) acc[r][c] = 0.0;
-    }
-    for (int64_t i = 0; i < n; ++i) {
-        const double iD = invD[i];
-        double e[NU_MAX_K + 1];
-        for (int r = 0; r < nr; ++r) {
-            const double x = (r < k) ? X[(int64_t)r * n + i] : y[i];
-            e[r] = x - hdot<NB>(s[r]);
-            E[i * nr + r] = e[r];
-        }
-        for (int r = 0; r < nr; ++r)
-            for (int c = 0; c <= r; ++c) acc[r][c] += e[r] * e[c] * iD;
-        if (i + 1 == n) break;
-        const double* Fn = F + (i + 1) * NB * 4;
-        for (int r = 0; r < nr; ++r) {
-            double tmp[J];
-#pragma unroll
-            for (int c = 0; c < J; ++c) tmp[c] = s[r][c] + kg[i * J + c] * e[r];
-            apply_F<NB>(Fn, tmp, s[r]);
-        }
-    }
-    for (int r = 0; r < nr; ++r)
-        for (int c = 0; c <= r; ++c) {
-            cross[r * nr + c] = acc[r][c];
-            cross[c * nr + r] = acc[r][c];
-        }
 }
 
 // -------------------------------------------------------------- null GLS
@@ -261,98 +138,6 @@ __global__ void k_rhs(int64_t n, int k, const double* __restrict__ E,
     logD[i] = log(Dpiv[i]);
 }
 
-// ---------------------------------------------------------- backward solves
-// One thread per right-hand side r: V[:, r] = L^-T U[:, r].
-template <int NB>
-__global__ void k_backward(int64_t n, int nr, const double* __restrict__ F,
-                           const double* __restrict__ kg, const double* __restrict__ U,
-                           double* __restrict__ z0, double* __restrict__ Zt, int k) {
-    constexpr int J = Dims<NB>::J;
-    const int r = threadIdx.x;
-    if (blockIdx.x != 0 || r >= nr) return;
-    double g[J];
-#pragma unroll
-    for (int c = 0; c < J; ++c) g[c] = 0.0;
-    for (int64_t i = n - 1; i >= 0; --i) {
-        double v = U[i * nr + r];
-#pragma unroll
-        for (int c = 0; c < J; ++c) v -= kg[i * J + c] * g[c];
-        if (r == 0) z0[i] = v; else Zt[i * k + (r - 1)] = v;
-        if (i == 0) break;
-        double tmp[J];
-#pragma unroll
-        for (int c = 0; c < J; ++c) tmp[c] = g[c];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) tmp[2 * b] += v;
-        apply_FT<NB>(F + i * NB * 4, tmp, g);
-    }
-}
-
-// ---------------------------------------------------- future information G
-template <int NB>
-__global__ void k_future(int64_t n, const double* __restrict__ F,
-                         const double* __restrict__ kg, const double* __restrict__ invD,
-                         double* __restrict__ G) {
-    constexpr int J = Dims<NB>::J;
-    constexpr int JJ = Dims<NB>::JJ;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double Gm[J][J];
-#pragma unroll
-    for (int r = 0; r < J; ++r)
-#pragma unroll
-        for (int c = 0; c < J; ++c) Gm[r][c] = 0.0;
-    for (int64_t i = n - 1; i >= 0; --i) {
-        if (i < n - 1) {
-            // A = F_{i+1} (I - kg_i h^T);  G <- A^T G A
-            const double* Fn = F + (i + 1) * NB * 4;
-            double A[J][J];
-#pragma unroll
-            for (int c = 0; c < J; ++c) {
-                double col[J], out[J];
-                const bool hc = (c % 2) == 0;
-#pragma unroll
-                for (int r = 0; r < J; ++r)
-                    col[r] = (r == c ? 1.0 : 0.0) - (hc ? kg[i * J + r] : 0.0);
-                apply_F<NB>(Fn, col, out);
-#pragma unroll
-                for (int r = 0; r < J; ++r) A[r][c] = out[r];
-            }
-            double T[J][J];   // T = G A
-#pragma unroll
-            for (int r = 0; r < J; ++r)
-#pragma unroll
-                for (int c = 0; c < J; ++c) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int p = 0; p < J; ++p) s += Gm[r][p] * A[p][c];
-                    T[r][c] = s;
-                }
-#pragma unroll
-            for (int r = 0; r < J; ++r)
-#pragma unroll
-                for (int c = r; c < J; ++c) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int p = 0; p < J; ++p) s += A[p][r] * T[p][c];
-                    Gm[r][c] = s;
-                    Gm[c][r] = s;
-                }
-        }
-        const double iD = invD[i];
-#pragma unroll
-        for (int r = 0; r < J; r += 2)
-#pragma unroll
-            for (int c = 0; c < J; c += 2) {
-                Gm[r][c] += iD;
-            }
-        double* Gi = G + i * JJ;
-#pragma unroll
-        for (int r = 0; r < J; ++r)
-#pragma unroll
-            for (int c = r; c < J; ++c) Gi[pk(r, c, J)] = Gm[r][c];
-    }
-}
-
 // -------------------------------------------------- deterministic reductions
 // partial[b] = sum over a contiguous range; then one block sums the partials.
 __global__ void k_sum_partial(const double* __restrict__ x, int64_t n, double* partial) {
@@ -369,6 +154,23 @@ __global__ void k_sum_partial(const double* __restrict__ x, int64_t n, double* p
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// cross[a][b] = sum over chunks of partial[c][a][b] (one block per entry)
+__global__ void k_reduce_cross(const double* __restrict__ partial, int64_t n_chunks, int nr,
+                               double* __restrict__ cross) {
+    __shared__ double sh[256];
+    const int a = blockIdx.x / nr, b = blockIdx.x % nr;
+    double s = 0.0;
+    for (int64_t c = threadIdx.x; c < n_chunks; c += blockDim.x)
+        s += partial[c * NRMAX * NRMAX + a * NRMAX + b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cross[a * nr + b] = sh[0];
 }
 
 __global__ void k_finalize(int64_t n, int nparts, const double* __restrict__ pchi,
@@ -391,17 +193,33 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 }
 
 // ------------------------------------------------------------------ driver
+// chunk length, group size and top-level count of the scans
+constexpr int SCAN_B = 32;
+constexpr int SCAN_G = 8;
+constexpr int SCAN_TOP = 16;
+
+template <int NB>
+static size_t factor_workspace(int64_t n, int k) {
+    const int64_t nc = (n + SCAN_B - 1) / SCAN_B;
+    size_t m = plan_scan<RiccatiOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes;
+    m = std::max(m, plan_scan<ForwardOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes);
+    m = std::max(m, plan_scan<BackwardOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes);
+    m = std::max(m, plan_scan<FutureOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes);
+    (void)k;
+    return m + (size_t)nc * NRMAX * NRMAX * sizeof(double) + 512;
+}
+
 template <int NB>
 static nu_status run_factor(nu_factor* f, const double* diag_var, const double* X,
-                            const double* y, double* scratch) {
+                            const double* y, double* scratch, char* ws) {
     constexpr int J = Dims<NB>::J;
     constexpr int JJ = Dims<NB>::JJ;
-    (void)J; (void)JJ;
     const int64_t n = f->n;
     const int k = f->k;
     const int nr = k + 1;
     cudaStream_t st = f->stream;
     const int nblk = div_up(n, 256);
+    const int64_t nc = (n + SCAN_B - 1) / SCAN_B;
     // scratch layout
     double* Dpiv = scratch;                 // n
     double* U = Dpiv + n;                   // n * nr
@@ -411,30 +229,70 @@ static nu_status run_factor(nu_factor* f, const double* diag_var, const double* 
     double* wR = cross + 32;                // 32
     double* pchi = wR + 32;                 // 256
     double* plog = pchi + 256;              // 256
+    int launched = 0;
     k_transitions<NB><<<nblk, 256, 0, st>>>(f->t, n, f->blocks, f->F, f->dstat);
-    k_riccati<NB><<<1, 32, 0, st>>>(n, f->blocks, diag_var, f->F, f->kg, f->invD, Dpiv,
-                                    f->dstat);
-    k_forward<NB><<<1, 32, 0, st>>>(n, k, X, y, f->F, f->kg, f->invD, f->work, cross);
-    if (k > 0) k_null_gls<<<1, 32, 0, st>>>(k, cross, wR, f->dstat);
+    ++launched;
+    // 1. pivots and gains
+    RiccatiOp<NB> ric;
+    ric.F = f->F;
+    ric.dv = diag_var;
+    ric.n = n;
+    ric.B = SCAN_B;
+    for (int b = 0; b < NB; ++b) {
+        ric.pinf[2 * b] = f->blocks.b[b].sigma2;
+        ric.pinf[2 * b + 1] = f->blocks.b[b].type == 0 ? f->blocks.b[b].sigma2 : 0.0;
+    }
+    ric.kg = f->kg;
+    ric.invD = f->invD;
+    ric.Dpiv = Dpiv;
+    ric.dstat = f->dstat;
+    launched += run_scan(ric, plan_scan<RiccatiOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
+    // 2. forward solves of X and y, cross products
+    double* partial = (double*)(ws + factor_workspace<NB>(n, k) -
+                                (size_t)nc * NRMAX * NRMAX * sizeof(double) - 256);
+    ForwardOp<NB> fw{f->F, f->kg, f->invD, X, y, n, k, SCAN_B, f->work, partial};
+    launched += run_scan(fw, plan_scan<ForwardOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
+    k_reduce_cross<<<nr * nr, 256, 0, st>>>(partial, nc, nr, cross);
+    ++launched;
+    // 3. null fit, right-hand sides, backward solves
+    if (k > 0) {
+        k_null_gls<<<1, 32, 0, st>>>(k, cross, wR, f->dstat);
+        ++launched;
+    }
     k_rhs<<<nblk, 256, 0, st>>>(n, k, f->work, f->invD, wR, U, chi_terms, Dpiv, logD);
-    k_backward<NB><<<1, 32, 0, st>>>(n, nr, f->F, f->kg, U, f->z0, f->Zt, k);
-    k_future<NB><<<1, 32, 0, st>>>(n, f->F, f->kg, f->invD, f->G);
+    ++launched;
+    BackwardOp<NB> bw{f->F, f->kg, U, n, nr, k, SCAN_B, nc, f->z0, f->Zt};
+    launched += run_scan(bw, plan_scan<BackwardOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
+    // 4. future information
+    FutureOp<NB> fu{f->F, f->kg, f->invD, n, SCAN_B, nc, f->G};
+    launched += run_scan(fu, plan_scan<FutureOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
+    // scalars and FP32 copies
     const int nparts = 256;
     k_sum_partial<<<nparts, 256, 0, st>>>(chi_terms, n, pchi);
     k_sum_partial<<<nparts, 256, 0, st>>>(logD, n, plog);
     k_finalize<<<1, 32, 0, st>>>(n, nparts, pchi, plog, f->scal);
+    launched += 3;
     const int64_t sizes[6] = {n * NB * 4, n * (int64_t)J, n, n * (int64_t)JJ, n, n * (int64_t)k};
     const double* src[6] = {f->F, f->kg, f->invD, f->G, f->z0, f->Zt};
     float* dst[6] = {f->F32, f->kg32, f->invD32, f->G32, f->z032, f->Zt32};
     for (int a = 0; a < 6; ++a)
-        if (sizes[a] > 0)
+        if (sizes[a] > 0) {
             k_to_f32<<<div_up(sizes[a], 256), 256, 0, st>>>(src[a], dst[a], sizes[a]);
-    int launched = 9 + (k > 0 ? 1 : 0);
-    for (int a = 0; a < 6; ++a) launched += sizes[a] > 0 ? 1 : 0;
+            ++launched;
+        }
     count_launches(launched);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "nu_gp_factor launch");
     return NU_OK;
+}
+
+static size_t workspace_bytes(int nb, int64_t n, int k) {
+    switch (nb) {
+        case 1: return factor_workspace<1>(n, k);
+        case 2: return factor_workspace<2>(n, k);
+        case 3: return factor_workspace<3>(n, k);
+        default: return factor_workspace<4>(n, k);
+    }
 }
 
 }  // namespace nu
@@ -508,12 +366,21 @@ extern "C" nu_status nu_gp_factor(const double* t_dev, const double* diag_var_de
         delete f;
         return cuda_fail(e, "nu_gp_factor: copy");
     }
-    switch (nb) {
-        case 1: s = run_factor<1>(f, diag_var_dev, X_dev, y_dev, scratch); break;
-        case 2: s = run_factor<2>(f, diag_var_dev, X_dev, y_dev, scratch); break;
-        case 3: s = run_factor<3>(f, diag_var_dev, X_dev, y_dev, scratch); break;
-        default: s = run_factor<4>(f, diag_var_dev, X_dev, y_dev, scratch); break;
+    const size_t ws_bytes = workspace_bytes(nb, n, k);
+    char* ws = nullptr;
+    e = cudaMallocAsync((void**)&ws, ws_bytes, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(f->mem, st);
+        delete f;
+        return cuda_fail(e, "nu_gp_factor: workspace");
     }
+    switch (nb) {
+        case 1: s = run_factor<1>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
+        case 2: s = run_factor<2>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
+        case 3: s = run_factor<3>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
+        default: s = run_factor<4>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
+    }
+    cudaFreeAsync(ws, st);
     if (s != NU_OK) {
         cudaFreeAsync(f->mem, st);
         delete f;

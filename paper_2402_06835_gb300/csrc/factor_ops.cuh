@@ -1,0 +1,609 @@
+// The four sequential recursions of the factor as chunked-scan operations
+// (see scan.cuh).  J = 2 NB is the state dimension, h picks the first
+// component of every 2x2 block, F_i is the block-diagonal transition into
+// sample i (F_0 is taken as 0: the prior at the first sample is P_inf).
+//
+// 1. Riccati: predicted covariances of the state-space form give the pivots
+//    D_i and gains kg_i of Sigma = L diag(D) L^T.  Chunk elements are those of
+//    the temporal parallelisation of Bayesian filters (Sarkka and
+//    Garcia-Fernandez 2021, IEEE TAC 66, 299): for a chunk, (A, C, Jm) with
+//    A the filtered-mean map from a known state before the chunk, C the
+//    filtered covariance from that known state and Jm the information the
+//    chunk's samples carry about it; they are built by running the filter
+//    from the known state, composed with
+//      A_ij = A_j X A_i, C_ij = A_j X C_i A_j^T + C_j,
+//      Jm_ij = (X A_i)^T Jm_j A_i + Jm_i,  X = (I + C_i Jm_j)^-1,
+//    and applied to an incoming filtered covariance P as
+//      A (I + P Jm)^-1 P A^T + C.
+// 2. Forward solve e = L^-1 x for the columns of X and y:
+//      s_{i+1} = F_{i+1} (s_i + kg_i (x_i - h^T s_i)),  e_i = x_i - h^T s_i,
+//    affine in s; elements (Phi, beta) map the state entering a chunk to the
+//    state leaving it.
+// 3. Backward solve v = L^-T u (reverse order):
+//      v_i = u_i - kg_i^T g_i,  g_{i-1} = F_i^T (g_i + h v_i).
+// 4. Future information G_i = h h^T / D_i + A_{i+1}^T G_{i+1} A_{i+1},
+//    A_{i+1} = F_{i+1} (I - kg_i h^T) (reverse order); elements (Psi, Gam)
+//    with G_s = Psi^T G_{e+1} Psi + Gam.
+#pragma once
+
+#include "scan.cuh"
+#include "ss.cuh"
+
+namespace nu {
+
+constexpr int NRMAX = NU_MAX_K + 1;
+
+// dense J x J copy of the block-diagonal transition into sample i
+template <int NB>
+__device__ __forceinline__ void dense_F(const double* __restrict__ F, int64_t i,
+                                        Mat<2 * NB>& Fm) {
+    mat_zero(Fm);
+    if (i == 0) return;
+    const double* f = F + i * NB * 4;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        Fm(2 * b, 2 * b) = f[4 * b];
+        Fm(2 * b, 2 * b + 1) = f[4 * b + 1];
+        Fm(2 * b + 1, 2 * b) = f[4 * b + 2];
+        Fm(2 * b + 1, 2 * b + 1) = f[4 * b + 3];
+    }
+}
+
+// M <- F M F^T for block-diagonal F (F_0 = 0)
+template <int NB>
+__device__ __forceinline__ void congruence_F(const double* __restrict__ F, int64_t i,
+                                             Mat<2 * NB>& M) {
+    constexpr int J = 2 * NB;
+    if (i == 0) {
+        mat_zero(M);
+        return;
+    }
+    const double* f = F + i * NB * 4;
+    Mat<J> T;
+#pragma unroll
+    for (int c = 0; c < J; ++c) {
+        double col[J], out[J];
+#pragma unroll
+        for (int r = 0; r < J; ++r) col[r] = M(r, c);
+        apply_F<NB>(f, col, out);
+#pragma unroll
+        for (int r = 0; r < J; ++r) T(r, c) = out[r];
+    }
+#pragma unroll
+    for (int r = 0; r < J; ++r) {
+        double row[J], out[J];
+#pragma unroll
+        for (int c = 0; c < J; ++c) row[c] = T(r, c);
+        apply_F<NB>(f, row, out);
+#pragma unroll
+        for (int c = 0; c < J; ++c) M(r, c) = out[c];
+    }
+    mat_symmetrize(M);
+}
+
+__device__ __forceinline__ void chunk_range(int64_t c, int B, int64_t n, int64_t& s,
+                                            int64_t& e) {
+    s = c * B;
+    e = s + B < n ? s + B - 1 : n - 1;
+}
+
+// --------------------------------------------------------------- Riccati
+template <int NB>
+struct RiccatiOp {
+    static constexpr int J = 2 * NB;
+    struct Elem {
+        Mat<J> A, C, Jm;
+    };
+    struct State {
+        Mat<J> P;          // filtered covariance after the previous chunk
+    };
+    const double* F;
+    const double* dv;
+    int64_t n;
+    int B;
+    double pinf[J];        // diagonal of P_inf
+    double* kg;
+    double* invD;
+    double* Dpiv;
+    long long* dstat;
+
+    __device__ void init_state(State& s) const { mat_zero(s.P); }
+
+    // one filter step from the explained covariance Mf (= P_inf - P_filtered)
+    // of the previous sample; returns D and the filtered Mf of this sample
+    __device__ __forceinline__ double step(int64_t i, Mat<J>& Mf, double* Ph) const {
+        congruence_F<NB>(F, i, Mf);                  // M_i = F_i Mf F_i^T
+        double hMh = 0.0;
+#pragma unroll
+        for (int r = 0; r < J; ++r) {
+            double s = Mf(r, 0);
+#pragma unroll
+            for (int b = 1; b < NB; ++b) s += Mf(r, 2 * b);
+            Ph[r] = (r % 2 == 0 ? pinf[r] : 0.0) - s;   // P h = (P_inf - M) h
+        }
+        double prior = 0.0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) prior += pinf[2 * b];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            double s = Mf(2 * b, 0);
+#pragma unroll
+            for (int q = 1; q < NB; ++q) s += Mf(2 * b, 2 * q);
+            hMh += s;
+        }
+        const double D = (prior + dv[i]) - hMh;
+        const double iD = 1.0 / D;
+#pragma unroll
+        for (int r = 0; r < J; ++r)
+#pragma unroll
+            for (int c = 0; c < J; ++c) Mf(r, c) = fma(Ph[r] * iD, Ph[c], Mf(r, c));
+        return D;
+    }
+
+    __device__ void elem(int64_t c, Elem& E) const {
+        int64_t s, e;
+        chunk_range(c, B, n, s, e);
+        Mat<J> Mf, Psi, Jacc;
+        mat_zero(Mf);
+#pragma unroll
+        for (int r = 0; r < J; ++r) Mf(r, r) = pinf[r];   // known state: P = 0
+        mat_eye(Psi);
+        mat_zero(Jacc);
+        for (int64_t i = s; i <= e; ++i) {
+            Mat<J> Fm, Phi;
+            dense_F<NB>(F, i, Fm);
+            mat_mul(Fm, Psi, Phi);                          // predicted sensitivity
+            double Ph[J];
+            const double D = step(i, Mf, Ph);
+            const double iD = 1.0 / D;
+            double g[J], hPhi[J];
+#pragma unroll
+            for (int q = 0; q < J; ++q) {
+                double t = Phi(0, q);
+#pragma unroll
+                for (int b = 1; b < NB; ++b) t += Phi(2 * b, q);
+                g[q] = t;
+                hPhi[q] = t;
+            }
+#pragma unroll
+            for (int r = 0; r < J; ++r)
+#pragma unroll
+                for (int q = 0; q < J; ++q) Jacc(r, q) = fma(g[r] * iD, g[q], Jacc(r, q));
+            // Psi = (I - k h^T) Phi, k = P h / D
+#pragma unroll
+            for (int r = 0; r < J; ++r)
+#pragma unroll
+                for (int q = 0; q < J; ++q) Psi(r, q) = fma(-Ph[r] * iD, hPhi[q], Phi(r, q));
+        }
+        E.A = Psi;
+#pragma unroll
+        for (int r = 0; r < J; ++r)
+#pragma unroll
+            for (int q = 0; q < J; ++q) E.C(r, q) = (r == q ? pinf[r] : 0.0) - Mf(r, q);
+        mat_symmetrize(E.C);
+        mat_symmetrize(Jacc);
+        E.Jm = Jacc;
+    }
+
+    __device__ void combine(Elem& ei, const Elem& ej) const {
+        // X = (I + C_i Jm_j)^-1 applied to A_i and C_i
+        Mat<J> M, Y1 = ei.A, Y2 = ei.C;
+        mat_mul(ei.C, ej.Jm, M);
+#pragma unroll
+        for (int r = 0; r < J; ++r) M(r, r) += 1.0;
+        Mat<J>* rhs[2] = {&Y1, &Y2};
+        mat_solve<J, 2>(M, rhs);
+        Mat<J> T, An, Cn, Jn;
+        mat_mul(ej.A, Y1, An);                // A_j X A_i
+        mat_mul(ej.A, Y2, T);                 // A_j X C_i
+        mat_mult(T, ej.A, Cn);                // ... A_j^T
+#pragma unroll
+        for (int i = 0; i < J * J; ++i) Cn.a[i] += ej.C.a[i];
+        mat_symmetrize(Cn);
+        mat_tmul(Y1, ej.Jm, T);               // (X A_i)^T Jm_j
+        mat_mul(T, ei.A, Jn);                 // ... A_i
+#pragma unroll
+        for (int i = 0; i < J * J; ++i) Jn.a[i] += ei.Jm.a[i];
+        mat_symmetrize(Jn);
+        ei.A = An;
+        ei.C = Cn;
+        ei.Jm = Jn;
+    }
+
+    __device__ void apply(const Elem& E, State& st) const {
+        Mat<J> M, Y = st.P;
+        mat_mul(st.P, E.Jm, M);
+#pragma unroll
+        for (int r = 0; r < J; ++r) M(r, r) += 1.0;
+        Mat<J>* rhs[1] = {&Y};
+        mat_solve<J, 1>(M, rhs);              // (I + P Jm)^-1 P
+        Mat<J> T;
+        mat_mul(E.A, Y, T);
+        mat_mult(T, E.A, st.P);
+#pragma unroll
+        for (int i = 0; i < J * J; ++i) st.P.a[i] += E.C.a[i];
+        mat_symmetrize(st.P);
+    }
+
+    __device__ void final(int64_t c, const State& st) const {
+        int64_t s, e;
+        chunk_range(c, B, n, s, e);
+        Mat<J> Mf;
+#pragma unroll
+        for (int r = 0; r < J; ++r)
+#pragma unroll
+            for (int q = 0; q < J; ++q) Mf(r, q) = (r == q ? pinf[r] : 0.0) - st.P(r, q);
+        for (int64_t i = s; i <= e; ++i) {
+            double Ph[J];
+            const double D = step(i, Mf, Ph);
+            if (!(D > 0.0) || !isfinite(D)) {
+                unsigned long long old = atomicMin((unsigned long long*)&dstat[1],
+                                                   (unsigned long long)i);
+                if ((long long)old > i)
+                    atomicExch((unsigned long long*)&dstat[0], 2ull);
+            }
+            const double iD = 1.0 / D;
+#pragma unroll
+            for (int r = 0; r < J; ++r) kg[i * J + r] = Ph[r] * iD;
+            invD[i] = iD;
+            Dpiv[i] = D;
+        }
+    }
+};
+
+// ---------------------------------------------------------- forward solve
+template <int NB>
+struct ForwardOp {
+    static constexpr int J = 2 * NB;
+    struct Elem {
+        Mat<J> Phi;
+        double beta[NRMAX][J];
+    };
+    struct State {
+        double s[NRMAX][J];
+    };
+    const double* F;
+    const double* kg;
+    const double* invD;
+    const double* X;       // column-major n x k
+    const double* y;
+    int64_t n;
+    int k;
+    int B;
+    double* E;             // innovations [n][k+1]
+    double* partial;       // per chunk (k+1)^2 weighted cross products
+
+    __device__ __forceinline__ double xval(int64_t i, int r) const {
+        return r < k ? X[(int64_t)r * n + i] : y[i];
+    }
+    __device__ void init_state(State& st) const {
+#pragma unroll
+        for (int r = 0; r < NRMAX; ++r)
+#pragma unroll
+            for (int q = 0; q < J; ++q) st.s[r][q] = 0.0;
+    }
+    __device__ void elem(int64_t c, Elem& El) const {
+        int64_t s, e;
+        chunk_range(c, B, n, s, e);
+        mat_eye(El.Phi);
+        const int nr = k + 1;
+#pragma unroll
+        for (int r = 0; r < NRMAX; ++r)
+#pragma unroll
+            for (int q = 0; q < J; ++q) El.beta[r][q] = 0.0;
+        for (int64_t i = s; i <= e && i + 1 < n; ++i) {
+            const double* kgi = kg + i * J;
+            const double* f = F + (i + 1) * NB * 4;
+            // Phi <- F (Phi - kg h^T Phi)
+#pragma unroll
+            for (int q = 0; q < J; ++q) {
+                double hp = El.Phi(0, q);
+#pragma unroll
+                for (int b = 1; b < NB; ++b) hp += El.Phi(2 * b, q);
+                double col[J], out[J];
+#pragma unroll
+                for (int r = 0; r < J; ++r) col[r] = fma(-kgi[r], hp, El.Phi(r, q));
+                apply_F<NB>(f, col, out);
+#pragma unroll
+                for (int r = 0; r < J; ++r) El.Phi(r, q) = out[r];
+            }
+            for (int r = 0; r < nr; ++r) {
+                const double innov = xval(i, r) - hdot<NB>(El.beta[r]);
+                double col[J];
+#pragma unroll
+                for (int q = 0; q < J; ++q) col[q] = fma(kgi[q], innov, El.beta[r][q]);
+                apply_F<NB>(f, col, El.beta[r]);
+            }
+        }
+    }
+    __device__ void combine(Elem& ei, const Elem& ej) const {
+        Mat<J> P;
+        mat_mul(ej.Phi, ei.Phi, P);
+        const int nr = k + 1;
+        for (int r = 0; r < nr; ++r) {
+            double out[J];
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                double t = ej.beta[r][a];
+#pragma unroll
+                for (int b = 0; b < J; ++b) t = fma(ej.Phi(a, b), ei.beta[r][b], t);
+                out[a] = t;
+            }
+#pragma unroll
+            for (int a = 0; a < J; ++a) ei.beta[r][a] = out[a];
+        }
+        ei.Phi = P;
+    }
+    __device__ void apply(const Elem& El, State& st) const {
+        const int nr = k + 1;
+        for (int r = 0; r < nr; ++r) {
+            double out[J];
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                double t = El.beta[r][a];
+#pragma unroll
+                for (int b = 0; b < J; ++b) t = fma(El.Phi(a, b), st.s[r][b], t);
+                out[a] = t;
+            }
+#pragma unroll
+            for (int a = 0; a < J; ++a) st.s[r][a] = out[a];
+        }
+    }
+    __device__ void final(int64_t c, const State& st0) const {
+        int64_t s, e;
+        chunk_range(c, B, n, s, e);
+        State st = st0;
+        const int nr = k + 1;
+        double acc[NRMAX][NRMAX];
+        for (int a = 0; a < nr; ++a)
+            for (int b = 0; b < nr; ++b) acc[a][b] = 0.0;
+        for (int64_t i = s; i <= e; ++i) {
+            const double iD = invD[i];
+            double ev[NRMAX];
+            for (int r = 0; r < nr; ++r) {
+                ev[r] = xval(i, r) - hdot<NB>(st.s[r]);
+                E[i * nr + r] = ev[r];
+            }
+            for (int a = 0; a < nr; ++a)
+                for (int b = 0; b <= a; ++b) acc[a][b] = fma(ev[a] * iD, ev[b], acc[a][b]);
+            if (i + 1 < n) {
+                const double* kgi = kg + i * J;
+                const double* f = F + (i + 1) * NB * 4;
+                for (int r = 0; r < nr; ++r) {
+                    double col[J];
+#pragma unroll
+                    for (int q = 0; q < J; ++q) col[q] = fma(kgi[q], ev[r], st.s[r][q]);
+                    apply_F<NB>(f, col, st.s[r]);
+                }
+            }
+        }
+        double* p = partial + c * NRMAX * NRMAX;
+        for (int a = 0; a < nr; ++a)
+            for (int b = 0; b <= a; ++b) {
+                p[a * NRMAX + b] = acc[a][b];
+                p[b * NRMAX + a] = acc[a][b];
+            }
+    }
+};
+
+// --------------------------------------------------------- backward solve
+template <int NB>
+struct BackwardOp {
+    static constexpr int J = 2 * NB;
+    struct Elem {
+        Mat<J> Phi;
+        double beta[NRMAX][J];
+    };
+    struct State {
+        double g[NRMAX][J];
+    };
+    const double* F;
+    const double* kg;
+    const double* U;       // right-hand sides [n][nr]
+    int64_t n;
+    int nr;
+    int k;
+    int B;
+    int64_t n_chunks;
+    double* z0;
+    double* Zt;            // [n][k]
+
+    __device__ void init_state(State& st) const {
+#pragma unroll
+        for (int r = 0; r < NRMAX; ++r)
+#pragma unroll
+            for (int q = 0; q < J; ++q) st.g[r][q] = 0.0;
+    }
+    __device__ void elem(int64_t q, Elem& El) const {
+        int64_t s, e;
+        chunk_range(n_chunks - 1 - q, B, n, s, e);
+        mat_eye(El.Phi);
+#pragma unroll
+        for (int r = 0; r < NRMAX; ++r)
+#pragma unroll
+            for (int a = 0; a < J; ++a) El.beta[r][a] = 0.0;
+        for (int64_t i = e; i >= s && i >= 1; --i) {
+            const double* kgi = kg + i * J;
+            const double* f = F + i * NB * 4;
+            // Phi <- F_i^T (Phi + h (-kg^T Phi))
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                double kp = 0.0;
+#pragma unroll
+                for (int b = 0; b < J; ++b) kp = fma(kgi[b], El.Phi(b, a), kp);
+                double col[J], out[J];
+#pragma unroll
+                for (int b = 0; b < J; ++b) col[b] = El.Phi(b, a) - ((b % 2 == 0) ? kp : 0.0);
+                apply_FT<NB>(f, col, out);
+#pragma unroll
+                for (int b = 0; b < J; ++b) El.Phi(b, a) = out[b];
+            }
+            for (int r = 0; r < nr; ++r) {
+                double v = U[i * nr + r];
+#pragma unroll
+                for (int b = 0; b < J; ++b) v = fma(-kgi[b], El.beta[r][b], v);
+                double col[J];
+#pragma unroll
+                for (int b = 0; b < J; ++b) col[b] = El.beta[r][b] + ((b % 2 == 0) ? v : 0.0);
+                apply_FT<NB>(f, col, El.beta[r]);
+            }
+        }
+    }
+    __device__ void combine(Elem& ei, const Elem& ej) const {
+        Mat<J> P;
+        mat_mul(ej.Phi, ei.Phi, P);
+        for (int r = 0; r < nr; ++r) {
+            double out[J];
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                double t = ej.beta[r][a];
+#pragma unroll
+                for (int b = 0; b < J; ++b) t = fma(ej.Phi(a, b), ei.beta[r][b], t);
+                out[a] = t;
+            }
+#pragma unroll
+            for (int a = 0; a < J; ++a) ei.beta[r][a] = out[a];
+        }
+        ei.Phi = P;
+    }
+    __device__ void apply(const Elem& El, State& st) const {
+        for (int r = 0; r < nr; ++r) {
+            double out[J];
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                double t = El.beta[r][a];
+#pragma unroll
+                for (int b = 0; b < J; ++b) t = fma(El.Phi(a, b), st.g[r][b], t);
+                out[a] = t;
+            }
+#pragma unroll
+            for (int a = 0; a < J; ++a) st.g[r][a] = out[a];
+        }
+    }
+    __device__ void final(int64_t q, const State& st0) const {
+        int64_t s, e;
+        chunk_range(n_chunks - 1 - q, B, n, s, e);
+        State st = st0;
+        for (int64_t i = e; i >= s; --i) {
+            const double* kgi = kg + i * J;
+            const double* f = F + i * NB * 4;
+            for (int r = 0; r < nr; ++r) {
+                double v = U[i * nr + r];
+#pragma unroll
+                for (int b = 0; b < J; ++b) v = fma(-kgi[b], st.g[r][b], v);
+                if (r == 0) z0[i] = v; else Zt[i * k + (r - 1)] = v;
+                if (i >= 1) {
+                    double col[J];
+#pragma unroll
+                    for (int b = 0; b < J; ++b) col[b] = st.g[r][b] + ((b % 2 == 0) ? v : 0.0);
+                    apply_FT<NB>(f, col, st.g[r]);
+                }
+            }
+        }
+    }
+};
+
+// ------------------------------------------------ future information G
+template <int NB>
+struct FutureOp {
+    static constexpr int J = 2 * NB;
+    static constexpr int JJ = J * (J + 1) / 2;
+    struct Elem {
+        Mat<J> Psi, Gam;
+    };
+    struct State {
+        Mat<J> G;
+    };
+    const double* F;
+    const double* kg;
+    const double* invD;
+    int64_t n;
+    int B;
+    int64_t n_chunks;
+    double* Gout;          // packed upper [n][JJ]
+
+    // A_{i+1} = F_{i+1} (I - kg_i h^T) as a dense matrix
+    __device__ __forceinline__ void closed_loop(int64_t i, Mat<J>& A) const {
+        const double* f = F + (i + 1) * NB * 4;
+        const double* kgi = kg + i * J;
+        double fk[J];
+        apply_F<NB>(f, kgi, fk);
+        dense_F<NB>(F, i + 1, A);
+#pragma unroll
+        for (int r = 0; r < J; ++r)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) A(r, 2 * b) -= fk[r];
+    }
+    __device__ void init_state(State& st) const { mat_zero(st.G); }
+    __device__ void elem(int64_t q, Elem& El) const {
+        int64_t s, e;
+        chunk_range(n_chunks - 1 - q, B, n, s, e);
+        mat_eye(El.Psi);
+        mat_zero(El.Gam);
+        for (int64_t i = e; i >= s; --i) {
+            if (i + 1 < n) {
+                Mat<J> A, T;
+                closed_loop(i, A);
+                mat_mul(El.Psi, A, T);
+                El.Psi = T;
+                mat_mul(El.Gam, A, T);
+                mat_tmul(A, T, El.Gam);
+            }
+            const double iD = invD[i];
+#pragma unroll
+            for (int r = 0; r < J; r += 2)
+#pragma unroll
+                for (int c = 0; c < J; c += 2) El.Gam(r, c) += iD;
+        }
+        mat_symmetrize(El.Gam);
+    }
+    __device__ void combine(Elem& ei, const Elem& ej) const {
+        // ei: later samples (earlier in scan order), ej: earlier samples
+        Mat<J> P, T, Gn;
+        mat_mul(ei.Psi, ej.Psi, P);
+        mat_mul(ei.Gam, ej.Psi, T);
+        mat_tmul(ej.Psi, T, Gn);
+#pragma unroll
+        for (int i = 0; i < J * J; ++i) Gn.a[i] += ej.Gam.a[i];
+        mat_symmetrize(Gn);
+        ei.Psi = P;
+        ei.Gam = Gn;
+    }
+    __device__ void apply(const Elem& El, State& st) const {
+        Mat<J> T, Gn;
+        mat_mul(st.G, El.Psi, T);
+        mat_tmul(El.Psi, T, Gn);
+#pragma unroll
+        for (int i = 0; i < J * J; ++i) Gn.a[i] += El.Gam.a[i];
+        mat_symmetrize(Gn);
+        st.G = Gn;
+    }
+    __device__ void final(int64_t q, const State& st0) const {
+        int64_t s, e;
+        chunk_range(n_chunks - 1 - q, B, n, s, e);
+        Mat<J> G = st0.G;
+        for (int64_t i = e; i >= s; --i) {
+            if (i + 1 < n) {
+                Mat<J> A, T;
+                closed_loop(i, A);
+                mat_mul(G, A, T);
+                mat_tmul(A, T, G);
+            } else {
+                mat_zero(G);
+            }
+            const double iD = invD[i];
+#pragma unroll
+            for (int r = 0; r < J; r += 2)
+#pragma unroll
+                for (int c = 0; c < J; c += 2) G(r, c) += iD;
+            mat_symmetrize(G);
+            double* Gi = Gout + i * JJ;
+#pragma unroll
+            for (int r = 0; r < J; ++r)
+#pragma unroll
+                for (int c = r; c < J; ++c) Gi[pk(r, c, J)] = G(r, c);
+        }
+    }
+};
+
+}  // namespace nu

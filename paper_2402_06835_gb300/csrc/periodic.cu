@@ -300,13 +300,15 @@ k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
     const int64_t n_phi = (int64_t)ceil(P / g.dt);
     const int64_t n_cells = n_phi * n_D;
     const double R = P * g.inv_dt;
+    const SlotWalk swp = slot_walk(1.0 / (double)n_phi, R);   // per-phase slot step
+    const SlotWalk swk = slot_walk(0.0, R);                   // per-epoch slot step
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
         const int d = (int)(cell / n_phi);
         const int64_t j = cell - (int64_t)d * n_phi;
         const double phi = (double)j / (double)n_phi;
         const Node4<T>* nd = nodes + (int64_t)d * g.n_t0;
-        const SlotWalk sw = slot_walk(phi, R);
+        const SlotWalk sw{(unsigned long long)j * swp.u0, swk.ustep};
         KSum<T> s_inv, s_d, s_l;
         s_inv.init();
         s_d.init();
@@ -461,15 +463,19 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
     const unsigned long long ulast = (unsigned long long)llrint(ulast_d);
     const unsigned long long ustep =
         R * SCALE < 4.0e18 ? (unsigned long long)llrint(R * SCALE) : 4000000000000000000ull;
+    // phase j starts at j * (R / n_phi) slots; per-cell work stays integer
+    const unsigned long long uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
+    const float inv_ustep = 1.0f / (float)ustep;
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
         const int d = (int)(cell / n_phi);
         const int64_t j = cell - (int64_t)d * n_phi;
-        const double u0_d = ((double)j / (double)n_phi) * R * SCALE;
-        if (!(u0_d <= ulast_d)) continue;
-        const unsigned long long u0 = (unsigned long long)llrint(u0_d);
+        const unsigned long long u0 = (unsigned long long)j * uph;
         if (u0 > ulast) continue;
-        const int64_t kmax = (int64_t)((ulast - u0) / ustep) + 1;
+        int64_t kk = (int64_t)((float)(ulast - u0) * inv_ustep);
+        while (kk > 0 && u0 + (unsigned long long)kk * ustep > ulast) --kk;
+        while (u0 + (unsigned long long)(kk + 1) * ustep <= ulast) ++kk;
+        const int64_t kmax = kk + 1;
         const Node4<float>* rd = rec + (int64_t)d * n_slots;
         SlotPass1 p1;
         p1.init();
