@@ -284,6 +284,66 @@ __device__ __forceinline__ int64_t guess_at(const FoldGeom& g, unsigned long lon
 }
 
 template <typename T>
+struct ExactAcc {
+    KSum<T> s_inv, s_d, s_l;
+    int K;
+    __device__ __forceinline__ void init() {
+        s_inv.init();
+        s_d.init();
+        s_l.init();
+        K = 0;
+    }
+    __device__ __forceinline__ void add(T dk, T sk2, T lk) {
+        const T iv = rcp_t<T>(sk2);
+        s_inv.add(iv);
+        s_d.add(dk * iv);
+        s_l.add(lk);
+        ++K;
+    }
+};
+
+// second sum of Eq. result: ln s_k^2 - ln(sigma^2 + s_k^2) accumulated as the
+// log of a product of ratios in [1/2, 1] (renormalised), plus
+// (Delta_k - Delta)^2 / (s_k^2 + sigma^2)
+template <typename T>
+struct ExactPen {
+    KSum<T> quad;
+    double prod;
+    int expo, cnt;
+    float lsum;
+    T s2, Dl;
+    __device__ __forceinline__ void init(T s2_, T Dl_) {
+        quad.init();
+        prod = 1.0;
+        expo = 0;
+        cnt = 0;
+        lsum = 0.f;
+        s2 = s2_;
+        Dl = Dl_;
+    }
+    __device__ __forceinline__ void add(T dk, T sk2) {
+        const T den = sk2 + s2;
+        const T iden = rcp_t<T>(den);
+        const T r = dk - Dl;
+        quad.add(r * r * iden);
+        if (sizeof(T) == 8) {
+            prod *= (double)(sk2 * iden);
+            if ((++cnt & 255) == 0) {
+                const int e = ((__double2hiint(prod) >> 20) & 0x7ff) - 1023;
+                prod = __hiloint2double(__double2hiint(prod) - (e << 20), __double2loint(prod));
+                expo += e;
+            }
+        } else {
+            lsum += lg2_32((float)(sk2 * iden));
+        }
+    }
+    __device__ __forceinline__ double logsum() const {
+        if (sizeof(T) == 8) return log(prod) + (double)expo * 0.69314718055994530942;
+        return (double)lsum * 0.69314718055994530942;
+    }
+};
+
+template <typename T, int KC>
 __global__ void __launch_bounds__(256)
 k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
              const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
@@ -302,73 +362,86 @@ k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
     const double R = P * g.inv_dt;
     const SlotWalk swp = slot_walk(1.0 / (double)n_phi, R);   // per-phase slot step
     const SlotWalk swk = slot_walk(0.0, R);                   // per-epoch slot step
-    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    const double SCALE = 1099511627776.0;
+    const double ulast_d = (g.t_last - g.t_ref) * g.inv_dt * SCALE;
+    const unsigned long long ulast =
+        ulast_d < 4.0e18 ? (unsigned long long)llrint(ulast_d) : 4000000000000000000ull;
+    const float inv_ustep = 1.0f / (float)swk.ustep;
+    double bl = -INFINITY;
+    long long bc = LLONG_MAX;
+    T bD = T(NAN), bs2 = T(NAN);
     for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
         const int d = (int)(cell / n_phi);
         const int64_t j = cell - (int64_t)d * n_phi;
         const double phi = (double)j / (double)n_phi;
         const Node4<T>* nd = nodes + (int64_t)d * g.n_t0;
-        const SlotWalk sw{(unsigned long long)j * swp.u0, swk.ustep};
-        KSum<T> s_inv, s_d, s_l;
-        s_inv.init();
-        s_d.init();
-        s_l.init();
-        int K = 0;
-        unsigned long long u = sw.u0;
-        for (int64_t k = 0;; ++k, u += sw.ustep) {
-            const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
-            if (Tk > g.t_last) break;
-            T dk, sk2, lk;
-            int64_t i = guess_at(g, u);
-            if (!event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) continue;
-            const T iv = rcp_t<T>(sk2);
-            s_inv.add(iv);
-            s_d.add(dk * iv);
-            s_l.add(lk);
-            ++K;
-        }
-        if (K == 0) continue;
-        const T s2 = T(1) / s_inv.s;
-        const T Dl = s2 * s_d.s;
-        // second sum of Eq. result: ln s_k^2 - ln(sigma^2 + s_k^2) accumulated
-        // as the log of a product of ratios in [1/2, 1] (renormalised), plus
-        // (Delta_k - Delta)^2 / (s_k^2 + sigma^2)
-        KSum<T> quad;
-        quad.init();
-        double prod = 1.0;
-        int expo = 0, cnt = 0;
-        float lsum = 0.f;
-        u = sw.u0;
-        for (int64_t k = 0;; ++k, u += sw.ustep) {
-            const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
-            if (Tk > g.t_last) break;
-            T dk, sk2, lk;
-            int64_t i = guess_at(g, u);
-            if (!event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) continue;
-            const T den = sk2 + s2;
-            const T iden = rcp_t<T>(den);
-            const T r = dk - Dl;
-            quad.add(r * r * iden);
-            if (sizeof(T) == 8) {
-                prod *= (double)(sk2 * iden);
-                if ((++cnt & 255) == 0) {
-                    const int e = ((__double2hiint(prod) >> 20) & 0x7ff) - 1023;
-                    prod = __hiloint2double(__double2hiint(prod) - (e << 20),
-                                            __double2loint(prod));
-                    expo += e;
+        const unsigned long long u0 = (unsigned long long)j * swp.u0;
+        // number of epochs with T <= t_last: integer estimate, then the exact
+        // FP64 comparisons of the definition
+        int64_t kk = u0 > ulast ? 0 : (int64_t)((float)(ulast - u0) * inv_ustep) + 1;
+        while (kk > 0 &&
+               __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)(kk - 1)), P)) > g.t_last)
+            --kk;
+        while (__dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)kk), P)) <= g.t_last) ++kk;
+        const int64_t kmax = kk;
+        ExactAcc<T> a1;
+        a1.init();
+        ExactPen<T> a2;
+        if (kmax <= KC) {
+            T cd[KC > 0 ? KC : 1], cs[KC > 0 ? KC : 1];
+            bool ok[KC > 0 ? KC : 1];
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                ok[k] = false;
+                if (k < kmax) {
+                    const double Tk =
+                        __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
+                    int64_t i = guess_at(g, u0 + (unsigned long long)k * swk.ustep);
+                    T dk, sk2, lk;
+                    ok[k] = event_exact<T>(g, nd, Tk, i, dk, sk2, lk);
+                    if (ok[k]) {
+                        cd[k] = dk;
+                        cs[k] = sk2;
+                        a1.add(dk, sk2, lk);
+                    }
                 }
-            } else {
-                lsum += lg2_32((float)(sk2 * iden));
+            }
+            if (a1.K == 0) continue;
+            const T s2 = T(1) / a1.s_inv.s;
+            a2.init(s2, s2 * a1.s_d.s);
+#pragma unroll
+            for (int k = 0; k < KC; ++k)
+                if (ok[k]) a2.add(cd[k], cs[k]);
+        } else {
+            unsigned long long u = u0;
+            for (int64_t k = 0; k < kmax; ++k, u += swk.ustep) {
+                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
+                T dk, sk2, lk;
+                int64_t i = guess_at(g, u);
+                if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a1.add(dk, sk2, lk);
+            }
+            if (a1.K == 0) continue;
+            const T s2 = T(1) / a1.s_inv.s;
+            a2.init(s2, s2 * a1.s_d.s);
+            u = u0;
+            for (int64_t k = 0; k < kmax; ++k, u += swk.ustep) {
+                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
+                T dk, sk2, lk;
+                int64_t i = guess_at(g, u);
+                if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a2.add(dk, sk2);
             }
         }
-        double logsum;
-        if (sizeof(T) == 8) logsum = log(prod) + (double)expo * 0.69314718055994530942;
-        else logsum = (double)lsum * 0.69314718055994530942;
-        const double lnp = (double)s_l.s - 0.5 * (logsum + (double)quad.s);
+        const double lnp = (double)a1.s_l.s - 0.5 * (a2.logsum() + (double)a2.quad.s);
         if (!(lnp == lnp)) continue;   // NaN never selected
-        Best cand{lnp, (long long)cell, (double)Dl, sqrt((double)s2)};
-        if (better(cand, best)) best = cand;
+        if (lnp > bl || (lnp == bl && cell < bc)) {
+            bl = lnp;
+            bc = cell;
+            bD = a2.Dl;
+            bs2 = a2.s2;
+        }
     }
+    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    if (bc != LLONG_MAX) best = Best{bl, bc, (double)bD, sqrt((double)bs2)};
     const Best b = block_argmax(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, g.t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
@@ -467,6 +540,8 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
     const unsigned long long uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
     const float inv_ustep = 1.0f / (float)ustep;
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    float bl = -INFINITY, bD = NAN, bs2 = NAN;
+    long long bc = LLONG_MAX;
     for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
         const int d = (int)(cell / n_phi);
         const int64_t j = cell - (int64_t)d * n_phi;
@@ -510,12 +585,18 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
                 p2.add(e.d, e.s);
             }
         }
-        const double lnp = (double)p1.s_l.s -
-                           0.5 * ((double)p2.lsum * 0.69314718055994530942 + (double)p2.quad.s);
+        // per-cell bookkeeping stays in FP32 (FP64 here would cost more than
+        // the epochs of a long period)
+        const float lnp = p1.s_l.s - 0.5f * (p2.lsum * 0.693147180559945f + p2.quad.s);
         if (!(lnp == lnp)) continue;
-        Best cand{lnp, (long long)cell, (double)p2.Dl, sqrt((double)p2.s2)};
-        if (better(cand, best)) best = cand;
+        if (lnp > bl || (lnp == bl && cell < bc)) {
+            bl = lnp;
+            bc = cell;
+            bD = p2.Dl;
+            bs2 = p2.s2;
+        }
     }
+    if (bc != LLONG_MAX) best = Best{(double)bl, (long long)bc, (double)bD, sqrt((double)bs2)};
     const Best b = block_argmax(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
@@ -636,14 +717,14 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
             k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
                 t0s_dev, n_t0, n_D, g.gap_max, (Node4<double>*)nodes);
-            k_fold_exact<double><<<(unsigned)n_P, 256, 0, st>>>(
+            k_fold_exact<double, 8><<<(unsigned)n_P, 256, 0, st>>>(
                 g, (const Node4<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
                 t0s_dev, n_t0, n_D, g.gap_max, (Node4<float>*)nodes);
-            k_fold_exact<float><<<(unsigned)n_P, 256, 0, st>>>(
+            k_fold_exact<float, 8><<<(unsigned)n_P, 256, 0, st>>>(
                 g, (const Node4<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         }
