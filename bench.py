@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--case", default=None, choices=["fold_small"],
+                    help="profiling case: one periodic search per precision on a "
+                         "sector-shaped grid with 300 periods (for ncu captures)")
     return ap.parse_args()
 
 
@@ -201,6 +205,39 @@ def run_e2e(pipe, api, torch, lc, steps):
     return ms, bi, bo
 
 
+# ------------------------------------------------------------ batch (C4)
+def run_batch(api, torch, w, precision, steps, warmup, flush):
+    """nu_batch_search over all curves of a survey workload; one step = one
+    batched call (factor, linear search and fold of every curve)."""
+    items = [(torch.as_tensor(lc.t, device="cuda"), torch.as_tensor(lc.y, device="cuda"),
+              torch.as_tensor(lc.diag_var, device="cuda"), lc.terms) for lc in w.curves]
+    periods = torch.as_tensor(w.periods, dtype=torch.float64, device="cuda")
+    dt = synth.CADENCE_DAYS
+    for _ in range(warmup):
+        api.nu_batch_search(items, w.durations, periods, k=2, precision=precision,
+                            phase_step=dt)
+    torch.cuda.synchronize()
+    times = []
+    for k in range(steps):
+        flush.fill_(k + 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = api.nu_batch_search(items, w.durations, periods, k=2, precision=precision,
+                                phase_step=dt)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    n_templates = sum(len(lc.t) for lc in w.curves) * len(w.durations)
+    ms = float(np.mean(times))
+    return {"workload": f"{w.name}: {len(w.curves)} curves, "
+                        f"{sum(len(lc.t) for lc in w.curves)} samples, "
+                        f"{len(w.durations)} durations, {len(w.periods)} periods",
+            "precision": precision, "ms_per_step": ms,
+            "value": n_templates / (ms / 1e3), "unit": "(t0,D) fits/s",
+            "period_trials_per_s": len(w.curves) * len(w.periods) / (ms / 1e3),
+            "failed_curves": int(sum(1 for s_ in r["status"] if s_ != 0))}
+
+
 # ---------------------------------------------------------------- oracle
 def oracle_sample(lc, Ds, periods, n_templates=256, n_periods=8, seed=0):
     """Time the oracle on a bounded sample and extrapolate to one full step."""
@@ -239,8 +276,33 @@ def blas_threads():
 
 
 # ---------------------------------------------------------------- main
+def profile_case(args):
+    """Small cases for ncu: one nu_periodic_search per precision on the
+    sector grid (19 440 epochs with the mid-sector gap, 10 durations), seeded
+    random single-event values, 300 periods over 0.2-13.5 d."""
+    import torch
+    from paper_2402_06835_gb300 import api
+    w = synth.sector_19440()
+    t = w.curves[0].t
+    n = len(t)
+    rng = np.random.default_rng(5)
+    g = dict(depth=rng.normal(0, 5e-4, (10, n)), var=rng.uniform(2e-8, 9e-8, (10, n)),
+             dlnl=rng.uniform(0, 6, (10, n)))
+    per = torch.tensor(np.linspace(0.2, 13.5, 300), dtype=torch.float64, device="cuda")
+    tt = torch.tensor(t, device="cuda")
+    dt = float(np.median(np.diff(t)))
+    for prec, dty in (("mixed", torch.float32), ("fp64", torch.float64)):
+        arr = [torch.tensor(g[k], dtype=dty, device="cuda") for k in ("depth", "var", "dlnl")]
+        r = api.nu_periodic_search(tt, w.durations, *arr, per, precision=prec, phase_step=dt)
+        torch.cuda.synchronize()
+        print(prec, float(r["Q"].max()))
+
+
 def main():
     args = parse()
+    if args.case == "fold_small":
+        profile_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -287,6 +349,28 @@ def main():
     from paper_2402_06835_gb300 import api
 
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if len(w.curves) > 1:
+        # survey workload: the batched call is the step
+        b = run_batch(api, torch, w, args.precision, args.steps, args.warmup, flush)
+        ms = b["ms_per_step"]
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        nt = sum(len(lc.t) for lc in w.curves) * len(w.durations)
+        out = {"metric": METRIC, "value": world * nt / (ms / 1e3), "unit": "(t0,D) fits/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+               "data": "synthetic", "config": {"workload": b["workload"],
+                                               "precision": args.precision,
+                                               "l2": "flushed (512 MB write) between timed steps"},
+               "period_trials_per_s": world * b["period_trials_per_s"], "batch": b}
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     pipe = Pipeline(api, torch, lc, w.durations, w.periods, args.precision, dev)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
@@ -360,6 +444,13 @@ def main():
                                           "periodic_search": float(sms[2])}}
         except Exception as exc:
             out["mixed"] = {"error": repr(exc)}
+
+    if not args.no_batch and args.precision == "fp64":
+        try:
+            out["batch_mixed"] = run_batch(api, torch, synth.survey_438(), "mixed",
+                                           max(1, min(args.steps, 2)), 1, flush)
+        except Exception as exc:
+            out["batch_mixed"] = {"error": repr(exc)}
 
     if world > 1:
         torch.distributed.barrier()

@@ -58,6 +58,7 @@ def _load():
                                        P, P, P, P, P, P]
     lib.nu_batch_search.argtypes = [I, P, P, P, P, ctypes.POINTER(nu_term), P, I, P, I,
                                     P, I64, D, I, P, P, P, P, P, P, P, P]
+    lib.nu_batch_search.restype = I
     lib.nu_last_error.restype = ctypes.c_char_p
     lib.nu_version.restype = ctypes.c_char_p
     lib.nu_launch_count.restype = ctypes.c_uint64
@@ -197,7 +198,7 @@ def nu_linear_search(factor, t0s, Ds, template="box", ingress_frac=0.1,
 
 
 def nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision="fp64",
-                       phase_step=0.0, gap_factor=1.5, stream=None):
+                       phase_step=0.0, gap_factor=1.5, stream=None, _entry=None):
     """Periodic search (Sect. 2.3-2.4).  Returns a dict of (n_P,) tensors."""
     t0s = _dev(t0s, "t0s")
     periods = _dev(periods, "periods")
@@ -213,12 +214,58 @@ def nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision="fp64",
     res["D_idx"] = torch.empty(n_P, dtype=torch.int32, device=dev)
     Ds_l = [float(d) for d in (Ds.tolist() if hasattr(Ds, "tolist") else Ds)]
     Ds_arr = (ctypes.c_double * max(1, len(Ds_l)))(*Ds_l)
-    st = LIB.nu_periodic_search(_p(t0s), t0s.numel(), Ds_arr, n_D, _p(depth), _p(var),
+    fn = _entry or LIB.nu_periodic_search
+    st = fn(_p(t0s), t0s.numel(), Ds_arr, n_D, _p(depth), _p(var),
                                 _p(dlnl), prec, _p(periods), n_P, float(phase_step),
                                 float(gap_factor), _stream_ptr(stream), _p(res["Q"]),
                                 _p(res["T0"]), _p(res["D_idx"]), _p(res["depth"]),
                                 _p(res["sigma"]), _p(res["lnP"]))
     _check(st, "nu_periodic_search")
+    return res
+
+
+def nu_batch_search(curves, Ds, periods, k=2, precision="fp64", phase_step=None,
+                    stream=None):
+    """Batched search (factor, box linear search with t0 = samples, periodic
+    search) of several light curves in one graph launch.
+
+    curves: list of (t, y, diag_var, terms); arrays may be numpy or CUDA
+    tensors (float64).  The design matrix of every curve is [1, t][:k].
+    phase_step: shared phase step (default: the median spacing of the first
+    curve).  Returns a dict of (n_lc, n_P) tensors and 'status' (list of
+    per-curve factor statuses, 0 = OK).
+    """
+    dev = torch.device("cuda", torch.cuda.current_device())
+    as_dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev).reshape(-1)
+    ts = [as_dev(c[0]) for c in curves]
+    t = torch.cat(ts).contiguous()
+    y = torch.cat([as_dev(c[1]) for c in curves]).contiguous()
+    dv = torch.cat([as_dev(c[2]) for c in curves]).contiguous()
+    n_lc = len(curves)
+    offs = [0]
+    for a in ts:
+        offs.append(offs[-1] + a.numel())
+    offsets = (ctypes.c_int64 * (n_lc + 1))(*offs)
+    flat = [tm for c in curves for tm in c[3]]
+    terms = make_terms(flat)
+    counts = (ctypes.c_int * n_lc)(*[len(c[3]) for c in curves])
+    Ds_l = [float(d) for d in (Ds.tolist() if hasattr(Ds, "tolist") else Ds)]
+    Ds_arr = (ctypes.c_double * len(Ds_l))(*Ds_l)
+    periods = as_dev(periods).contiguous()
+    n_P = periods.numel()
+    if phase_step is None:
+        phase_step = float(torch.median(ts[0][1:] - ts[0][:-1]).item())
+    res = {name: torch.empty((n_lc, n_P), dtype=torch.float64, device=dev)
+           for name in ("Q", "T0", "depth", "sigma", "lnP")}
+    res["D_idx"] = torch.empty((n_lc, n_P), dtype=torch.int32, device=dev)
+    status = (ctypes.c_int * n_lc)()
+    st = LIB.nu_batch_search(n_lc, offsets, _p(t), _p(y), _p(dv), terms, counts, int(k),
+                             Ds_arr, len(Ds_l), _p(periods), n_P, float(phase_step),
+                             _PREC[precision], _stream_ptr(stream), _p(res["Q"]),
+                             _p(res["T0"]), _p(res["D_idx"]), _p(res["depth"]),
+                             _p(res["sigma"]), _p(res["lnP"]), status)
+    _check(st, "nu_batch_search")
+    res["status"] = list(status)
     return res
 
 

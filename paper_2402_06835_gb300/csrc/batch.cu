@@ -1,0 +1,324 @@
+// nu_batch_search: a survey of light curves of uneven length in one graph.
+//
+// The curves are packed back to back.  Every stage treats them as segments
+// of one problem: the factor scans run over the chunks of all curves (a
+// chunk never crosses a curve), the linear search covers every curve's
+// (D, t0) grid with t0 = its samples, and the fold is a persistent kernel
+// that takes (curve, period) work items from a device counter, which
+// balances curves of different spans.  Host work (validation, layout, a
+// regularity test of each curve's cadence, uploads of the small tables)
+// happens before capture; the kernels are captured into one CUDA graph and
+// launched once.  The fold's launch shape (threads per block, resident
+// blocks per SM) is chosen by a small autotuner the first time a
+// configuration is seen: the candidates are timed on a slice of the batch
+// and the fastest is cached for the process.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "factor_core.cuh"
+#include "fold.cuh"
+#include "nu_internal.cuh"
+
+namespace nu {
+
+__global__ void k_init_dstat(long long* dstat, const int64_t* __restrict__ s_off, int n_seg) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_seg) return;
+    dstat[2 * g] = 0;
+    dstat[2 * g + 1] = s_off[g + 1] - s_off[g];
+}
+
+__global__ void k_gather_ends(const double* __restrict__ t, const int64_t* __restrict__ s_off,
+                              int n_seg, double* __restrict__ ends) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_seg) return;
+    ends[2 * g] = t[s_off[g]];
+    ends[2 * g + 1] = t[s_off[g + 1] - 1];
+}
+
+struct TuneKey {
+    int nb, k, prec, n_D;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nb, k, prec, n_D) < std::tie(o.nb, o.k, o.prec, o.n_D);
+    }
+};
+struct TuneVal {
+    int blocks_per_sm, threads;
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+}  // namespace nu
+
+using namespace nu;
+
+extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
+                                     const double* t_dev, const double* y_dev,
+                                     const double* diag_var_dev, const nu_term* terms_host,
+                                     const int* n_terms_host, int k, const double* Ds_host,
+                                     int n_D, const double* periods_dev, int64_t n_P,
+                                     double phase_step, nu_precision prec, void* stream,
+                                     double* Q_dev, double* T0_dev, int32_t* D_idx_dev,
+                                     double* depth_out_dev, double* sigma_out_dev,
+                                     double* lnP_dev, int* status_host) {
+    // ------------------------------------------------------------ checks
+    if (n_lc < 1 || !offsets_host || !t_dev || !y_dev || !diag_var_dev || !terms_host ||
+        !n_terms_host || !Ds_host || !periods_dev || !Q_dev || !T0_dev || !D_idx_dev ||
+        !depth_out_dev || !sigma_out_dev || !lnP_dev || !status_host)
+        return fail(NU_EINVAL, "nu_batch_search: null argument or n_lc < 1");
+    if (k < 0 || k > 2) return fail(NU_EINVAL, "nu_batch_search: k must be 0, 1 or 2");
+    if (n_D < 1 || n_P < 1) return fail(NU_EINVAL, "nu_batch_search: empty grid");
+    if (!(phase_step > 0.0) || !std::isfinite(phase_step))
+        return fail(NU_EINVAL, "nu_batch_search: phase_step must be > 0");
+    if (prec != NU_FP64 && prec != NU_MIXED)
+        return fail(NU_EINVAL, "nu_batch_search: unknown precision");
+    if (offsets_host[0] != 0) return fail(NU_EINVAL, "nu_batch_search: offsets[0] must be 0");
+    for (int g = 0; g < n_lc; ++g)
+        if (offsets_host[g + 1] - offsets_host[g] < 2)
+            return fail(NU_EINVAL, "nu_batch_search: curve %d has fewer than 2 samples", g);
+    for (int j = 0; j < n_D; ++j)
+        if (!(Ds_host[j] > 0.0) || !std::isfinite(Ds_host[j]))
+            return fail(NU_EINVAL, "nu_batch_search: durations must be finite and > 0");
+    std::vector<Blocks> blocks(n_lc);
+    {
+        int tb = 0;
+        for (int g = 0; g < n_lc; ++g) {
+            const nu_status s = expand_terms(terms_host + tb, n_terms_host[g], &blocks[g]);
+            if (s != NU_OK) return s;
+            tb += n_terms_host[g];
+            if (blocks[g].nb != blocks[0].nb)
+                return fail(NU_EINVAL, "nu_batch_search: every curve must have the same "
+                                       "state dimension (curve %d differs)", g);
+        }
+    }
+    const int nb = blocks[0].nb, J = 2 * nb, JJ = J * (J + 1) / 2;
+    const bool fp64 = prec == NU_FP64;
+    const double gap_factor = 1.5;
+    const int64_t N = offsets_host[n_lc];
+    std::vector<int64_t> n_per(n_lc);
+    for (int g = 0; g < n_lc; ++g) n_per[g] = offsets_host[g + 1] - offsets_host[g];
+    const FactorPlan plan = plan_factor(n_per.data(), blocks.data(), n_lc, k);
+    cudaStream_t st = (cudaStream_t)stream;
+    pool_keep_memory();
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    // ------------------------------------------------------- factor memory
+    const size_t esz = fp64 ? 8 : 4;
+    size_t off = 0;
+    const size_t o_F = off;     off += al((size_t)N * nb * 4 * 8);
+    const size_t o_kg = off;    off += al((size_t)N * J * 8);
+    const size_t o_iD = off;    off += al((size_t)N * 8);
+    const size_t o_G = off;     off += al((size_t)N * JJ * 8);
+    const size_t o_z0 = off;    off += al((size_t)N * 8);
+    const size_t o_Zt = off;    off += al((size_t)N * (k > 0 ? k : 1) * 8);
+    const size_t o_work = off;  off += al((size_t)N * (k + 1) * 8);
+    const size_t o_scal = off;  off += al((size_t)n_lc * 4 * 8);
+    const size_t o_dstat = off; off += al((size_t)n_lc * 2 * 8);
+    const size_t o_f32 = off;   off += fp64 ? 0 : al((size_t)N * (nb * 4 + J + 1 + JJ + 1 + k) * 4 + 1024);
+    const size_t o_ws = off;    off += al(plan.bytes);
+    const size_t o_lin = off;   off += al((size_t)N * n_D * esz) * 3;
+    const size_t o_ends = off;  off += al((size_t)n_lc * 2 * 8);
+    const size_t o_irr = off;   off += al((size_t)n_lc * 4);
+    const size_t o_Ds = off;    off += al((size_t)n_D * 8);
+    const size_t o_ctr = off;   off += 256;
+    const size_t base_bytes = off;
+    char* mem = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&mem, base_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "nu_batch_search: cudaMallocAsync");
+    char* fold_mem = nullptr;
+    auto cleanup = [&]() {
+        if (fold_mem) cudaFreeAsync(fold_mem, st);
+        cudaFreeAsync(mem, st);
+    };
+    FactorBuffers fb{t_dev,
+                     (double*)(mem + o_F), (double*)(mem + o_kg), (double*)(mem + o_iD),
+                     (double*)(mem + o_G), (double*)(mem + o_z0), (double*)(mem + o_Zt),
+                     (double*)(mem + o_work), (double*)(mem + o_scal),
+                     (long long*)(mem + o_dstat), nullptr, nullptr, nullptr, nullptr,
+                     nullptr, nullptr};
+    if (!fp64) {
+        float* q = (float*)(mem + o_f32);
+        fb.F32 = q;    q += N * nb * 4;
+        fb.kg32 = q;   q += N * J;
+        fb.invD32 = q; q += N;
+        fb.G32 = q;    q += N * JJ;
+        fb.z032 = q;   q += N;
+        fb.Zt32 = q;
+    }
+    char* ws = mem + o_ws;
+    void* lin_d = mem + o_lin;
+    void* lin_v = mem + o_lin + al((size_t)N * n_D * esz);
+    void* lin_l = mem + o_lin + 2 * al((size_t)N * n_D * esz);
+    const int64_t* s_off_dev = (const int64_t*)(ws + plan.off_s_off);
+    // ------------------------------------------------------ pre-capture work
+    nu_status s = upload_factor_plan(plan, ws, st);
+    if (s != NU_OK) {
+        cleanup();
+        return s;
+    }
+    std::vector<double> ends(2 * (size_t)n_lc);
+    std::vector<int> irregular(n_lc, 0);
+    int launched = 0;
+    k_gather_ends<<<div_up(n_lc, 128), 128, 0, st>>>(t_dev, s_off_dev, n_lc,
+                                                     (double*)(mem + o_ends));
+    ++launched;
+    e = cudaMemsetAsync(mem + o_irr, 0, (size_t)n_lc * 4, st);
+    if (!fp64 && e == cudaSuccess)
+        launched += launch_slots_test(t_dev, s_off_dev, n_lc, N, phase_step,
+                                      (int*)(mem + o_irr), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ends.data(), mem + o_ends, ends.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(irregular.data(), mem + o_irr, (size_t)n_lc * 4,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mem + o_Ds, Ds_host, (size_t)n_D * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    count_launches(launched);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "nu_batch_search: setup");
+    }
+    std::vector<double> t_first(n_lc), t_last(n_lc);
+    for (int g = 0; g < n_lc; ++g) {
+        t_first[g] = ends[2 * g];
+        t_last[g] = ends[2 * g + 1];
+        if (!(t_last[g] >= t_first[g]) || (t_last[g] - t_first[g]) / phase_step > 1.0e9) {
+            cleanup();
+            return fail(NU_EINVAL, "nu_batch_search: curve %d: times unsorted or span too "
+                                   "long for the phase step", g);
+        }
+    }
+    FoldBatch fbat;
+    plan_fold_batch(plan.s_off, t_first, t_last, irregular, fp64, phase_step, gap_factor, n_D,
+                    fbat);
+    size_t foff = 0;
+    const size_t f_segs = foff;  foff += al(fbat.segs.size() * sizeof(FoldSeg));
+    const size_t f_nodes = foff; foff += fbat.any_exact ? al((size_t)N * n_D * 4 * esz) : 0;
+    const size_t f_buck = foff;  foff += al((size_t)(fbat.n_bucket_total + 1) * 4);
+    const size_t f_rec = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(Node4<float>));
+    e = cudaMallocAsync((void**)&fold_mem, foff, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fold_mem + f_segs, fbat.segs.data(), fbat.segs.size() * sizeof(FoldSeg),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "nu_batch_search: fold setup");
+    }
+    const FoldSeg* fsegs = (const FoldSeg*)(fold_mem + f_segs);
+    void* nodes = fold_mem + f_nodes;
+    int* bucket = (int*)(fold_mem + f_buck);
+    Node4<float>* rec = (Node4<float>*)(fold_mem + f_rec);
+    unsigned long long* ctr = (unsigned long long*)(mem + o_ctr);
+    const double* Ds_dev = (const double*)(mem + o_Ds);
+    int dev = 0, n_sm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    // the enqueue of everything after setup (graph body)
+    auto enqueue = [&](int grid, int threads, int64_t nP_run, int n_run,
+                       cudaStream_t st) -> int {
+        int l = 0;
+        k_init_dstat<<<div_up(n_lc, 128), 128, 0, st>>>(fb.dstat, s_off_dev, n_lc);
+        ++l;
+        int lf = 0;
+        launch_factor(plan, fb, ws, diag_var_dev, nullptr, 0, y_dev, st, &lf);
+        l += lf;
+        if (fp64) {
+            FactorView<double> fv{fb.F, fb.kg, fb.invD, fb.G, fb.z0, fb.Zt};
+            l += launch_window_batch(nb, true, t_dev, k, &fv, s_off_dev, n_lc, N, Ds_dev, n_D,
+                                     lin_d, lin_v, lin_l, st);
+        } else {
+            FactorView<float> fv{fb.F32, fb.kg32, fb.invD32, fb.G32, fb.z032, fb.Zt32};
+            l += launch_window_batch(nb, false, t_dev, k, &fv, s_off_dev, n_lc, N, Ds_dev, n_D,
+                                     lin_d, lin_v, lin_l, st);
+        }
+        l += launch_fold_prep(fbat, fsegs, s_off_dev, n_lc, N, fp64, t_dev, lin_d, lin_v,
+                              lin_l, n_D, phase_step, gap_factor, nodes, bucket, rec, st);
+        cudaMemsetAsync(ctr, 0, 16, st);
+        l += launch_fold_batch(fbat, fsegs, n_run, fp64, t_dev, nodes, bucket, rec, n_D,
+                               phase_step, gap_factor, periods_dev, nP_run, ctr, grid, threads,
+                               Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
+                               lnP_dev, st);
+        count_launches(l - lf);      // launch_factor counted its own
+        return l;
+    };
+    // ------------------------------------------------------- autotuning
+    const TuneKey key{nb, k, (int)prec, n_D};
+    TuneVal tv{0, 0};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) tv = it->second;
+    }
+    if (tv.threads == 0) {
+        // time the fold on a slice (first curves, first periods) for each shape
+        const int n_run = n_lc < 8 ? n_lc : 8;
+        const int64_t nP_run = n_P < 256 ? n_P : 256;
+        const int cand[4][2] = {{2, 256}, {4, 256}, {4, 128}, {8, 128}};
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        launched += enqueue(n_sm * 2, 256, nP_run, n_run, st);    // warm the caches
+        for (int c = 0; c < 4; ++c) {
+            cudaMemsetAsync(ctr, 0, 16, st);
+            cudaEventRecord(e0, st);
+            const int lt = launch_fold_batch(fbat, fsegs, n_run, fp64, t_dev, nodes, bucket,
+                                             rec, n_D, phase_step, gap_factor, periods_dev,
+                                             nP_run, ctr, n_sm * cand[c][0], cand[c][1], Q_dev,
+                                             T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
+                                             lnP_dev, st);
+            count_launches(lt);
+            launched += lt;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                tv = TuneVal{cand[c][0], cand[c][1]};
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = tv;
+    }
+    // ------------------------------------------------ capture and launch
+    // capture on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured), launch on the caller's stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    int in_graph = 0;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        in_graph = enqueue(n_sm * tv.blocks_per_sm, tv.threads, n_P, n_lc, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "nu_batch_search: graph");
+    }
+    launched += in_graph;
+    std::vector<long long> ds(2 * (size_t)n_lc);
+    e = cudaMemcpyAsync(ds.data(), fb.dstat, ds.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "nu_batch_search: status");
+    for (int g = 0; g < n_lc; ++g) status_host[g] = (int)ds[2 * g];
+    (void)launched;
+    return NU_OK;
+}

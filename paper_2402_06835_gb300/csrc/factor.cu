@@ -18,7 +18,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
+#include "factor_core.cuh"
 #include "factor_ops.cuh"
 #include "nu_internal.cuh"
 #include "ss.cuh"
@@ -27,23 +29,35 @@ namespace nu {
 
 enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOTPD = 2 };
 
-__device__ inline void flag_bad(long long* dstat, int code, long long idx) {
-    // keep the smallest failing index; the first code that claims it wins
-    unsigned long long old = atomicMin((unsigned long long*)&dstat[1],
-                                       (unsigned long long)idx);
-    if ((long long)old > idx) atomicExch((unsigned long long*)&dstat[0],
-                                         (unsigned long long)code);
+__device__ inline void flag_bad(long long* ds, int code, long long idx) {
+    // keep the smallest failing local index; the code that claims it wins
+    const unsigned long long old = atomicMin((unsigned long long*)&ds[1], (unsigned long long)idx);
+    if ((long long)old > idx) atomicExch((unsigned long long*)&ds[0], (unsigned long long)code);
+}
+
+// segment of packed sample i: s_off[g] <= i < s_off[g + 1]
+__device__ __forceinline__ int seg_of(const int64_t* __restrict__ s_off, int n_seg, int64_t i) {
+    int lo = 0, hi = n_seg;                  // find the last g with s_off[g] <= i
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // ---------------------------------------------------------------- transitions
 template <int NB>
-__global__ void k_transitions(const double* __restrict__ t, int64_t n, Blocks bl,
-                              double* __restrict__ F, long long* dstat) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void k_transitions(const double* __restrict__ t, int64_t n,
+                              const int64_t* __restrict__ s_off, int n_seg,
+                              const Blocks* __restrict__ blocks, double* __restrict__ F,
+                              long long* dstat) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int g = seg_of(s_off, n_seg, i);
+    const int64_t loc = i - s_off[g];
     double* Fi = F + i * NB * 4;
-    if (!isfinite(t[i])) flag_bad(dstat, ST_EINVAL, i);
-    if (i == 0) {
+    if (!isfinite(t[i])) flag_bad(dstat + 2 * g, ST_EINVAL, loc);
+    if (loc == 0) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             Fi[4 * b] = 1.0; Fi[4 * b + 1] = 0.0; Fi[4 * b + 2] = 0.0; Fi[4 * b + 3] = 1.0;
@@ -51,7 +65,8 @@ __global__ void k_transitions(const double* __restrict__ t, int64_t n, Blocks bl
         return;
     }
     const double tau = t[i] - t[i - 1];
-    if (!(tau > 0.0)) flag_bad(dstat, ST_EINVAL, i);
+    if (!(tau > 0.0)) flag_bad(dstat + 2 * g, ST_EINVAL, loc);
+    const Blocks bl = blocks[g];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         double f[4];
@@ -60,13 +75,38 @@ __global__ void k_transitions(const double* __restrict__ t, int64_t n, Blocks bl
     }
 }
 
-// -------------------------------------------------------------- null GLS
-// One thread: A = X^T Sigma^-1 X = R^T R (Cholesky), w = A^-1 X^T Sigma^-1 y,
-// Rinv = R^-1.  wR layout: [0..k) w, [k .. k+k*k) Rinv row-major.
-__global__ void k_null_gls(int k, const double* __restrict__ cross, double* __restrict__ wR,
-                           long long* dstat) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (dstat[0] != 0) return;       // the factor already failed
+// ------------------------------------------------- cross products per segment
+// cross[g][a][b] = sum over the segment's chunks of partial[c][a][b]
+__global__ void k_reduce_cross(const double* __restrict__ partial, const SegInfo* __restrict__ segs,
+                               int nr, double* __restrict__ cross) {
+    __shared__ double sh[128];
+    const int g = blockIdx.x / (nr * nr);
+    const int ab = blockIdx.x % (nr * nr);
+    const int a = ab / nr, b = ab % nr;
+    const SegInfo sg = segs[g];
+    double s = 0.0;
+    for (int64_t c = threadIdx.x; c < sg.n_c; c += blockDim.x)
+        s += partial[(sg.c_off + c) * NRMAX * NRMAX + a * NRMAX + b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cross[(int64_t)g * NRMAX * NRMAX + a * nr + b] = sh[0];
+}
+
+// ------------------------------------------------------------------ null GLS
+// One thread per segment: A = X^T Sigma^-1 X = R^T R, w = A^-1 X^T Sigma^-1 y,
+// Rinv = R^-1.  wR[g]: [0..k) w, [k .. k+k*k) Rinv row-major.
+__global__ void k_null_gls(int k, int n_seg, const double* __restrict__ cross_all,
+                           double* __restrict__ wR_all, long long* dstat) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_seg) return;
+    long long* ds = dstat + 2 * g;
+    if (ds[0] != 0) return;       // the factor of this segment already failed
+    const double* cross = cross_all + (int64_t)g * NRMAX * NRMAX;
+    double* wR = wR_all + (int64_t)g * 32;
     const int nr = k + 1;
     double R[NU_MAX_K][NU_MAX_K] = {};
     for (int i = 0; i < k; ++i) {
@@ -74,11 +114,8 @@ __global__ void k_null_gls(int k, const double* __restrict__ cross, double* __re
             double s = cross[i * nr + j];
             for (int p = 0; p < i; ++p) s -= R[p][i] * R[p][j];
             if (i == j) {
-                if (!(s > 0.0)) {
-                    // X is rank deficient under Sigma: no null fit
-                    unsigned long long old = atomicMin((unsigned long long*)&dstat[1], 0ull);
-                    (void)old;
-                    atomicExch((unsigned long long*)&dstat[0], (unsigned long long)ST_EINVAL);
+                if (!(s > 0.0)) {          // X rank deficient under Sigma
+                    flag_bad(ds, ST_EINVAL, 0);
                     return;
                 }
                 R[i][i] = sqrt(s);
@@ -87,7 +124,6 @@ __global__ void k_null_gls(int k, const double* __restrict__ cross, double* __re
             }
         }
     }
-    // Rinv (upper triangular)
     double Ri[NU_MAX_K][NU_MAX_K] = {};
     for (int j = 0; j < k; ++j) {
         Ri[j][j] = 1.0 / R[j][j];
@@ -97,9 +133,8 @@ __global__ void k_null_gls(int k, const double* __restrict__ cross, double* __re
             Ri[i][j] = -s / R[i][i];
         }
     }
-    // w = R^-1 R^-T u, u_a = cross[a][k] (X_a^T Sigma^-1 y)
     double z[NU_MAX_K];
-    for (int i = 0; i < k; ++i) {          // R^T z = u
+    for (int i = 0; i < k; ++i) {          // R^T z = u, u_a = X_a^T Sigma^-1 y
         double s = cross[i * nr + k];
         for (int p = 0; p < i; ++p) s -= R[p][i] * z[p];
         z[i] = s / R[i][i];
@@ -115,14 +150,16 @@ __global__ void k_null_gls(int k, const double* __restrict__ cross, double* __re
 
 // ------------------------------------------- right-hand sides of the solves
 // Per sample: null residual innovation e0 = e_y - sum_c w_c e_c, its weighted
-// square (chi-square terms), and the backward right-hand sides
-// U[i][0] = e0 / D, U[i][1+a] = (sum_c e_c Rinv[c][a]) / D.
-__global__ void k_rhs(int64_t n, int k, const double* __restrict__ E,
-                      const double* __restrict__ invD, const double* __restrict__ wR,
+// square, ln D, and the backward right-hand sides U[i][0] = e0 / D,
+// U[i][1+a] = (sum_c e_c Rinv[c][a]) / D.
+__global__ void k_rhs(int64_t n, int k, const int64_t* __restrict__ s_off, int n_seg,
+                      const double* __restrict__ E, const double* __restrict__ invD,
+                      const double* __restrict__ wR_all, const double* __restrict__ Dpiv,
                       double* __restrict__ U, double* __restrict__ chi_terms,
-                      const double* __restrict__ Dpiv, double* __restrict__ logD) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                      double* __restrict__ logD) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double* wR = wR_all + (int64_t)seg_of(s_off, n_seg, i) * 32;
     const int nr = k + 1;
     const double* e = E + i * nr;
     double e0 = e[k];
@@ -138,161 +175,210 @@ __global__ void k_rhs(int64_t n, int k, const double* __restrict__ E,
     logD[i] = log(Dpiv[i]);
 }
 
-// -------------------------------------------------- deterministic reductions
-// partial[b] = sum over a contiguous range; then one block sums the partials.
-__global__ void k_sum_partial(const double* __restrict__ x, int64_t n, double* partial) {
-    __shared__ double sh[256];
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = blockIdx.x * per;
-    const int64_t hi = lo + per < n ? lo + per : n;
-    double s = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += x[i];
-    sh[threadIdx.x] = s;
+// ------------------------------------------------ per-segment scalars
+// One block per segment: ln|Sigma| = sum ln D, chi2 of the null fit, and the
+// null log-likelihood of Eq. linear_search_ll (deterministic tree sums).
+__global__ void k_seg_scalars(const double* __restrict__ chi_terms,
+                              const double* __restrict__ logD, const SegInfo* __restrict__ segs,
+                              double* __restrict__ scal) {
+    __shared__ double sc[256], sl[256];
+    const SegInfo sg = segs[blockIdx.x];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < sg.n; i += blockDim.x) {
+        a += chi_terms[sg.s_off + i];
+        b += logD[sg.s_off + i];
+    }
+    sc[threadIdx.x] = a;
+    sl[threadIdx.x] = b;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        if (threadIdx.x < w) {
+            sc[threadIdx.x] += sc[threadIdx.x + w];
+            sl[threadIdx.x] += sl[threadIdx.x + w];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
-}
-
-// cross[a][b] = sum over chunks of partial[c][a][b] (one block per entry)
-__global__ void k_reduce_cross(const double* __restrict__ partial, int64_t n_chunks, int nr,
-                               double* __restrict__ cross) {
-    __shared__ double sh[256];
-    const int a = blockIdx.x / nr, b = blockIdx.x % nr;
-    double s = 0.0;
-    for (int64_t c = threadIdx.x; c < n_chunks; c += blockDim.x)
-        s += partial[c * NRMAX * NRMAX + a * NRMAX + b];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double* s = scal + 4 * blockIdx.x;
+        s[0] = sl[0];
+        s[2] = sc[0];
+        s[1] = -0.5 * sc[0] - 0.5 * sl[0] - 0.5 * (double)sg.n * log(2.0 * M_PI);
     }
-    if (threadIdx.x == 0) cross[a * nr + b] = sh[0];
-}
-
-__global__ void k_finalize(int64_t n, int nparts, const double* __restrict__ pchi,
-                           const double* __restrict__ plog, double* scal) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double chi = 0.0, lg = 0.0;
-    for (int b = 0; b < nparts; ++b) {
-        chi += pchi[b];
-        lg += plog[b];
-    }
-    scal[0] = lg;
-    scal[2] = chi;
-    scal[1] = -0.5 * chi - 0.5 * lg - 0.5 * (double)n * log(2.0 * M_PI);
 }
 
 // ------------------------------------------------------------- FP32 copies
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
 }
 
-// ------------------------------------------------------------------ driver
-// chunk length, group size and top-level count of the scans
-constexpr int SCAN_B = 32;
-constexpr int SCAN_G = 8;
-constexpr int SCAN_TOP = 16;
-
+// ------------------------------------------------------------------ plan
 template <int NB>
-static size_t factor_workspace(int64_t n, int k) {
-    const int64_t nc = (n + SCAN_B - 1) / SCAN_B;
-    size_t m = plan_scan<RiccatiOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes;
-    m = std::max(m, plan_scan<ForwardOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes);
-    m = std::max(m, plan_scan<BackwardOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes);
-    m = std::max(m, plan_scan<FutureOp<NB>>(nc, SCAN_G, SCAN_TOP).bytes);
-    (void)k;
-    return m + (size_t)nc * NRMAX * NRMAX * sizeof(double) + 512;
+static size_t scan_workspace(const ScanShape& sh) {
+    size_t m = scan_bytes<RiccatiOp<NB>>(sh);
+    m = std::max(m, scan_bytes<ForwardOp<NB>>(sh));
+    m = std::max(m, scan_bytes<BackwardOp<NB>>(sh));
+    m = std::max(m, scan_bytes<FutureOp<NB>>(sh));
+    return m;
 }
 
-template <int NB>
-static nu_status run_factor(nu_factor* f, const double* diag_var, const double* X,
-                            const double* y, double* scratch, char* ws) {
-    constexpr int J = Dims<NB>::J;
-    constexpr int JJ = Dims<NB>::JJ;
-    const int64_t n = f->n;
-    const int k = f->k;
-    const int nr = k + 1;
-    cudaStream_t st = f->stream;
-    const int nblk = div_up(n, 256);
-    const int64_t nc = (n + SCAN_B - 1) / SCAN_B;
-    // scratch layout
-    double* Dpiv = scratch;                 // n
-    double* U = Dpiv + n;                   // n * nr
-    double* chi_terms = U + n * nr;         // n
-    double* logD = chi_terms + n;           // n
-    double* cross = logD + n;               // 32
-    double* wR = cross + 32;                // 32
-    double* pchi = wR + 32;                 // 256
-    double* plog = pchi + 256;              // 256
-    int launched = 0;
-    k_transitions<NB><<<nblk, 256, 0, st>>>(f->t, n, f->blocks, f->F, f->dstat);
-    ++launched;
-    // 1. pivots and gains
-    RiccatiOp<NB> ric;
-    ric.F = f->F;
-    ric.dv = diag_var;
-    ric.n = n;
-    ric.B = SCAN_B;
-    for (int b = 0; b < NB; ++b) {
-        ric.pinf[2 * b] = f->blocks.b[b].sigma2;
-        ric.pinf[2 * b + 1] = f->blocks.b[b].type == 0 ? f->blocks.b[b].sigma2 : 0.0;
-    }
-    ric.kg = f->kg;
-    ric.invD = f->invD;
-    ric.Dpiv = Dpiv;
-    ric.dstat = f->dstat;
-    launched += run_scan(ric, plan_scan<RiccatiOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
-    // 2. forward solves of X and y, cross products
-    double* partial = (double*)(ws + factor_workspace<NB>(n, k) -
-                                (size_t)nc * NRMAX * NRMAX * sizeof(double) - 256);
-    ForwardOp<NB> fw{f->F, f->kg, f->invD, X, y, n, k, SCAN_B, f->work, partial};
-    launched += run_scan(fw, plan_scan<ForwardOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
-    k_reduce_cross<<<nr * nr, 256, 0, st>>>(partial, nc, nr, cross);
-    ++launched;
-    // 3. null fit, right-hand sides, backward solves
-    if (k > 0) {
-        k_null_gls<<<1, 32, 0, st>>>(k, cross, wR, f->dstat);
-        ++launched;
-    }
-    k_rhs<<<nblk, 256, 0, st>>>(n, k, f->work, f->invD, wR, U, chi_terms, Dpiv, logD);
-    ++launched;
-    BackwardOp<NB> bw{f->F, f->kg, U, n, nr, k, SCAN_B, nc, f->z0, f->Zt};
-    launched += run_scan(bw, plan_scan<BackwardOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
-    // 4. future information
-    FutureOp<NB> fu{f->F, f->kg, f->invD, n, SCAN_B, nc, f->G};
-    launched += run_scan(fu, plan_scan<FutureOp<NB>>(nc, SCAN_G, SCAN_TOP), ws, st);
-    // scalars and FP32 copies
-    const int nparts = 256;
-    k_sum_partial<<<nparts, 256, 0, st>>>(chi_terms, n, pchi);
-    k_sum_partial<<<nparts, 256, 0, st>>>(logD, n, plog);
-    k_finalize<<<1, 32, 0, st>>>(n, nparts, pchi, plog, f->scal);
-    launched += 3;
-    const int64_t sizes[6] = {n * NB * 4, n * (int64_t)J, n, n * (int64_t)JJ, n, n * (int64_t)k};
-    const double* src[6] = {f->F, f->kg, f->invD, f->G, f->z0, f->Zt};
-    float* dst[6] = {f->F32, f->kg32, f->invD32, f->G32, f->z032, f->Zt32};
-    for (int a = 0; a < 6; ++a)
-        if (sizes[a] > 0) {
-            k_to_f32<<<div_up(sizes[a], 256), 256, 0, st>>>(src[a], dst[a], sizes[a]);
-            ++launched;
+FactorPlan plan_factor(const int64_t* n_per_seg, const Blocks* blocks, int n_seg, int k) {
+    FactorPlan p{};
+    p.nb = blocks[0].nb;
+    p.k = k;
+    p.n_seg = n_seg;
+    std::vector<int64_t> nc(n_seg);
+    p.s_off.assign(n_seg + 1, 0);
+    p.segs.resize(n_seg);
+    p.blocks.assign(blocks, blocks + n_seg);
+    for (int g = 0; g < n_seg; ++g) {
+        nc[g] = (n_per_seg[g] + SCAN_B - 1) / SCAN_B;
+        SegInfo& sg = p.segs[g];
+        sg.s_off = p.n_total;
+        sg.n = n_per_seg[g];
+        sg.c_off = p.n_chunks;
+        sg.n_c = nc[g];
+        for (int j = 0; j < 2 * NU_MAX_BLOCKS; ++j) sg.pinf[j] = 0.0;
+        for (int b = 0; b < blocks[g].nb; ++b) {
+            sg.pinf[2 * b] = blocks[g].b[b].sigma2;
+            sg.pinf[2 * b + 1] = blocks[g].b[b].type == 0 ? blocks[g].b[b].sigma2 : 0.0;
         }
-    count_launches(launched);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "nu_gp_factor launch");
+        p.n_total += n_per_seg[g];
+        p.n_chunks += nc[g];
+        p.s_off[g + 1] = p.n_total;
+    }
+    p.shape = build_scan_shape(nc.data(), n_seg, SCAN_G, SCAN_TOP, nullptr);
+    p.index.assign(p.shape.n_index, 0);
+    build_scan_shape(nc.data(), n_seg, SCAN_G, SCAN_TOP, p.index.data());
+    p.chunk_seg.resize(p.n_chunks);
+    int64_t c = 0;
+    for (int g = 0; g < n_seg; ++g)
+        for (int64_t q = 0; q < nc[g]; ++q) p.chunk_seg[c++] = g;
+    size_t scan = 0;
+    switch (p.nb) {
+        case 1: scan = scan_workspace<1>(p.shape); break;
+        case 2: scan = scan_workspace<2>(p.shape); break;
+        case 3: scan = scan_workspace<3>(p.shape); break;
+        default: scan = scan_workspace<4>(p.shape); break;
+    }
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const int nr = k + 1;
+    size_t off = 0;
+    p.off_scan = off;       off += al(scan);
+    p.off_partial = off;    off += al((size_t)p.n_chunks * NRMAX * NRMAX * 8);
+    p.off_idx = off;        off += al(p.index.size() * 8);
+    p.off_chunk_seg = off;  off += al(p.chunk_seg.size() * 4);
+    p.off_segs = off;       off += al((size_t)n_seg * sizeof(SegInfo));
+    p.off_blocks = off;     off += al((size_t)n_seg * sizeof(Blocks));
+    p.off_s_off = off;      off += al((size_t)(n_seg + 1) * 8);
+    p.off_cross = off;      off += al((size_t)n_seg * NRMAX * NRMAX * 8);
+    p.off_wR = off;         off += al((size_t)n_seg * 32 * 8);
+    p.off_Dpiv = off;       off += al((size_t)p.n_total * 8);
+    p.off_U = off;          off += al((size_t)p.n_total * nr * 8);
+    p.off_chi = off;        off += al((size_t)p.n_total * 8);
+    p.off_logD = off;       off += al((size_t)p.n_total * 8);
+    p.bytes = off;
+    return p;
+}
+
+nu_status upload_factor_plan(const FactorPlan& p, char* ws, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(ws + p.off_idx, p.index.data(), p.index.size() * 8,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + p.off_chunk_seg, p.chunk_seg.data(), p.chunk_seg.size() * 4,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + p.off_segs, p.segs.data(), p.segs.size() * sizeof(SegInfo),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + p.off_blocks, p.blocks.data(), p.blocks.size() * sizeof(Blocks),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + p.off_s_off, p.s_off.data(), p.s_off.size() * 8,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host sources are temporaries
+    if (e != cudaSuccess) return cuda_fail(e, "factor plan upload");
     return NU_OK;
 }
 
-static size_t workspace_bytes(int nb, int64_t n, int k) {
-    switch (nb) {
-        case 1: return factor_workspace<1>(n, k);
-        case 2: return factor_workspace<2>(n, k);
-        case 3: return factor_workspace<3>(n, k);
-        default: return factor_workspace<4>(n, k);
+template <int NB>
+static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* ws,
+                            const double* dv, const double* X, int64_t ldx, const double* y,
+                            cudaStream_t st) {
+    constexpr int J = Dims<NB>::J;
+    constexpr int JJ = Dims<NB>::JJ;
+    const int64_t n = p.n_total;
+    const int k = p.k;
+    const int nr = k + 1;
+    const int nblk = div_up(n, 256);
+    char* scan_ws = ws + p.off_scan;
+    double* partial = (double*)(ws + p.off_partial);
+    const int64_t* idx = (const int64_t*)(ws + p.off_idx);
+    const int* chunk_seg = (const int*)(ws + p.off_chunk_seg);
+    const SegInfo* segs = (const SegInfo*)(ws + p.off_segs);
+    const Blocks* blocks = (const Blocks*)(ws + p.off_blocks);
+    const int64_t* s_off = (const int64_t*)(ws + p.off_s_off);
+    double* cross = (double*)(ws + p.off_cross);
+    double* wR = (double*)(ws + p.off_wR);
+    double* Dpiv = (double*)(ws + p.off_Dpiv);
+    double* U = (double*)(ws + p.off_U);
+    double* chi = (double*)(ws + p.off_chi);
+    double* logD = (double*)(ws + p.off_logD);
+    int launched = 0;
+    k_transitions<NB><<<nblk, 256, 0, st>>>(b.t, n, s_off, p.n_seg, blocks, b.F, b.dstat);
+    ++launched;
+    // 1. pivots and gains
+    RiccatiOp<NB> ric{segs, chunk_seg, b.F, dv, SCAN_B, b.kg, b.invD, Dpiv, b.dstat};
+    launched += run_scan(ric, p.shape, idx, scan_ws, st);
+    // 2. forward solves of X and y, cross products
+    ForwardOp<NB> fw{segs, chunk_seg, b.F, b.kg, b.invD, X, ldx, b.t, y, k, SCAN_B, b.work,
+                     partial};
+    launched += run_scan(fw, p.shape, idx, scan_ws, st);
+    k_reduce_cross<<<p.n_seg * nr * nr, 128, 0, st>>>(partial, segs, nr, cross);
+    ++launched;
+    // 3. null fit, right-hand sides, backward solves
+    if (k > 0) {
+        k_null_gls<<<div_up(p.n_seg, 64), 64, 0, st>>>(k, p.n_seg, cross, wR, b.dstat);
+        ++launched;
     }
+    k_rhs<<<nblk, 256, 0, st>>>(n, k, s_off, p.n_seg, b.work, b.invD, wR, Dpiv, U, chi, logD);
+    ++launched;
+    BackwardOp<NB> bw{segs, chunk_seg, b.F, b.kg, U, nr, k, SCAN_B, b.z0, b.Zt};
+    launched += run_scan(bw, p.shape, idx, scan_ws, st);
+    // 4. future information
+    FutureOp<NB> fu{segs, chunk_seg, b.F, b.kg, b.invD, SCAN_B, b.G};
+    launched += run_scan(fu, p.shape, idx, scan_ws, st);
+    k_seg_scalars<<<p.n_seg, 256, 0, st>>>(chi, logD, segs, b.scal);
+    ++launched;
+    if (b.F32) {
+        const int64_t sizes[6] = {n * NB * 4, n * (int64_t)J, n, n * (int64_t)JJ, n,
+                                  n * (int64_t)k};
+        const double* src[6] = {b.F, b.kg, b.invD, b.G, b.z0, b.Zt};
+        float* dst[6] = {b.F32, b.kg32, b.invD32, b.G32, b.z032, b.Zt32};
+        for (int a = 0; a < 6; ++a)
+            if (sizes[a] > 0) {
+                k_to_f32<<<div_up(sizes[a], 256), 256, 0, st>>>(src[a], dst[a], sizes[a]);
+                ++launched;
+            }
+    }
+    return launched;
+}
+
+nu_status launch_factor(const FactorPlan& p, const FactorBuffers& b, char* ws,
+                        const double* dv, const double* X, int64_t ldx, const double* y,
+                        cudaStream_t st, int* launched) {
+    int l = 0;
+    switch (p.nb) {
+        case 1: l = launch_factor_nb<1>(p, b, ws, dv, X, ldx, y, st); break;
+        case 2: l = launch_factor_nb<2>(p, b, ws, dv, X, ldx, y, st); break;
+        case 3: l = launch_factor_nb<3>(p, b, ws, dv, X, ldx, y, st); break;
+        default: l = launch_factor_nb<4>(p, b, ws, dv, X, ldx, y, st); break;
+    }
+    if (launched) *launched += l;
+    count_launches(l);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "factor launch");
+    return NU_OK;
 }
 
 }  // namespace nu
@@ -314,13 +400,13 @@ extern "C" nu_status nu_gp_factor(const double* t_dev, const double* diag_var_de
     if (s != NU_OK) return s;
     const int nb = bl.nb;
     const int J = 2 * nb, JJ = J * (J + 1) / 2;
-    // sizes in 8-byte words
+    const FactorPlan plan = plan_factor(&n, &bl, 1, k);
+    // persistent arrays (8-byte words)
     const int64_t w_t = n, w_F = n * nb * 4, w_kg = n * J, w_iD = n, w_G = n * JJ,
                   w_z0 = n, w_Zt = n * k, w_work = n * (k + 1), w_scal = 8, w_stat = 2;
-    const int64_t w_scratch = n + n * (k + 1) + n + n + 32 + 32 + 256 + 256;
     const int64_t w_f32 = (w_F + w_kg + w_iD + w_G + w_z0 + w_Zt + 8) / 2 + 8;
     const int64_t words = w_t + w_F + w_kg + w_iD + w_G + w_z0 + w_Zt + w_work + w_scal +
-                          w_stat + w_scratch + w_f32 + 64;
+                          w_stat + w_f32 + 64;
     nu_factor* f = new nu_factor();
     f->n = n;
     f->nb = nb;
@@ -328,11 +414,19 @@ extern "C" nu_status nu_gp_factor(const double* t_dev, const double* diag_var_de
     f->blocks = bl;
     f->stream = (cudaStream_t)stream;
     f->mem_bytes = (size_t)words * 8;
+    cudaStream_t st = f->stream;
     pool_keep_memory();
-    cudaError_t e = cudaMallocAsync(&f->mem, f->mem_bytes, f->stream);
+    cudaError_t e = cudaMallocAsync(&f->mem, f->mem_bytes, st);
     if (e != cudaSuccess) {
         delete f;
         return cuda_fail(e, "nu_gp_factor: cudaMallocAsync");
+    }
+    char* ws = nullptr;
+    e = cudaMallocAsync((void**)&ws, plan.bytes, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(f->mem, st);
+        delete f;
+        return cuda_fail(e, "nu_gp_factor: workspace");
     }
     double* p = (double*)f->mem;
     f->t = p; p += w_t;
@@ -345,7 +439,6 @@ extern "C" nu_status nu_gp_factor(const double* t_dev, const double* diag_var_de
     f->work = p; p += w_work;
     f->scal = p; p += w_scal;
     f->dstat = (long long*)p; p += w_stat;
-    double* scratch = p; p += w_scratch;
     float* q = (float*)p;
     f->F32 = q; q += w_F;
     f->kg32 = q; q += w_kg;
@@ -353,32 +446,23 @@ extern "C" nu_status nu_gp_factor(const double* t_dev, const double* diag_var_de
     f->G32 = q; q += w_G;
     f->z032 = q; q += w_z0;
     f->Zt32 = q; q += w_Zt;
-    cudaStream_t st = f->stream;
     long long init[2] = {0, (long long)n};
     e = cudaMemsetAsync(f->mem, 0, f->mem_bytes, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f->dstat, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(f->t, t_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // init is a host temporary
     if (e != cudaSuccess) {
+        cudaFreeAsync(ws, st);
         cudaFreeAsync(f->mem, st);
         delete f;
         return cuda_fail(e, "nu_gp_factor: copy");
     }
-    const size_t ws_bytes = workspace_bytes(nb, n, k);
-    char* ws = nullptr;
-    e = cudaMallocAsync((void**)&ws, ws_bytes, st);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(f->mem, st);
-        delete f;
-        return cuda_fail(e, "nu_gp_factor: workspace");
-    }
-    switch (nb) {
-        case 1: s = run_factor<1>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
-        case 2: s = run_factor<2>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
-        case 3: s = run_factor<3>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
-        default: s = run_factor<4>(f, diag_var_dev, X_dev, y_dev, scratch, ws); break;
+    s = upload_factor_plan(plan, ws, st);            // synchronises: init is a temporary
+    if (s == NU_OK) {
+        FactorBuffers b{f->t, f->F, f->kg, f->invD, f->G, f->z0, f->Zt, f->work, f->scal,
+                        f->dstat, f->F32, f->kg32, f->invD32, f->G32, f->z032, f->Zt32};
+        s = launch_factor(plan, b, ws, diag_var_dev, X_dev, n, y_dev, st, nullptr);
     }
     cudaFreeAsync(ws, st);
     if (s != NU_OK) {

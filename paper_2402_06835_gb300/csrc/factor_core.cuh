@@ -1,0 +1,69 @@
+// Factor of one or several light curves (segments) packed back to back.
+// Shared by nu_gp_factor (one segment) and nu_batch_search (many).
+#pragma once
+
+#include <vector>
+
+#include "factor_ops.cuh"
+#include "nu_internal.cuh"
+
+namespace nu {
+
+// chunk length, group size and top-level count of the scans
+constexpr int SCAN_B = 32;
+constexpr int SCAN_G = 8;
+constexpr int SCAN_TOP = 16;
+
+// Device arrays of a factor, all indexed by packed sample.
+struct FactorBuffers {
+    const double* t;
+    double* F;          // [n][nb][4]
+    double* kg;         // [n][J]
+    double* invD;       // [n]
+    double* G;          // [n][J(J+1)/2]
+    double* z0;         // [n]
+    double* Zt;         // [n][k]
+    double* work;       // [n][k+1] forward innovations
+    double* scal;       // per segment [4]: logdet, lnL_null, chi2, -
+    long long* dstat;   // per segment [2]: status, first bad local sample
+    float* F32;         // FP32 copies (null: not made)
+    float* kg32;
+    float* invD32;
+    float* G32;
+    float* z032;
+    float* Zt32;
+};
+
+// Host plan: segment table, scan structure, workspace layout.
+struct FactorPlan {
+    int nb;
+    int k;
+    int n_seg;
+    int64_t n_total;
+    int64_t n_chunks;
+    ScanShape shape;
+    std::vector<int64_t> index;      // scan index arrays
+    std::vector<int> chunk_seg;      // segment of each chunk
+    std::vector<int64_t> s_off;      // [n_seg + 1]
+    std::vector<SegInfo> segs;
+    std::vector<Blocks> blocks;
+    // workspace layout (bytes)
+    size_t off_scan, off_partial, off_idx, off_chunk_seg, off_segs, off_blocks, off_s_off,
+        off_cross, off_wR, off_Dpiv, off_U, off_chi, off_logD, bytes;
+};
+
+// Build the plan for segments of n_g samples with the given covariance blocks
+// (all segments must have the same number of blocks).
+FactorPlan plan_factor(const int64_t* n_per_seg, const Blocks* blocks, int n_seg, int k);
+
+// Copy the plan's tables into the workspace (synchronises the stream).
+nu_status upload_factor_plan(const FactorPlan& p, char* ws, cudaStream_t st);
+
+// Enqueue every kernel of the factor (no host synchronisation, no
+// allocation): safe to capture in a CUDA graph.  X may be null (then the
+// columns are [1, t] up to k), with leading dimension ldx otherwise.
+nu_status launch_factor(const FactorPlan& p, const FactorBuffers& b, char* ws,
+                        const double* diag_var, const double* X, int64_t ldx,
+                        const double* y, cudaStream_t st, int* launched);
+
+}  // namespace nu

@@ -33,12 +33,42 @@ namespace nu {
 
 constexpr int NRMAX = NU_MAX_K + 1;
 
+// One light curve inside packed per-sample arrays.
+struct SegInfo {
+    int64_t s_off;                    // first sample
+    int64_t n;                        // samples
+    int64_t c_off;                    // first chunk (level-0 scan element)
+    int64_t n_c;                      // chunks
+    double pinf[2 * NU_MAX_BLOCKS];   // diagonal of the stationary covariance
+};
+
+// Samples [s, e] of global chunk gc (time order), the segment's first sample
+// and its end (one past the last sample).  rev: chunks in reverse time order.
+struct ChunkRange {
+    int g;
+    int64_t s, e, base, end;
+};
+__device__ __forceinline__ ChunkRange chunk_of(const SegInfo* __restrict__ segs,
+                                               const int* __restrict__ chunk_seg,
+                                               int64_t gc, int B, bool rev) {
+    ChunkRange r;
+    r.g = chunk_seg[gc];
+    const SegInfo sg = segs[r.g];
+    int64_t c = gc - sg.c_off;
+    if (rev) c = sg.n_c - 1 - c;
+    r.base = sg.s_off;
+    r.end = sg.s_off + sg.n;
+    r.s = r.base + c * B;
+    r.e = (r.s + B < r.end ? r.s + B : r.end) - 1;
+    return r;
+}
+
 // dense J x J copy of the block-diagonal transition into sample i
 template <int NB>
 __device__ __forceinline__ void dense_F(const double* __restrict__ F, int64_t i,
-                                        Mat<2 * NB>& Fm) {
+                                        Mat<2 * NB>& Fm, bool first = false) {
     mat_zero(Fm);
-    if (i == 0) return;
+    if (first) return;
     const double* f = F + i * NB * 4;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -52,9 +82,9 @@ __device__ __forceinline__ void dense_F(const double* __restrict__ F, int64_t i,
 // M <- F M F^T for block-diagonal F (F_0 = 0)
 template <int NB>
 __device__ __forceinline__ void congruence_F(const double* __restrict__ F, int64_t i,
-                                             Mat<2 * NB>& M) {
+                                             Mat<2 * NB>& M, bool first) {
     constexpr int J = 2 * NB;
-    if (i == 0) {
+    if (first) {
         mat_zero(M);
         return;
     }
@@ -81,11 +111,6 @@ __device__ __forceinline__ void congruence_F(const double* __restrict__ F, int64
     mat_symmetrize(M);
 }
 
-__device__ __forceinline__ void chunk_range(int64_t c, int B, int64_t n, int64_t& s,
-                                            int64_t& e) {
-    s = c * B;
-    e = s + B < n ? s + B - 1 : n - 1;
-}
 
 // --------------------------------------------------------------- Riccati
 template <int NB>
@@ -97,39 +122,34 @@ struct RiccatiOp {
     struct State {
         Mat<J> P;          // filtered covariance after the previous chunk
     };
+    const SegInfo* segs;
+    const int* chunk_seg;
     const double* F;
     const double* dv;
-    int64_t n;
     int B;
-    double pinf[J];        // diagonal of P_inf
     double* kg;
     double* invD;
     double* Dpiv;
-    long long* dstat;
+    long long* dstat;      // per segment: [2 g] status, [2 g + 1] first bad sample (local)
 
     __device__ void init_state(State& s) const { mat_zero(s.P); }
 
     // one filter step from the explained covariance Mf (= P_inf - P_filtered)
-    // of the previous sample; returns D and the filtered Mf of this sample
-    __device__ __forceinline__ double step(int64_t i, Mat<J>& Mf, double* Ph) const {
-        congruence_F<NB>(F, i, Mf);                  // M_i = F_i Mf F_i^T
-        double hMh = 0.0;
+    // of the previous sample; returns D, P h and the filtered Mf of this sample
+    __device__ __forceinline__ double step(int64_t i, bool first, const double* pinf,
+                                           Mat<J>& Mf, double* Ph) const {
+        congruence_F<NB>(F, i, Mf, first);           // M_i = F_i Mf F_i^T
+        double hMh = 0.0, prior = 0.0;
 #pragma unroll
         for (int r = 0; r < J; ++r) {
-            double s = Mf(r, 0);
+            double t = Mf(r, 0);
 #pragma unroll
-            for (int b = 1; b < NB; ++b) s += Mf(r, 2 * b);
-            Ph[r] = (r % 2 == 0 ? pinf[r] : 0.0) - s;   // P h = (P_inf - M) h
-        }
-        double prior = 0.0;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) prior += pinf[2 * b];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            double s = Mf(2 * b, 0);
-#pragma unroll
-            for (int q = 1; q < NB; ++q) s += Mf(2 * b, 2 * q);
-            hMh += s;
+            for (int b = 1; b < NB; ++b) t += Mf(r, 2 * b);
+            Ph[r] = (r % 2 == 0 ? pinf[r] : 0.0) - t;   // P h = (P_inf - M) h
+            if (r % 2 == 0) {
+                hMh += t;
+                prior += pinf[r];
+            }
         }
         const double D = (prior + dv[i]) - hMh;
         const double iD = 1.0 / D;
@@ -140,30 +160,30 @@ struct RiccatiOp {
         return D;
     }
 
-    __device__ void elem(int64_t c, Elem& E) const {
-        int64_t s, e;
-        chunk_range(c, B, n, s, e);
+    __device__ void elem(int64_t gc, Elem& E) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, false);
+        const double* pinf = segs[cr.g].pinf;
         Mat<J> Mf, Psi, Jacc;
         mat_zero(Mf);
 #pragma unroll
         for (int r = 0; r < J; ++r) Mf(r, r) = pinf[r];   // known state: P = 0
         mat_eye(Psi);
         mat_zero(Jacc);
-        for (int64_t i = s; i <= e; ++i) {
+        for (int64_t i = cr.s; i <= cr.e; ++i) {
+            const bool first = i == cr.base;
             Mat<J> Fm, Phi;
-            dense_F<NB>(F, i, Fm);
+            dense_F<NB>(F, i, Fm, first);
             mat_mul(Fm, Psi, Phi);                          // predicted sensitivity
             double Ph[J];
-            const double D = step(i, Mf, Ph);
+            const double D = step(i, first, pinf, Mf, Ph);
             const double iD = 1.0 / D;
-            double g[J], hPhi[J];
+            double g[J];
 #pragma unroll
             for (int q = 0; q < J; ++q) {
                 double t = Phi(0, q);
 #pragma unroll
                 for (int b = 1; b < NB; ++b) t += Phi(2 * b, q);
                 g[q] = t;
-                hPhi[q] = t;
             }
 #pragma unroll
             for (int r = 0; r < J; ++r)
@@ -173,7 +193,7 @@ struct RiccatiOp {
 #pragma unroll
             for (int r = 0; r < J; ++r)
 #pragma unroll
-                for (int q = 0; q < J; ++q) Psi(r, q) = fma(-Ph[r] * iD, hPhi[q], Phi(r, q));
+                for (int q = 0; q < J; ++q) Psi(r, q) = fma(-Ph[r] * iD, g[q], Phi(r, q));
         }
         E.A = Psi;
 #pragma unroll
@@ -225,22 +245,22 @@ struct RiccatiOp {
         mat_symmetrize(st.P);
     }
 
-    __device__ void final(int64_t c, const State& st) const {
-        int64_t s, e;
-        chunk_range(c, B, n, s, e);
+    __device__ void final(int64_t gc, const State& st) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, false);
+        const double* pinf = segs[cr.g].pinf;
         Mat<J> Mf;
 #pragma unroll
         for (int r = 0; r < J; ++r)
 #pragma unroll
             for (int q = 0; q < J; ++q) Mf(r, q) = (r == q ? pinf[r] : 0.0) - st.P(r, q);
-        for (int64_t i = s; i <= e; ++i) {
+        for (int64_t i = cr.s; i <= cr.e; ++i) {
             double Ph[J];
-            const double D = step(i, Mf, Ph);
+            const double D = step(i, i == cr.base, pinf, Mf, Ph);
             if (!(D > 0.0) || !isfinite(D)) {
-                unsigned long long old = atomicMin((unsigned long long*)&dstat[1],
-                                                   (unsigned long long)i);
-                if ((long long)old > i)
-                    atomicExch((unsigned long long*)&dstat[0], 2ull);
+                long long* ds = dstat + 2 * cr.g;
+                const unsigned long long loc = (unsigned long long)(i - cr.base);
+                const unsigned long long old = atomicMin((unsigned long long*)&ds[1], loc);
+                if (old > loc) atomicExch((unsigned long long*)&ds[0], 2ull);
             }
             const double iD = 1.0 / D;
 #pragma unroll
@@ -252,6 +272,8 @@ struct RiccatiOp {
 };
 
 // ---------------------------------------------------------- forward solve
+// Right-hand sides: the k columns of X (column-major with leading dimension
+// ldx, or the polynomial columns [1, t] when X is null) and y.
 template <int NB>
 struct ForwardOp {
     static constexpr int J = 2 * NB;
@@ -262,19 +284,24 @@ struct ForwardOp {
     struct State {
         double s[NRMAX][J];
     };
+    const SegInfo* segs;
+    const int* chunk_seg;
     const double* F;
     const double* kg;
     const double* invD;
-    const double* X;       // column-major n x k
+    const double* X;
+    int64_t ldx;
+    const double* t;       // for polynomial columns
     const double* y;
-    int64_t n;
     int k;
     int B;
     double* E;             // innovations [n][k+1]
     double* partial;       // per chunk (k+1)^2 weighted cross products
 
     __device__ __forceinline__ double xval(int64_t i, int r) const {
-        return r < k ? X[(int64_t)r * n + i] : y[i];
+        if (r == k) return y[i];
+        if (X) return X[(int64_t)r * ldx + i];
+        return r == 0 ? 1.0 : t[i];
     }
     __device__ void init_state(State& st) const {
 #pragma unroll
@@ -282,16 +309,15 @@ struct ForwardOp {
 #pragma unroll
             for (int q = 0; q < J; ++q) st.s[r][q] = 0.0;
     }
-    __device__ void elem(int64_t c, Elem& El) const {
-        int64_t s, e;
-        chunk_range(c, B, n, s, e);
+    __device__ void elem(int64_t gc, Elem& El) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, false);
         mat_eye(El.Phi);
         const int nr = k + 1;
 #pragma unroll
         for (int r = 0; r < NRMAX; ++r)
 #pragma unroll
             for (int q = 0; q < J; ++q) El.beta[r][q] = 0.0;
-        for (int64_t i = s; i <= e && i + 1 < n; ++i) {
+        for (int64_t i = cr.s; i <= cr.e && i + 1 < cr.end; ++i) {
             const double* kgi = kg + i * J;
             const double* f = F + (i + 1) * NB * 4;
             // Phi <- F (Phi - kg h^T Phi)
@@ -324,10 +350,10 @@ struct ForwardOp {
             double out[J];
 #pragma unroll
             for (int a = 0; a < J; ++a) {
-                double t = ej.beta[r][a];
+                double v = ej.beta[r][a];
 #pragma unroll
-                for (int b = 0; b < J; ++b) t = fma(ej.Phi(a, b), ei.beta[r][b], t);
-                out[a] = t;
+                for (int b = 0; b < J; ++b) v = fma(ej.Phi(a, b), ei.beta[r][b], v);
+                out[a] = v;
             }
 #pragma unroll
             for (int a = 0; a < J; ++a) ei.beta[r][a] = out[a];
@@ -340,24 +366,23 @@ struct ForwardOp {
             double out[J];
 #pragma unroll
             for (int a = 0; a < J; ++a) {
-                double t = El.beta[r][a];
+                double v = El.beta[r][a];
 #pragma unroll
-                for (int b = 0; b < J; ++b) t = fma(El.Phi(a, b), st.s[r][b], t);
-                out[a] = t;
+                for (int b = 0; b < J; ++b) v = fma(El.Phi(a, b), st.s[r][b], v);
+                out[a] = v;
             }
 #pragma unroll
             for (int a = 0; a < J; ++a) st.s[r][a] = out[a];
         }
     }
-    __device__ void final(int64_t c, const State& st0) const {
-        int64_t s, e;
-        chunk_range(c, B, n, s, e);
+    __device__ void final(int64_t gc, const State& st0) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, false);
         State st = st0;
         const int nr = k + 1;
         double acc[NRMAX][NRMAX];
         for (int a = 0; a < nr; ++a)
             for (int b = 0; b < nr; ++b) acc[a][b] = 0.0;
-        for (int64_t i = s; i <= e; ++i) {
+        for (int64_t i = cr.s; i <= cr.e; ++i) {
             const double iD = invD[i];
             double ev[NRMAX];
             for (int r = 0; r < nr; ++r) {
@@ -366,7 +391,7 @@ struct ForwardOp {
             }
             for (int a = 0; a < nr; ++a)
                 for (int b = 0; b <= a; ++b) acc[a][b] = fma(ev[a] * iD, ev[b], acc[a][b]);
-            if (i + 1 < n) {
+            if (i + 1 < cr.end) {
                 const double* kgi = kg + i * J;
                 const double* f = F + (i + 1) * NB * 4;
                 for (int r = 0; r < nr; ++r) {
@@ -377,7 +402,7 @@ struct ForwardOp {
                 }
             }
         }
-        double* p = partial + c * NRMAX * NRMAX;
+        double* p = partial + gc * NRMAX * NRMAX;
         for (int a = 0; a < nr; ++a)
             for (int b = 0; b <= a; ++b) {
                 p[a * NRMAX + b] = acc[a][b];
@@ -397,14 +422,14 @@ struct BackwardOp {
     struct State {
         double g[NRMAX][J];
     };
+    const SegInfo* segs;
+    const int* chunk_seg;
     const double* F;
     const double* kg;
     const double* U;       // right-hand sides [n][nr]
-    int64_t n;
     int nr;
     int k;
     int B;
-    int64_t n_chunks;
     double* z0;
     double* Zt;            // [n][k]
 
@@ -414,18 +439,17 @@ struct BackwardOp {
 #pragma unroll
             for (int q = 0; q < J; ++q) st.g[r][q] = 0.0;
     }
-    __device__ void elem(int64_t q, Elem& El) const {
-        int64_t s, e;
-        chunk_range(n_chunks - 1 - q, B, n, s, e);
+    __device__ void elem(int64_t gc, Elem& El) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, true);
         mat_eye(El.Phi);
 #pragma unroll
         for (int r = 0; r < NRMAX; ++r)
 #pragma unroll
             for (int a = 0; a < J; ++a) El.beta[r][a] = 0.0;
-        for (int64_t i = e; i >= s && i >= 1; --i) {
+        for (int64_t i = cr.e; i >= cr.s && i > cr.base; --i) {
             const double* kgi = kg + i * J;
             const double* f = F + i * NB * 4;
-            // Phi <- F_i^T (Phi + h (-kg^T Phi))
+            // Phi <- F_i^T (Phi - h kg^T Phi)
 #pragma unroll
             for (int a = 0; a < J; ++a) {
                 double kp = 0.0;
@@ -456,10 +480,10 @@ struct BackwardOp {
             double out[J];
 #pragma unroll
             for (int a = 0; a < J; ++a) {
-                double t = ej.beta[r][a];
+                double v = ej.beta[r][a];
 #pragma unroll
-                for (int b = 0; b < J; ++b) t = fma(ej.Phi(a, b), ei.beta[r][b], t);
-                out[a] = t;
+                for (int b = 0; b < J; ++b) v = fma(ej.Phi(a, b), ei.beta[r][b], v);
+                out[a] = v;
             }
 #pragma unroll
             for (int a = 0; a < J; ++a) ei.beta[r][a] = out[a];
@@ -471,20 +495,19 @@ struct BackwardOp {
             double out[J];
 #pragma unroll
             for (int a = 0; a < J; ++a) {
-                double t = El.beta[r][a];
+                double v = El.beta[r][a];
 #pragma unroll
-                for (int b = 0; b < J; ++b) t = fma(El.Phi(a, b), st.g[r][b], t);
-                out[a] = t;
+                for (int b = 0; b < J; ++b) v = fma(El.Phi(a, b), st.g[r][b], v);
+                out[a] = v;
             }
 #pragma unroll
             for (int a = 0; a < J; ++a) st.g[r][a] = out[a];
         }
     }
-    __device__ void final(int64_t q, const State& st0) const {
-        int64_t s, e;
-        chunk_range(n_chunks - 1 - q, B, n, s, e);
+    __device__ void final(int64_t gc, const State& st0) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, true);
         State st = st0;
-        for (int64_t i = e; i >= s; --i) {
+        for (int64_t i = cr.e; i >= cr.s; --i) {
             const double* kgi = kg + i * J;
             const double* f = F + i * NB * 4;
             for (int r = 0; r < nr; ++r) {
@@ -492,7 +515,7 @@ struct BackwardOp {
 #pragma unroll
                 for (int b = 0; b < J; ++b) v = fma(-kgi[b], st.g[r][b], v);
                 if (r == 0) z0[i] = v; else Zt[i * k + (r - 1)] = v;
-                if (i >= 1) {
+                if (i > cr.base) {
                     double col[J];
 #pragma unroll
                     for (int b = 0; b < J; ++b) col[b] = st.g[r][b] + ((b % 2 == 0) ? v : 0.0);
@@ -514,12 +537,12 @@ struct FutureOp {
     struct State {
         Mat<J> G;
     };
+    const SegInfo* segs;
+    const int* chunk_seg;
     const double* F;
     const double* kg;
     const double* invD;
-    int64_t n;
     int B;
-    int64_t n_chunks;
     double* Gout;          // packed upper [n][JJ]
 
     // A_{i+1} = F_{i+1} (I - kg_i h^T) as a dense matrix
@@ -535,13 +558,12 @@ struct FutureOp {
             for (int b = 0; b < NB; ++b) A(r, 2 * b) -= fk[r];
     }
     __device__ void init_state(State& st) const { mat_zero(st.G); }
-    __device__ void elem(int64_t q, Elem& El) const {
-        int64_t s, e;
-        chunk_range(n_chunks - 1 - q, B, n, s, e);
+    __device__ void elem(int64_t gc, Elem& El) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, true);
         mat_eye(El.Psi);
         mat_zero(El.Gam);
-        for (int64_t i = e; i >= s; --i) {
-            if (i + 1 < n) {
+        for (int64_t i = cr.e; i >= cr.s; --i) {
+            if (i + 1 < cr.end) {
                 Mat<J> A, T;
                 closed_loop(i, A);
                 mat_mul(El.Psi, A, T);
@@ -578,12 +600,11 @@ struct FutureOp {
         mat_symmetrize(Gn);
         st.G = Gn;
     }
-    __device__ void final(int64_t q, const State& st0) const {
-        int64_t s, e;
-        chunk_range(n_chunks - 1 - q, B, n, s, e);
+    __device__ void final(int64_t gc, const State& st0) const {
+        const ChunkRange cr = chunk_of(segs, chunk_seg, gc, B, true);
         Mat<J> G = st0.G;
-        for (int64_t i = e; i >= s; --i) {
-            if (i + 1 < n) {
+        for (int64_t i = cr.e; i >= cr.s; --i) {
+            if (i + 1 < cr.end) {
                 Mat<J> A, T;
                 closed_loop(i, A);
                 mat_mul(G, A, T);

@@ -53,41 +53,24 @@ template <> struct Acc<double> {
     __device__ __forceinline__ double get() const { return s; }
 };
 
-template <typename T> struct FactorView {
-    const T* F;
-    const T* kg;
-    const T* invD;
-    const T* G;
-    const T* z0;
-    const T* Zt;
-};
 
-// One thread per (duration j, epoch i).
+// One window: the fit of template m(t0, D) against the factor of one light
+// curve (arrays already offset to the curve, n samples).
 template <int NB, typename T, int TMPL>
-__global__ void __launch_bounds__(128)
-k_window(const double* __restrict__ t, int64_t n, int k, FactorView<T> fv,
-         const double* __restrict__ t0s, int64_t n_t0, const double* __restrict__ Ds,
-         int n_D, double ingress_frac, T* __restrict__ out_depth, T* __restrict__ out_var,
-         T* __restrict__ out_dlnl) {
+__device__ __forceinline__ void window_fit(const double* __restrict__ t, int64_t n, int k,
+                                           const FactorView<T>& fv, double t0, double D,
+                                           double ingress_frac, T& out_d, T& out_v, T& out_l) {
     constexpr int J = Dims<NB>::J;
     constexpr int JJ = Dims<NB>::JJ;
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= n_t0 * (int64_t)n_D) return;
-    const int j = (int)(gid / n_t0);
-    const int64_t i = gid - (int64_t)j * n_t0;
-    const double t0 = t0s[i];
-    const double D = Ds[j];
     const double half = D * 0.5;
     // window of Sect. 2.1's box, half-open: t0 - D/2 <= t < t0 + D/2
     const int64_t lo = lower_bound_d(t, n, __dsub_rn(t0, half));
     const int64_t hi = lower_bound_d(t, n, __dadd_rn(t0, half));
     const T nanv = T(NAN);
-    if (hi <= lo) {
-        out_depth[gid] = nanv;
-        out_var[gid] = nanv;
-        out_dlnl[gid] = nanv;
-        return;
-    }
+    out_d = nanv;
+    out_v = nanv;
+    out_l = nanv;
+    if (hi <= lo) return;
     const double ramp = ingress_frac * D;
     T s[J];
 #pragma unroll
@@ -134,17 +117,65 @@ k_window(const double* __restrict__ t, int64_t n, int k, FactorView<T> fv,
     T bb = T(0);
     for (int a = 0; a < k; ++a) bb += bt[a].get() * bt[a].get();
     const T sch = cval - bb;
-    if (!(sch > T(0))) {
-        out_depth[gid] = nanv;
-        out_var[gid] = nanv;
-        out_dlnl[gid] = nanv;
-        return;
-    }
+    if (!(sch > T(0))) return;
     const T nm = num.get();
     const T dep = nm / sch;
-    out_depth[gid] = dep;
-    out_var[gid] = T(1) / sch;
-    out_dlnl[gid] = T(0.5) * nm * dep;
+    out_d = dep;
+    out_v = T(1) / sch;
+    out_l = T(0.5) * nm * dep;
+}
+
+template <int NB, typename T>
+__device__ __forceinline__ FactorView<T> view_at(const FactorView<T>& fv, int64_t s0, int k) {
+    constexpr int J = Dims<NB>::J;
+    constexpr int JJ = Dims<NB>::JJ;
+    return FactorView<T>{fv.F + s0 * NB * 4, fv.kg + s0 * J, fv.invD + s0, fv.G + s0 * JJ,
+                         fv.z0 + s0, fv.Zt + s0 * k};
+}
+
+// One thread per (duration j, epoch i) of one light curve.
+template <int NB, typename T, int TMPL>
+__global__ void __launch_bounds__(128)
+k_window(const double* __restrict__ t, int64_t n, int k, FactorView<T> fv,
+         const double* __restrict__ t0s, int64_t n_t0, const double* __restrict__ Ds,
+         int n_D, double ingress_frac, T* __restrict__ out_depth, T* __restrict__ out_var,
+         T* __restrict__ out_dlnl) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= n_t0 * (int64_t)n_D) return;
+    const int j = (int)(gid / n_t0);
+    const int64_t i = gid - (int64_t)j * n_t0;
+    T d, v, l;
+    window_fit<NB, T, TMPL>(t, n, k, fv, t0s[i], Ds[j], ingress_frac, d, v, l);
+    out_depth[gid] = d;
+    out_var[gid] = v;
+    out_dlnl[gid] = l;
+}
+
+// Several light curves packed back to back (segments), epochs = the curves'
+// own samples; outputs of curve g are [n_D][n_g] at n_D * s_off[g].
+template <int NB, typename T>
+__global__ void __launch_bounds__(128)
+k_window_batch(const double* __restrict__ t, int k, FactorView<T> fv,
+               const int64_t* __restrict__ s_off, int n_seg, const double* __restrict__ Ds,
+               int n_D, T* __restrict__ out_depth, T* __restrict__ out_var,
+               T* __restrict__ out_dlnl) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= s_off[n_seg] * (int64_t)n_D) return;
+    int lo = 0, hi = n_seg;                     // segment: n_D s_off[g] <= gid
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] * (int64_t)n_D <= gid) lo = mid; else hi = mid;
+    }
+    const int64_t s0 = s_off[lo], ng = s_off[lo + 1] - s0;
+    const int64_t w = gid - s0 * n_D;
+    const int j = (int)(w / ng);
+    const int64_t i = w - (int64_t)j * ng;
+    T d, v, l;
+    window_fit<NB, T, NU_BOX>(t + s0, ng, k, view_at<NB, T>(fv, s0, k), t[s0 + i], Ds[j], 0.1,
+                              d, v, l);
+    out_depth[gid] = d;
+    out_var[gid] = v;
+    out_dlnl[gid] = l;
 }
 
 template <int NB, typename T>
@@ -161,6 +192,35 @@ static void launch_window(const nu_factor* f, FactorView<T> fv, const double* t0
     else
         k_window<NB, T, NU_TRAPEZOID><<<blocks, th, 0, st>>>(
             f->t, f->n, f->k, fv, t0s, n_t0, Ds_dev, n_D, ingress, (T*)d, (T*)v, (T*)l);
+}
+
+// Linear search of packed light curves (batch path); no allocation, no sync.
+int launch_window_batch(int nb, bool fp64, const double* t, int k, const void* fv,
+                        const int64_t* s_off, int n_seg, int64_t n_total, const double* Ds,
+                        int n_D, void* d, void* v, void* l, cudaStream_t st) {
+    const int64_t total = n_total * (int64_t)n_D;
+    const int th = 128;
+    const int blocks = div_up(total, th);
+#define NU_WB(NB_, T_)                                                                   \
+    k_window_batch<NB_, T_><<<blocks, th, 0, st>>>(t, k, *(const FactorView<T_>*)fv, s_off, \
+                                                  n_seg, Ds, n_D, (T_*)d, (T_*)v, (T_*)l)
+    if (fp64) {
+        switch (nb) {
+            case 1: NU_WB(1, double); break;
+            case 2: NU_WB(2, double); break;
+            case 3: NU_WB(3, double); break;
+            default: NU_WB(4, double); break;
+        }
+    } else {
+        switch (nb) {
+            case 1: NU_WB(1, float); break;
+            case 2: NU_WB(2, float); break;
+            case 3: NU_WB(3, float); break;
+            default: NU_WB(4, float); break;
+        }
+    }
+#undef NU_WB
+    return 1;
 }
 
 }  // namespace nu

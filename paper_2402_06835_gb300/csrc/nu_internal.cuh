@@ -58,6 +58,21 @@ nu_status expand_terms(const nu_term* terms, int n_terms, Blocks* out);
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Per-sample factor arrays as read by the linear search (FP64 or FP32 copies).
+template <typename T> struct FactorView {
+    const T* F;
+    const T* kg;
+    const T* invD;
+    const T* G;
+    const T* z0;
+    const T* Zt;
+};
+
+// Linear search of packed light curves (batch path); no allocation, no sync.
+int launch_window_batch(int nb, bool fp64, const double* t, int k, const void* fv,
+                        const int64_t* s_off, int n_seg, int64_t n_total, const double* Ds,
+                        int n_D, void* d, void* v, void* l, cudaStream_t st);
+
 }  // namespace nu
 
 // Library-owned factor of one light curve.  All arrays are device memory

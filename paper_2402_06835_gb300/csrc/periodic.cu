@@ -20,6 +20,7 @@
 #include <cmath>
 #include <vector>
 
+#include "fold.cuh"
 #include "nu_internal.cuh"
 
 namespace nu {
@@ -46,14 +47,6 @@ __device__ __forceinline__ float lg2_32(float x) {
     return y;
 }
 
-// Node record of the single-event grid: depth, sigma = sqrt(var) (NaN when
-// any of depth/var/gain is not finite or var <= 0), gain, and ig = 1/(gap to
-// the next epoch) (NaN when there is no next epoch or the gap exceeds the
-// limit).  Interpolating with a NaN anywhere yields a NaN sigma, which is how
-// an epoch is dropped.
-template <typename T> struct __align__(4 * sizeof(T)) Node4 {
-    T d, s, l, ig;
-};
 
 struct FoldGeom {
     const double* t0s;
@@ -343,16 +336,18 @@ struct ExactPen {
     }
 };
 
+// One period P of one light curve: every (duration, phase) cell, then the
+// block argmax; results at index p of the outputs.  Called by all threads of
+// the block.
 template <typename T, int KC>
-__global__ void __launch_bounds__(256)
-k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
-             const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
-             double* __restrict__ T0_out, int* __restrict__ Didx_out,
-             double* __restrict__ dep_out, double* __restrict__ sig_out,
-             double* __restrict__ lnp_out) {
-    const int64_t p = blockIdx.x;
-    if (p >= n_P) return;
-    const double P = periods[p];
+__device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node4<T>* __restrict__ nodes,
+                                               int n_D, double P, int64_t p,
+                                               double* __restrict__ Q_out,
+                                               double* __restrict__ T0_out,
+                                               int* __restrict__ Didx_out,
+                                               double* __restrict__ dep_out,
+                                               double* __restrict__ sig_out,
+                                               double* __restrict__ lnp_out) {
     if (bad_period(P, g)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
@@ -370,10 +365,22 @@ k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
     double bl = -INFINITY;
     long long bc = LLONG_MAX;
     T bD = T(NAN), bs2 = T(NAN);
-    for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
-        const int d = (int)(cell / n_phi);
-        const int64_t j = cell - (int64_t)d * n_phi;
-        const double phi = (double)j / (double)n_phi;
+    // phase j / n_phi: reciprocal plus one FMA correction of the quotient
+    // (Markstein 1990), instead of a division per cell
+    const double nphi_d = (double)n_phi;
+    const double rphi = 1.0 / nphi_d;
+    // cells walk (duration, phase) incrementally: no 64-bit division per cell
+    int d = (int)(threadIdx.x / n_phi);
+    int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
+    for (int64_t cell = threadIdx.x; cell < n_cells;
+         cell += blockDim.x, j += blockDim.x) {
+        while (j >= n_phi) {
+            j -= n_phi;
+            ++d;
+        }
+        const double jd = (double)j;
+        const double q0 = jd * rphi;
+        const double phi = fma(fma(-q0, nphi_d, jd), rphi, q0);
         const Node4<T>* nd = nodes + (int64_t)d * g.n_t0;
         const unsigned long long u0 = (unsigned long long)j * swp.u0;
         // number of epochs with T <= t_last: integer estimate, then the exact
@@ -447,6 +454,19 @@ k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
         write_best(b, p, n_phi, g.t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
+template <typename T, int KC>
+__global__ void __launch_bounds__(256)
+k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
+             const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
+             double* __restrict__ T0_out, int* __restrict__ Didx_out,
+             double* __restrict__ dep_out, double* __restrict__ sig_out,
+             double* __restrict__ lnp_out) {
+    const int64_t p = blockIdx.x;
+    if (p >= n_P) return;
+    fold_exact_one<T, KC>(g, nodes, n_D, periods[p], p, Q_out, T0_out, Didx_out, dep_out,
+                          sig_out, lnp_out);
+}
+
 // ---------------------------------------- slot path (mixed, regular grids)
 // Epochs walk the slot grid in 24.40 fixed point: u = (T - t_ref)/dt =
 // (j/n_phi + k) P/dt.  The interval is (slot, slot+1) and the weight is the
@@ -514,15 +534,15 @@ struct SlotPass2 {
 // slot centres (checked to be below 1e-3 slot).  Cells with at most KC epochs
 // keep their events in registers for the second pass.
 template <int KC>
-__global__ void __launch_bounds__(256)
-k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, double dt,
-             double t_ref, double t_last, const double* __restrict__ periods, int64_t n_P,
-             double* __restrict__ Q_out, double* __restrict__ T0_out,
-             int* __restrict__ Didx_out, double* __restrict__ dep_out,
-             double* __restrict__ sig_out, double* __restrict__ lnp_out) {
-    const int64_t p = blockIdx.x;
-    if (p >= n_P) return;
-    const double P = periods[p];
+__device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ rec,
+                                               int64_t n_slots, int n_D, double dt,
+                                               double t_ref, double t_last, double P, int64_t p,
+                                               double* __restrict__ Q_out,
+                                               double* __restrict__ T0_out,
+                                               int* __restrict__ Didx_out,
+                                               double* __restrict__ dep_out,
+                                               double* __restrict__ sig_out,
+                                               double* __restrict__ lnp_out) {
     FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
     if (bad_period(P, gg)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
@@ -542,9 +562,14 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     float bl = -INFINITY, bD = NAN, bs2 = NAN;
     long long bc = LLONG_MAX;
-    for (int64_t cell = threadIdx.x; cell < n_cells; cell += blockDim.x) {
-        const int d = (int)(cell / n_phi);
-        const int64_t j = cell - (int64_t)d * n_phi;
+    int d = (int)(threadIdx.x / n_phi);
+    int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
+    for (int64_t cell = threadIdx.x; cell < n_cells;
+         cell += blockDim.x, j += blockDim.x) {
+        while (j >= n_phi) {
+            j -= n_phi;
+            ++d;
+        }
         const unsigned long long u0 = (unsigned long long)j * uph;
         if (u0 > ulast) continue;
         int64_t kk = (int64_t)((float)(ulast - u0) * inv_ustep);
@@ -600,6 +625,257 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
     const Best b = block_argmax(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
+}
+
+template <int KC>
+__global__ void __launch_bounds__(256)
+k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, double dt,
+             double t_ref, double t_last, const double* __restrict__ periods, int64_t n_P,
+             double* __restrict__ Q_out, double* __restrict__ T0_out,
+             int* __restrict__ Didx_out, double* __restrict__ dep_out,
+             double* __restrict__ sig_out, double* __restrict__ lnp_out) {
+    const int64_t p = blockIdx.x;
+    if (p >= n_P) return;
+    fold_slots_one<KC>(rec, n_slots, n_D, dt, t_ref, t_last, periods[p], p, Q_out, T0_out,
+                       Didx_out, dep_out, sig_out, lnp_out);
+}
+
+// ------------------------------------------------------------ batch path
+
+// Persistent fold over (curve, period) work items taken from a device
+// counter (no waits: a block takes items until none are left).  kind 0: the
+// exact FP64-epoch path with FP64 values; 1: exact path, FP32 values;
+// 2: slot path (mixed precision, regular grids).  Items of curves that do not
+// use this kernel's path are skipped.
+template <int KIND>
+__global__ void __launch_bounds__(256)
+k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restrict__ t,
+             const void* __restrict__ nodes, const int* __restrict__ bucket,
+             const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
+             const double* __restrict__ periods, int64_t n_P, unsigned long long* counter,
+             double* __restrict__ Q_out, double* __restrict__ T0_out,
+             int* __restrict__ Didx_out, double* __restrict__ dep_out,
+             double* __restrict__ sig_out, double* __restrict__ lnp_out) {
+    __shared__ unsigned long long item_sh;
+    const unsigned long long total = (unsigned long long)n_seg * (unsigned long long)n_P;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1ull);
+        __syncthreads();
+        const unsigned long long item = item_sh;
+        if (item >= total) break;
+        const int g = (int)(item / (unsigned long long)n_P);
+        const int64_t p = (int64_t)(item % (unsigned long long)n_P);
+        const FoldSeg fs = segs[g];
+        if ((KIND == 2) != (fs.use_slots != 0)) continue;
+        const int64_t o = (int64_t)g * n_P + p;
+        if (KIND == 2) {
+            fold_slots_one<8>(rec + fs.rec_off, fs.n_slots, n_D, dt, fs.t_ref, fs.t_last,
+                              periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
+                              lnp_out);
+        } else {
+            FoldGeom gg{t + fs.s_off, fs.n_t0, fs.t_ref, fs.t_last, dt, 1.0 / dt,
+                        gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
+            if (KIND == 0)
+                fold_exact_one<double, 8>(gg, (const Node4<double>*)nodes + fs.s_off * n_D,
+                                          n_D, periods[p], o, Q_out, T0_out, Didx_out,
+                                          dep_out, sig_out, lnp_out);
+            else
+                fold_exact_one<float, 8>(gg, (const Node4<float>*)nodes + fs.s_off * n_D, n_D,
+                                         periods[p], o, Q_out, T0_out, Didx_out, dep_out,
+                                         sig_out, lnp_out);
+        }
+    }
+}
+
+// Per-curve node records (exact path) and bucket tables; slot tables.
+template <typename T>
+__global__ void k_nodes_batch(const T* __restrict__ depth, const T* __restrict__ var,
+                              const T* __restrict__ gain, const double* __restrict__ t,
+                              const FoldSeg* __restrict__ segs, int n_seg,
+                              const int64_t* __restrict__ s_off, int n_D, double gap_max,
+                              Node4<T>* __restrict__ nodes) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= s_off[n_seg] * (int64_t)n_D) return;
+    int lo = 0, hi = n_seg;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] * (int64_t)n_D <= gid) lo = mid; else hi = mid;
+    }
+    const int64_t s0 = s_off[lo], ng = s_off[lo + 1] - s0;
+    const int64_t i = (gid - s0 * n_D) % ng;
+    const T d = depth[gid], v = var[gid], l = gain[gid];
+    Node4<T> r;
+    r.d = d;
+    r.l = l;
+    r.s = (isfinite(d) && isfinite(v) && isfinite(l) && v > T(0)) ? sqrt(v) : T(NAN);
+    T ig = T(NAN);
+    if (i + 1 < ng) {
+        const double gap = t[s0 + i + 1] - t[s0 + i];
+        if (gap <= gap_max && gap > 0.0) ig = (T)(1.0 / gap);
+    }
+    r.ig = ig;
+    nodes[gid] = r;
+}
+
+__global__ void k_buckets_batch(const double* __restrict__ t, const FoldSeg* __restrict__ segs,
+                                int n_seg, int64_t n_bucket_total, double dt,
+                                int* __restrict__ bucket) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n_bucket_total) return;
+    int lo = 0, hi = n_seg;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (segs[mid].bucket_off <= b) lo = mid; else hi = mid;
+    }
+    const FoldSeg fs = segs[lo];
+    const double edge = fs.t_ref + (double)(b - fs.bucket_off) * dt;
+    const double* t0 = t + fs.s_off;
+    int64_t l = 0, h = fs.n_t0;
+    while (l < h) {
+        const int64_t mid = (l + h) >> 1;
+        if (t0[mid] <= edge) l = mid + 1; else h = mid;
+    }
+    bucket[b] = (int)l;
+}
+
+__global__ void k_slot_fill_batch(const float* __restrict__ depth, const float* __restrict__ var,
+                                  const float* __restrict__ gain, const double* __restrict__ t,
+                                  const FoldSeg* __restrict__ segs, int n_seg,
+                                  const int64_t* __restrict__ s_off, int n_D, double inv_dt,
+                                  Node4<float>* __restrict__ rec) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= s_off[n_seg] * (int64_t)n_D) return;
+    int lo = 0, hi = n_seg;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] * (int64_t)n_D <= gid) lo = mid; else hi = mid;
+    }
+    const FoldSeg fs = segs[lo];
+    if (!fs.use_slots) return;
+    const int64_t s0 = s_off[lo], ng = s_off[lo + 1] - s0;
+    const int64_t w = gid - s0 * n_D;
+    const int64_t d = w / ng, i = w - d * ng;
+    const int64_t s = (int64_t)rint((t[s0 + i] - fs.t_ref) * inv_dt);
+    if (s < 0 || s >= fs.n_slots) return;
+    const float dd = depth[gid], v = var[gid], l = gain[gid];
+    Node4<float> r;
+    r.d = dd;
+    r.l = l;
+    r.s = (isfinite(dd) && isfinite(v) && isfinite(l) && v > 0.f) ? sqrtf(v) : NAN;
+    r.ig = 0.f;
+    rec[fs.rec_off + d * fs.n_slots + s] = r;
+}
+
+// Regularity of each curve's epochs for the slot path (flag[g] = 1 if not).
+__global__ void k_slots_batch(const double* __restrict__ t, const int64_t* __restrict__ s_off,
+                              int n_seg, double inv_dt, int* __restrict__ irregular) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= s_off[n_seg]) return;
+    int lo = 0, hi = n_seg;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int64_t s0 = s_off[lo];
+    const double tr = t[s0];
+    const double u = (t[i] - tr) * inv_dt;
+    const double sl = rint(u);
+    bool bad = !(fabs(u - sl) <= 1e-3) || !(sl >= 0.0) || sl > 2.0e9;
+    if (i > s0) bad = bad || !(sl > rint((t[i - 1] - tr) * inv_dt));
+    if (bad) atomicExch(&irregular[lo], 1);
+}
+
+// Host side of the batch fold: per-curve layout and launches.
+
+void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double>& t_first,
+                     const std::vector<double>& t_last, const std::vector<int>& irregular,
+                     bool fp64, double dt, double gap_factor, int n_D, FoldBatch& fb) {
+    const int n_seg = (int)t_first.size();
+    fb.segs.resize(n_seg);
+    for (int g = 0; g < n_seg; ++g) {
+        FoldSeg& f = fb.segs[g];
+        f.s_off = s_off[g];
+        f.n_t0 = s_off[g + 1] - s_off[g];
+        f.t_ref = t_first[g];
+        f.t_last = t_last[g];
+        const double span = (t_last[g] - t_first[g]) / dt;
+        f.n_bucket = (int64_t)span + 2;
+        f.n_slots = f.n_bucket + 2;
+        f.use_slots = (!fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span < 4.0e6 &&
+                       !irregular[g]) ? 1 : 0;
+        f.bucket_off = fb.n_bucket_total;
+        fb.n_bucket_total += f.use_slots ? 0 : f.n_bucket;
+        f.rec_off = fb.n_rec_total;
+        fb.n_rec_total += f.use_slots ? f.n_slots * n_D : 0;
+        fb.any_slots = fb.any_slots || f.use_slots;
+        fb.any_exact = fb.any_exact || !f.use_slots;
+    }
+}
+
+int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t* s_off_dev,
+                     int n_seg, int64_t n_total, bool fp64, const double* t, const void* depth,
+                     const void* var, const void* gain, int n_D, double dt, double gap_factor,
+                     void* nodes, int* bucket, Node4<float>* rec, cudaStream_t st) {
+    int launched = 0;
+    const int64_t ngrid = n_total * (int64_t)n_D;
+    if (fb.any_exact) {
+        if (fp64)
+            k_nodes_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
+                n_seg, s_off_dev, n_D, gap_factor * dt, (Node4<double>*)nodes);
+        else
+            k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
+                s_off_dev, n_D, gap_factor * dt, (Node4<float>*)nodes);
+        k_buckets_batch<<<div_up(fb.n_bucket_total, 256), 256, 0, st>>>(
+            t, segs_dev, n_seg, fb.n_bucket_total, dt, bucket);
+        launched += 2;
+    }
+    if (fb.any_slots) {
+        k_fill_nan<<<div_up(fb.n_rec_total, 256), 256, 0, st>>>(rec, fb.n_rec_total);
+        k_slot_fill_batch<<<div_up(ngrid, 256), 256, 0, st>>>(
+            (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
+            s_off_dev, n_D, 1.0 / dt, rec);
+        launched += 2;
+    }
+    return launched;
+}
+
+// The persistent fold kernels; counter[0..1] must be zero.  blocks_per_sm
+// and threads come from the autotuner.
+int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg, bool fp64,
+                      const double* t, const void* nodes, const int* bucket,
+                      const Node4<float>* rec, int n_D, double dt, double gap_factor,
+                      const double* periods, int64_t n_P, unsigned long long* counter,
+                      int grid, int threads, double* Q, double* T0, int* Didx, double* dep,
+                      double* sig, double* lnp, cudaStream_t st) {
+    int launched = 0;
+    if (fb.any_exact) {
+        if (fp64)
+            k_fold_batch<0><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, bucket, rec,
+                                                      n_D, dt, gap_factor, periods, n_P,
+                                                      counter, Q, T0, Didx, dep, sig, lnp);
+        else
+            k_fold_batch<1><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, bucket, rec,
+                                                      n_D, dt, gap_factor, periods, n_P,
+                                                      counter, Q, T0, Didx, dep, sig, lnp);
+        ++launched;
+    }
+    if (fb.any_slots) {
+        k_fold_batch<2><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, bucket, rec, n_D,
+                                                  dt, gap_factor, periods, n_P, counter + 1, Q,
+                                                  T0, Didx, dep, sig, lnp);
+        ++launched;
+    }
+    return launched;
+}
+
+int launch_slots_test(const double* t, const int64_t* s_off_dev, int n_seg, int64_t n_total,
+                      double dt, int* irregular, cudaStream_t st) {
+    k_slots_batch<<<div_up(n_total, 256), 256, 0, st>>>(t, s_off_dev, n_seg, 1.0 / dt,
+                                                       irregular);
+    return 1;
 }
 
 }  // namespace nu
@@ -736,22 +1012,4 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
     e = cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: cudaFreeAsync");
     return NU_OK;
-}
-
-extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
-                                     const double* t_dev, const double* y_dev,
-                                     const double* diag_var_dev,
-                                     const nu_term* terms_host, const int* n_terms_host,
-                                     int k, const double* Ds_host, int n_D,
-                                     const double* periods_dev, int64_t n_P,
-                                     double phase_step, nu_precision prec, void* stream,
-                                     double* Q_dev, double* T0_dev, int32_t* D_idx_dev,
-                                     double* depth_out_dev, double* sigma_out_dev,
-                                     double* lnP_dev, int* status_host) {
-    (void)n_lc; (void)offsets_host; (void)t_dev; (void)y_dev; (void)diag_var_dev;
-    (void)terms_host; (void)n_terms_host; (void)k; (void)Ds_host; (void)n_D;
-    (void)periods_dev; (void)n_P; (void)phase_step; (void)prec; (void)stream; (void)Q_dev;
-    (void)T0_dev; (void)D_idx_dev; (void)depth_out_dev; (void)sigma_out_dev; (void)lnP_dev;
-    (void)status_host;
-    return fail(NU_EINVAL, "nu_batch_search: not built yet");
 }

@@ -20,10 +20,18 @@
 // functions; Elem and State are plain structs.
 #pragma once
 
+#include <algorithm>
+#include <vector>
+
 #include "nu_internal.cuh"
 
 namespace nu {
 
+// Segments: several independent recursions (light curves) share one scan.
+// Level-0 elements are the chunks of all segments, segment after segment;
+// level l+1 element q composes the level-l elements [child_begin, child_end)
+// of the same segment; the top level holds, per segment, the elements
+// [top_begin, top_end).  A single light curve is one segment.
 template <class Op>
 __global__ void k_scan_elem(Op op, int64_t n_chunks, typename Op::Elem* __restrict__ E) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -32,41 +40,41 @@ __global__ void k_scan_elem(Op op, int64_t n_chunks, typename Op::Elem* __restri
 }
 
 template <class Op>
-__global__ void k_scan_combine(Op op, const typename Op::Elem* __restrict__ Ein, int64_t n_in,
-                               int G, typename Op::Elem* __restrict__ Eout) {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t q0 = g * G;
-    if (q0 >= n_in) return;
-    typename Op::Elem acc = Ein[q0];
-    const int64_t q1 = q0 + G < n_in ? q0 + G : n_in;
-    for (int64_t q = q0 + 1; q < q1; ++q) op.combine(acc, Ein[q]);
-    Eout[g] = acc;
+__global__ void k_scan_combine(Op op, const typename Op::Elem* __restrict__ Ein,
+                               const int64_t* __restrict__ cb, const int64_t* __restrict__ ce,
+                               int64_t n_out, typename Op::Elem* __restrict__ Eout) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_out) return;
+    typename Op::Elem acc = Ein[cb[q]];
+    for (int64_t r = cb[q] + 1; r < ce[q]; ++r) op.combine(acc, Ein[r]);
+    Eout[q] = acc;
 }
 
 template <class Op>
-__global__ void k_scan_top(Op op, const typename Op::Elem* __restrict__ E, int64_t n,
-                           typename Op::State* __restrict__ S) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+__global__ void k_scan_top(Op op, const typename Op::Elem* __restrict__ E,
+                           const int64_t* __restrict__ tb, const int64_t* __restrict__ te,
+                           int n_seg, typename Op::State* __restrict__ S) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_seg) return;
     typename Op::State s;
     op.init_state(s);
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t i = tb[g]; i < te[g]; ++i) {
         S[i] = s;
         op.apply(E[i], s);
     }
 }
 
 template <class Op>
-__global__ void k_scan_down(Op op, const typename Op::Elem* __restrict__ E, int64_t n, int G,
-                            const typename Op::State* __restrict__ Sparent,
+__global__ void k_scan_down(Op op, const typename Op::Elem* __restrict__ E,
+                            const int64_t* __restrict__ cb, const int64_t* __restrict__ ce,
+                            int64_t n_parent, const typename Op::State* __restrict__ Sparent,
                             typename Op::State* __restrict__ S) {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t q0 = g * G;
-    if (q0 >= n) return;
-    typename Op::State s = Sparent[g];
-    const int64_t q1 = q0 + G < n ? q0 + G : n;
-    for (int64_t q = q0; q < q1; ++q) {
-        S[q] = s;
-        op.apply(E[q], s);
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_parent) return;
+    typename Op::State s = Sparent[q];
+    for (int64_t r = cb[q]; r < ce[q]; ++r) {
+        S[r] = s;
+        op.apply(E[r], s);
     }
 }
 
@@ -77,66 +85,119 @@ __global__ void k_scan_final(Op op, int64_t n_chunks, const typename Op::State* 
     op.final(c, S[c]);
 }
 
-// Workspace layout of one scan (byte sizes, 256-aligned).
-struct ScanPlan {
-    int64_t n_chunks;
-    int G;
-    int levels;              // number of combine levels
-    int64_t count[16];       // elements per level (level 0 = chunks)
-    size_t elem_off[16];
-    size_t state_off[16];
-    size_t bytes;
+// Host-side construction of the level structure for segments with nc[l]
+// chunks each.  idx receives the int64 index arrays (child ranges per level,
+// then top ranges); the caller uploads them and fills the pointers.
+struct ScanShape {
+    int levels;
+    int n_seg;
+    int64_t count[16];
+    size_t child_off[16];      // offset (in int64 entries) of child_begin of level l
+    size_t top_off;            // offset of top_begin; top_end follows
+    size_t n_index;            // total int64 entries
 };
 
-template <class Op>
-inline ScanPlan plan_scan(int64_t n_chunks, int G, int top) {
-    ScanPlan p{};
-    p.n_chunks = n_chunks;
-    p.G = G;
-    p.count[0] = n_chunks;
-    int l = 0;
-    while (p.count[l] > top && l < 14) {
-        p.count[l + 1] = (p.count[l] + G - 1) / G;
-        ++l;
+inline ScanShape build_scan_shape(const int64_t* nc, int n_seg, int G, int top,
+                                  int64_t* idx /* null: only size the arrays */) {
+    ScanShape sh{};
+    sh.n_seg = n_seg;
+    std::vector<int64_t> cnt(nc, nc + n_seg);       // per-segment count, current level
+    int64_t total = 0, cur_max = 0;
+    for (int g = 0; g < n_seg; ++g) {
+        total += cnt[g];
+        cur_max = std::max(cur_max, cnt[g]);
     }
-    p.levels = l;
-    size_t off = 0;
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    for (int i = 0; i <= l; ++i) {
-        p.elem_off[i] = off;
-        off += al((size_t)p.count[i] * sizeof(typename Op::Elem));
-        p.state_off[i] = off;
-        off += al((size_t)p.count[i] * sizeof(typename Op::State));
+    sh.count[0] = total;
+    size_t pos = 0;
+    int levels = 0;
+    while (cur_max > top && levels < 14) {
+        const int l = ++levels;
+        int64_t out_total = 0;
+        for (int g = 0; g < n_seg; ++g) out_total += (cnt[g] + G - 1) / G;
+        sh.child_off[l] = pos;
+        sh.count[l] = out_total;
+        int64_t q_out = 0, in_off = 0;
+        for (int g = 0; g < n_seg; ++g) {
+            const int64_t nout = (cnt[g] + G - 1) / G;
+            for (int64_t q = 0; q < nout; ++q, ++q_out) {
+                if (idx) {
+                    idx[pos + q_out] = in_off + q * G;                           // begin
+                    idx[pos + out_total + q_out] = in_off + std::min((q + 1) * G, cnt[g]);
+                }
+            }
+            in_off += cnt[g];
+            cnt[g] = nout;
+        }
+        pos += 2 * (size_t)out_total;
+        cur_max = 0;
+        for (int g = 0; g < n_seg; ++g) cur_max = std::max(cur_max, cnt[g]);
     }
-    p.bytes = off;
-    return p;
+    sh.levels = levels;
+    sh.top_off = pos;
+    int64_t off = 0;
+    for (int g = 0; g < n_seg; ++g) {
+        if (idx) {
+            idx[pos + g] = off;
+            idx[pos + n_seg + g] = off + cnt[g];
+        }
+        off += cnt[g];
+    }
+    sh.n_index = pos + 2 * (size_t)n_seg;
+    return sh;
 }
 
-// Enqueue the whole scan on `st`; returns the number of kernel launches.
+// Device workspace of one scan: elements and states of every level.
 template <class Op>
-inline int run_scan(const Op& op, const ScanPlan& p, char* ws, cudaStream_t st) {
+inline size_t scan_bytes(const ScanShape& sh) {
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t off = 0;
+    for (int l = 0; l <= sh.levels; ++l) {
+        off += al((size_t)sh.count[l] * sizeof(typename Op::Elem));
+        off += al((size_t)sh.count[l] * sizeof(typename Op::State));
+    }
+    return off;
+}
+
+// Enqueue the whole scan on `st`; idx_dev holds the uploaded index arrays.
+// Returns the number of kernel launches.
+template <class Op>
+inline int run_scan(const Op& op, const ScanShape& sh, const int64_t* idx_dev, char* ws,
+                    cudaStream_t st) {
     using E = typename Op::Elem;
     using S = typename Op::State;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    E* Ep[16];
+    S* Sp[16];
+    size_t off = 0;
+    for (int l = 0; l <= sh.levels; ++l) {
+        Ep[l] = (E*)(ws + off);
+        off += al((size_t)sh.count[l] * sizeof(E));
+        Sp[l] = (S*)(ws + off);
+        off += al((size_t)sh.count[l] * sizeof(S));
+    }
     const int TH = 64;
     int launches = 0;
-    k_scan_elem<Op><<<div_up(p.n_chunks, TH), TH, 0, st>>>(op, p.n_chunks, (E*)(ws + p.elem_off[0]));
+    k_scan_elem<Op><<<div_up(sh.count[0], TH), TH, 0, st>>>(op, sh.count[0], Ep[0]);
     ++launches;
-    for (int l = 0; l < p.levels; ++l) {
-        k_scan_combine<Op><<<div_up(p.count[l + 1], TH), TH, 0, st>>>(
-            op, (const E*)(ws + p.elem_off[l]), p.count[l], p.G, (E*)(ws + p.elem_off[l + 1]));
+    for (int l = 1; l <= sh.levels; ++l) {
+        const int64_t* cb = idx_dev + sh.child_off[l];
+        const int64_t* ce = cb + sh.count[l];
+        k_scan_combine<Op><<<div_up(sh.count[l], TH), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
+                                                                 sh.count[l], Ep[l]);
         ++launches;
     }
-    k_scan_top<Op><<<1, 32, 0, st>>>(op, (const E*)(ws + p.elem_off[p.levels]),
-                                     p.count[p.levels], (S*)(ws + p.state_off[p.levels]));
+    const int64_t* tb = idx_dev + sh.top_off;
+    k_scan_top<Op><<<div_up(sh.n_seg, 32), 32, 0, st>>>(op, Ep[sh.levels], tb, tb + sh.n_seg,
+                                                       sh.n_seg, Sp[sh.levels]);
     ++launches;
-    for (int l = p.levels - 1; l >= 0; --l) {
-        k_scan_down<Op><<<div_up(p.count[l + 1], TH), TH, 0, st>>>(
-            op, (const E*)(ws + p.elem_off[l]), p.count[l], p.G,
-            (const S*)(ws + p.state_off[l + 1]), (S*)(ws + p.state_off[l]));
+    for (int l = sh.levels; l >= 1; --l) {
+        const int64_t* cb = idx_dev + sh.child_off[l];
+        const int64_t* ce = cb + sh.count[l];
+        k_scan_down<Op><<<div_up(sh.count[l], TH), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
+                                                              sh.count[l], Sp[l], Sp[l - 1]);
         ++launches;
     }
-    k_scan_final<Op><<<div_up(p.n_chunks, TH), TH, 0, st>>>(op, p.n_chunks,
-                                                          (const S*)(ws + p.state_off[0]));
+    k_scan_final<Op><<<div_up(sh.count[0], TH), TH, 0, st>>>(op, sh.count[0], Sp[0]);
     ++launches;
     return launches;
 }

@@ -1,0 +1,95 @@
+"""GPU tests of the batched survey search (nu_batch_search).
+
+The batch runs the same kernel bodies as the single-curve calls on packed
+curves, so in FP64 its results must equal those of one nu_gp_factor +
+nu_linear_search + nu_periodic_search per curve; two curves are also checked
+against the oracle (FP64 1e-9, mixed 1e-3 absolute on Q), and a curve whose
+times are unsorted must fail alone.
+"""
+import numpy as np
+import pytest
+
+from oracle import linear, periodic
+from paper_2402_06835_gb300 import synth
+from parity import FP64_TOL, MIXED_SNR_ABS, periodic_compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2402_06835_gb300 import api  # noqa: E402
+
+DS = np.array([0.02, 0.045, 0.07])
+PERIODS = np.linspace(0.11, 0.9, 157)
+
+
+def _curves():
+    out = []
+    for c, (n, gap, p_rot, sig) in enumerate([(300, None, 0.4, 1e-2), (520, 40, 0.9, 2e-2),
+                                               (410, 25, 0.2, 5e-3), (677, 90, 1.7, 3e-2),
+                                               (333, None, 0.6, 8e-3)]):
+        out.append(synth.small_curve(n=n, seed=100 + c, p_rot=p_rot, sigma=sig, gap=gap,
+                                     inject=(2.5e-3, 1.0 / 24.0, 0.37)))
+    return out
+
+
+def _single(lc, precision, dt):
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    f = api.nu_gp_factor(cu(lc.t), cu(lc.diag_var), lc.terms, cu(lc.X), cu(lc.y))
+    d, v, l = api.nu_linear_search(f, cu(lc.t), DS, precision=precision)
+    r = api.nu_periodic_search(cu(lc.t), DS, d, v, l, cu(PERIODS), precision=precision,
+                               phase_step=dt)
+    return {k: x.cpu().numpy() for k, x in r.items()}
+
+
+@pytest.fixture(scope="module")
+def curves():
+    return _curves()
+
+
+def test_batch_fp64_equals_single_curve_calls(curves):
+    dt = synth.CADENCE_DAYS
+    res = api.nu_batch_search([(lc.t, lc.y, lc.diag_var, lc.terms) for lc in curves], DS,
+                              PERIODS, k=2, precision="fp64", phase_step=dt)
+    assert res["status"] == [0] * len(curves)
+    for c, lc in enumerate(curves):
+        one = _single(lc, "fp64", dt)
+        assert np.array_equal(res["D_idx"][c].cpu().numpy(), one["D_idx"])
+        for key in ("Q", "T0", "lnP", "depth", "sigma"):
+            a, b = res[key][c].cpu().numpy(), one[key]
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=0, err_msg=key)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_against_oracle(curves, precision):
+    dt = synth.CADENCE_DAYS
+    res = api.nu_batch_search([(lc.t, lc.y, lc.diag_var, lc.terms) for lc in curves], DS,
+                              PERIODS, k=2, precision=precision, phase_step=dt)
+    for c in (1, 3):
+        lc = curves[c]
+        g = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t, DS)
+        ora = periodic.periodic_search(lc.t, g["depth"], g["var"], g["dlnl"], PERIODS, dt)
+        gpu = {k: res[k][c].cpu().numpy() for k in ("Q", "T0", "D_idx", "depth", "sigma", "lnP")}
+        if precision == "fp64":
+            wl, wq, dif = periodic_compare(gpu, ora, lc.t, g["depth"], g["var"], g["dlnl"],
+                                           PERIODS, dt, FP64_TOL, FP64_TOL, periodic.fold_period)
+        else:
+            wl, wq, dif = periodic_compare(gpu, ora, lc.t, g["depth"], g["var"], g["dlnl"],
+                                           PERIODS, dt, 1e-4, MIXED_SNR_ABS,
+                                           periodic.fold_period, max_reeval=len(PERIODS),
+                                           q_abs=True)
+        print(f"batch {precision} curve {c}: lnP err {wl:.2e} Q err {wq:.2e} ties {dif}")
+
+
+def test_batch_reports_a_failing_curve_alone(curves):
+    dt = synth.CADENCE_DAYS
+    bad = curves[2]
+    t = bad.t.copy()
+    t[100], t[101] = t[101], t[100]
+    items = [(lc.t, lc.y, lc.diag_var, lc.terms) for lc in curves]
+    items[2] = (t, bad.y, bad.diag_var, bad.terms)
+    res = api.nu_batch_search(items, DS, PERIODS, k=2, precision="fp64", phase_step=dt)
+    st = res["status"]
+    assert st[2] != 0 and all(s == 0 for i, s in enumerate(st) if i != 2)
