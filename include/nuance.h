@@ -180,6 +180,41 @@ nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
                              double* depth_out_dev, double* sigma_out_dev,
                              double* lnP_dev);
 
+/* Periodic search without device allocation (no counterpart in the paper).
+ *
+ * Same inputs, outputs and results as nu_periodic_search, for callers that
+ * cannot allocate device memory while they run: a runtime that reserves all
+ * of its device memory up front, a plugin whose host framework forbids
+ * allocation inside a step, or a process already at its memory limit where a
+ * mid-run allocation could fail.  The scratch (packed epoch records, lookup
+ * tables) lives in a fixed array of NU_NOALLOC_SCRATCH_LIMIT bytes inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits; grids that need more return NU_EINVAL (nu_periodic_search handles
+ * them).  This call makes no cudaMalloc/cudaFree or other allocating call.
+ *   - phase_step must be > 0 (the median-spacing default would need a host
+ *     buffer).
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents; the call clears what must start at zero.  Calls whose
+ *     work overlaps on the GPU (different streams, threads or processes using
+ *     the same library image) race on it: serialise them.
+ * Errors: as nu_periodic_search, plus NU_EINVAL when the grid needs more
+ * scratch than the limit. */
+#define NU_NOALLOC_SCRATCH_LIMIT (32ull << 20)
+nu_status nu_periodic_search_noalloc(const double* t0s_dev, int64_t n_t0,
+                                     const double* Ds_host, int n_D,
+                                     const void* depth_dev, const void* var_dev,
+                                     const void* dlnl_dev, nu_precision prec,
+                                     const double* periods_dev, int64_t n_P,
+                                     double phase_step, double gap_factor, void* stream,
+                                     double* Q_dev, double* T0_dev, int32_t* D_idx_dev,
+                                     double* depth_out_dev, double* sigma_out_dev,
+                                     double* lnP_dev);
+
+/* Scratch limit of nu_periodic_search_noalloc in bytes. */
+uint64_t nu_periodic_search_noalloc_limit(void);
+
 /* Batched survey search: factor, linear search (box template, t0s = the
  * sample times of each curve) and periodic search for n_lc light curves of
  * uneven length packed back to back, launched as one graph on `stream`.

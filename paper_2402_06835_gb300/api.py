@@ -56,6 +56,9 @@ def _load():
     lib.nu_linear_search.argtypes = [P, P, I64, P, I, I, D, I, P, P, P, P]
     lib.nu_periodic_search.argtypes = [P, I64, P, I, P, P, P, I, P, I64, D, D, P,
                                        P, P, P, P, P, P]
+    lib.nu_periodic_search_noalloc.argtypes = lib.nu_periodic_search.argtypes
+    lib.nu_periodic_search_noalloc.restype = I
+    lib.nu_periodic_search_noalloc_limit.restype = ctypes.c_uint64
     lib.nu_batch_search.argtypes = [I, P, P, P, P, ctypes.POINTER(nu_term), P, I, P, I,
                                     P, I64, D, I, P, P, P, P, P, P, P, P]
     lib.nu_batch_search.restype = I
@@ -222,6 +225,20 @@ def nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision="fp64",
                                 _p(res["sigma"]), _p(res["lnP"]))
     _check(st, "nu_periodic_search")
     return res
+
+
+def nu_periodic_search_noalloc(t0s, Ds, depth, var, dlnl, periods, precision="fp64",
+                               phase_step=0.0, gap_factor=1.5, stream=None):
+    """nu_periodic_search with the library's fixed scratch array (no device
+    allocation inside the library call; phase_step must be > 0).  The output
+    tensors are still allocated here, by the caller side of the ABI."""
+    return nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision=precision,
+                              phase_step=phase_step, gap_factor=gap_factor, stream=stream,
+                              _entry=LIB.nu_periodic_search_noalloc)
+
+
+def nu_periodic_search_noalloc_limit():
+    return int(LIB.nu_periodic_search_noalloc_limit())
 
 
 def nu_batch_search(curves, Ds, periods, k=2, precision="fp64", phase_step=None,

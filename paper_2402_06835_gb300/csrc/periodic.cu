@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "fold.cuh"
@@ -1011,5 +1012,157 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: launch");
     e = cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: cudaFreeAsync");
+    return NU_OK;
+}
+
+// ------------------------------------------------ allocation-free variant
+// nu_periodic_search_noalloc runs the same kernels as nu_periodic_search but
+// takes its scratch (packed epoch records, bucket table, slot table, flag)
+// from the file-scope device array below instead of the stream-ordered pool,
+// for callers that must not allocate device memory.  The array is part of the
+// library image: every GPU that loads the library holds it until the process
+// exits.  Its address is looked up once per device (cudaGetSymbolAddress with
+// that device current) on the first call made on the device.
+#define NU_NOALLOC_SCRATCH_BYTES (32ull << 20)
+
+static __device__ __align__(256) unsigned char g_fold_scratch[NU_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[64] = {};
+}
+
+static nu_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_fold_scratch);
+        if (e != cudaSuccess || !p)
+            return cuda_fail(e, "nu_periodic_search_noalloc: cudaGetSymbolAddress");
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return NU_OK;
+}
+
+extern "C" uint64_t nu_periodic_search_noalloc_limit(void) { return NU_NOALLOC_SCRATCH_BYTES; }
+
+extern "C" nu_status nu_periodic_search_noalloc(const double* t0s_dev, int64_t n_t0,
+                                                const double* Ds_host, int n_D,
+                                                const void* depth_dev, const void* var_dev,
+                                                const void* dlnl_dev, nu_precision prec,
+                                                const double* periods_dev, int64_t n_P,
+                                                double phase_step, double gap_factor,
+                                                void* stream, double* Q_dev, double* T0_dev,
+                                                int32_t* D_idx_dev, double* depth_out_dev,
+                                                double* sigma_out_dev, double* lnP_dev) {
+    (void)Ds_host;
+    if (!t0s_dev || !depth_dev || !var_dev || !dlnl_dev || !periods_dev || !Q_dev ||
+        !T0_dev || !D_idx_dev || !depth_out_dev || !sigma_out_dev || !lnP_dev)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: null array");
+    if (n_t0 < 2 || n_D < 1 || n_P < 1)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: need n_t0 >= 2, n_D >= 1, n_P >= 1");
+    if (prec != NU_FP64 && prec != NU_MIXED)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: unknown precision");
+    if (!(gap_factor > 0.0))
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: gap_factor <= 0");
+    if (!(phase_step > 0.0) || !std::isfinite(phase_step))
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: phase_step must be given (> 0)");
+    if (n_t0 > 2000000000LL)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: n_t0 too large");
+    void* base = nullptr;
+    nu_status ss = noalloc_scratch(&base);
+    if (ss != NU_OK) return ss;
+    cudaStream_t st = (cudaStream_t)stream;
+    double ends[2];
+    cudaError_t e = cudaMemcpyAsync(&ends[0], t0s_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&ends[1], t0s_dev + n_t0 - 1, sizeof(double), cudaMemcpyDeviceToHost,
+                            st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: copy ends");
+    const double t_ref = ends[0], t_last = ends[1];
+    if (!(t_last >= t_ref)) return fail(NU_EINVAL, "nu_periodic_search_noalloc: t0s not sorted");
+    const double span_steps = (t_last - t_ref) / phase_step;
+    if (span_steps > 1.0e9)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: phase grid too fine");
+    const int64_t n_bucket = (int64_t)span_steps + 2;
+    const bool fp64 = prec == NU_FP64;
+    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+    const int64_t ngrid = n_t0 * (int64_t)n_D;
+    const int64_t n_slots = n_bucket + 2;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_nodes = al((size_t)ngrid * 4 * esz);
+    const size_t b_bucket = al((size_t)n_bucket * sizeof(int));
+    const size_t b_slot_of = al((size_t)n_t0 * sizeof(int));
+    const size_t b_flag = 256;
+    const size_t b_rec = fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>));
+    const size_t need = b_nodes + b_bucket + b_slot_of + b_flag + b_rec;
+    if (need > NU_NOALLOC_SCRATCH_BYTES)
+        return fail(NU_EINVAL,
+                    "nu_periodic_search_noalloc: this grid needs %zu bytes of scratch, more "
+                    "than the fixed %llu bytes; use nu_periodic_search",
+                    need, (unsigned long long)NU_NOALLOC_SCRATCH_BYTES);
+    char* scratch = (char*)base;
+    void* nodes = scratch;
+    int* bucket = (int*)(scratch + b_nodes);
+    int* slot_of = (int*)(scratch + b_nodes + b_bucket);
+    int* flag = (int*)(scratch + b_nodes + b_bucket + b_slot_of);
+    Node4<float>* rec = (Node4<float>*)(scratch + b_nodes + b_bucket + b_slot_of + b_flag);
+    int launched = 0;
+    bool use_slots = !fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span_steps < 4.0e6;
+    if (use_slots) {
+        int irregular = 0;
+        e = cudaMemsetAsync(flag, 0, sizeof(int), st);   // the array keeps old contents
+        k_slots<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, 1.0 / phase_step,
+                                                  slot_of, flag);
+        ++launched;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&irregular, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: slot test");
+        use_slots = irregular == 0;
+    }
+    if (use_slots) {
+        const int64_t nrec = n_slots * n_D;
+        k_fill_nan<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec);
+        k_slot_fill<<<div_up(ngrid, 256), 256, 0, st>>>(
+            (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
+            n_t0, n_D, n_slots, rec);
+        k_fold_slots<8><<<(unsigned)n_P, 256, 0, st>>>(rec, n_slots, n_D, phase_step, t_ref,
+                                                      t_last, periods_dev, n_P, Q_dev, T0_dev,
+                                                      D_idx_dev, depth_out_dev, sigma_out_dev,
+                                                      lnP_dev);
+        launched += 3;
+    } else {
+        k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
+                                                        n_bucket, bucket);
+        FoldGeom g{t0s_dev, n_t0, t_ref, t_last, phase_step, 1.0 / phase_step,
+                   gap_factor * phase_step, bucket, n_bucket};
+        if (fp64) {
+            k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
+                t0s_dev, n_t0, n_D, g.gap_max, (Node4<double>*)nodes);
+            k_fold_exact<double, 8><<<(unsigned)n_P, 256, 0, st>>>(
+                g, (const Node4<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+        } else {
+            k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
+                t0s_dev, n_t0, n_D, g.gap_max, (Node4<float>*)nodes);
+            k_fold_exact<float, 8><<<(unsigned)n_P, 256, 0, st>>>(
+                g, (const Node4<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+        }
+        launched += 3;
+    }
+    count_launches(launched);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: launch");
     return NU_OK;
 }
