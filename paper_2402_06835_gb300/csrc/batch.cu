@@ -198,7 +198,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
                     fbat);
     size_t foff = 0;
     const size_t f_segs = foff;  foff += al(fbat.segs.size() * sizeof(FoldSeg));
-    const size_t f_nodes = foff; foff += fbat.any_exact ? al((size_t)N * n_D * 4 * esz) : 0;
+    const size_t f_nodes = foff; foff += fbat.any_exact ? al((size_t)N * n_D * 8 * esz) : 0;
     const size_t f_buck = foff;  foff += al((size_t)(fbat.n_bucket_total + 1) * 4);
     const size_t f_rec = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(Node4<float>));
     e = cudaMallocAsync((void**)&fold_mem, foff, st);

@@ -16,6 +16,13 @@ template <typename T> struct __align__(4 * sizeof(T)) Node4 {
     T d, s, l, ig;
 };
 
+// Node record of the exact path: the Node4 fields plus the differences to the
+// next epoch's depth, sigma and gain (NaN when the next epoch is missing or
+// invalid), so that an event is one record load and three FMAs.
+template <typename T> struct __align__(8 * sizeof(T)) Node8 {
+    T d, s, l, ig, dd, ds, dl, pad;
+};
+
 // Geometry of one light curve of a batch fold.
 struct FoldSeg {
     int64_t s_off;      // first epoch (= first sample) in the packed arrays

@@ -76,24 +76,44 @@ __global__ void k_buckets(const double* __restrict__ t0s, int64_t n_t0, double t
 
 // Per-(duration, epoch) node records for the exact path.
 template <typename T>
+__device__ __forceinline__ T node_sigma(T d, T v, T l) {
+    return (isfinite(d) && isfinite(v) && isfinite(l) && v > T(0)) ? sqrt(v) : T(NAN);
+}
+
+template <typename T>
+__device__ __forceinline__ Node8<T> make_node8(const T* __restrict__ depth,
+                                               const T* __restrict__ var,
+                                               const T* __restrict__ gain,
+                                               const double* __restrict__ t0, int64_t gid,
+                                               int64_t i, int64_t n, double gap_max) {
+    Node8<T> r;
+    r.d = depth[gid];
+    r.l = gain[gid];
+    r.s = node_sigma<T>(r.d, var[gid], r.l);
+    r.ig = T(NAN);
+    r.dd = T(NAN);
+    r.ds = T(NAN);
+    r.dl = T(NAN);
+    r.pad = T(0);
+    if (i + 1 < n) {
+        const double gap = t0[i + 1] - t0[i];
+        if (gap <= gap_max && gap > 0.0) r.ig = (T)(1.0 / gap);
+        const T d1 = depth[gid + 1], l1 = gain[gid + 1];
+        const T s1 = node_sigma<T>(d1, var[gid + 1], l1);
+        r.dd = d1 - r.d;
+        r.ds = s1 - r.s;
+        r.dl = l1 - r.l;
+    }
+    return r;
+}
+
+template <typename T>
 __global__ void k_nodes(const T* __restrict__ depth, const T* __restrict__ var,
                         const T* __restrict__ gain, const double* __restrict__ t0s,
-                        int64_t n_t0, int n_D, double gap_max, Node4<T>* __restrict__ nodes) {
+                        int64_t n_t0, int n_D, double gap_max, Node8<T>* __restrict__ nodes) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= n_t0 * (int64_t)n_D) return;
-    const int64_t i = gid % n_t0;
-    const T d = depth[gid], v = var[gid], l = gain[gid];
-    Node4<T> r;
-    r.d = d;
-    r.l = l;
-    r.s = (isfinite(d) && isfinite(v) && isfinite(l) && v > T(0)) ? sqrt(v) : T(NAN);
-    T ig = T(NAN);
-    if (i + 1 < n_t0) {
-        const double gap = t0s[i + 1] - t0s[i];
-        if (gap <= gap_max && gap > 0.0) ig = (T)(1.0 / gap);
-    }
-    r.ig = ig;
-    nodes[gid] = r;
+    nodes[gid] = make_node8<T>(depth, var, gain, t0s, gid, gid % n_t0, n_t0, gap_max);
 }
 
 // Regular-grid test for the slot path: every epoch within 1e-3 slot of
@@ -204,6 +224,33 @@ __device__ __forceinline__ Best block_argmax(Best best) {
     return sh[0];
 }
 
+// Bound used to skip the second pass of a cell that cannot be the argmax.
+// With x_k = sigma^2 / s_k^2 (sum x_k = 1 by Eq. sigma_delta) the log terms of
+// Eq. result contribute -1/2 sum ln(s_k^2/(sigma^2+s_k^2)) = 1/2 sum ln(1+x_k)
+// <= 1/2 sum x_k = 1/2.  Because sigma^2 <= s_k^2, the depth terms satisfy
+//   sum (Delta_k - Delta)^2 / (s_k^2 + sigma^2) >= 1/2 sum (Delta_k - Delta)^2 / s_k^2
+//                                          = 1/2 (S_dd - S_d^2 / S_inv)
+// with S_dd = sum Delta_k^2 / s_k^2 from the first pass.  Hence
+//   ln P <= S_L + 1/2 - 1/4 (S_dd - S_d^2 / S_inv),
+// and a cell whose bound is below the best ln P found so far cannot win:
+// skipping its second pass changes no result.  The margins (on the bound and
+// on the cancellation in S_dd - S_d^2/S_inv) are far above the rounding of
+// each precision.
+__device__ __forceinline__ bool cannot_win(double s_l, double s_inv, double s_d, double s_dd,
+                                           double best) {
+    const double q = fmax(0.0, s_dd - s_d * s_d / s_inv - 1e-9 * s_dd);
+    const double ub = s_l + 0.5 - 0.25 * q;
+    return ub + 1e-6 * fmax(1.0, fabs(ub)) < best;
+}
+
+// FP32 form for the mixed kernel
+__device__ __forceinline__ bool cannot_win_f(float s_l, float s_inv, float s_d, float s_dd,
+                                             float best) {
+    const float q = fmaxf(0.0f, s_dd - s_d * s_d / s_inv - 1e-4f * s_dd);
+    const float ub = s_l + 0.5f - 0.25f * q;
+    return ub + 1e-4f * fmaxf(1.0f, fabsf(ub)) < best;
+}
+
 __device__ __forceinline__ bool bad_period(double P, const FoldGeom& g) {
     // a period must be finite, > 0 and give at most 1e9 epochs and phases
     return !(P > 0.0) || !isfinite(P) || (g.t_last - g.t_ref) / P > 1.0e9 ||
@@ -222,11 +269,22 @@ __device__ __forceinline__ void write_bad(int64_t p, double* Q_out, double* T0_o
 }
 
 // ------------------------------------------------ exact path (FP64 epochs)
+// Order-preserving integer key of a non-NaN double (so comparisons of times
+// run on the integer pipe; -0.0 never occurs among the epochs compared here).
+__device__ __forceinline__ long long okey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
 // largest i with t0[i] <= T starting from a guess (exact)
-__device__ __forceinline__ int64_t bracket_from(const FoldGeom& g, double T, int64_t i) {
-    while (i + 1 < g.n_t0 && g.t0s[i + 1] <= T) ++i;
-    while (i > 0 && g.t0s[i] > T) --i;
+__device__ __forceinline__ int64_t bracket_from(const FoldGeom& g, long long kT, int64_t i) {
+    while (i + 1 < g.n_t0 && okey(g.t0s[i + 1]) <= kT) ++i;
+    while (i > 0 && okey(g.t0s[i]) > kT) --i;
     return i;
+}
+
+__device__ __forceinline__ bool nan64(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
 }
 
 __device__ __forceinline__ int64_t bracket_guess(const FoldGeom& g, double T) {
@@ -242,17 +300,15 @@ template <> __device__ __forceinline__ float rcp_t<float>(float x) { return rcp3
 
 // One single event at epoch Tk: interpolated depth, variance and gain.
 template <typename T>
-__device__ __forceinline__ bool event_exact(const FoldGeom& g, const Node4<T>* __restrict__ nd,
+__device__ __forceinline__ bool event_exact(const FoldGeom& g, const Node8<T>* __restrict__ nd,
                                             double Tk, int64_t& i, T& dk, T& sk2, T& lk) {
-    i = bracket_from(g, Tk, i);
-    if (i > g.n_t0 - 2) return false;
-    const Node4<T> a = nd[i];
-    const Node4<T> b = nd[i + 1];
-    const T w = (T)((Tk - g.t0s[i]) * (double)a.ig);   // NaN across a gap
-    const T s = a.s + w * (b.s - a.s);
-    if (isnan(s)) return false;
-    dk = a.d + w * (b.d - a.d);
-    lk = a.l + w * (b.l - a.l);
+    i = bracket_from(g, okey(Tk), i);
+    const Node8<T> a = nd[i];
+    const T w = (T)((Tk - g.t0s[i]) * (double)a.ig);   // NaN across a gap / at the end
+    const T s = fma(w, a.ds, a.s);
+    if (sizeof(T) == 8 ? nan64((double)s) : isnan(s)) return false;
+    dk = fma(w, a.dd, a.d);
+    lk = fma(w, a.dl, a.l);
     sk2 = s * s;
     return true;
 }
@@ -280,19 +336,27 @@ __device__ __forceinline__ int64_t guess_at(const FoldGeom& g, unsigned long lon
 template <typename T>
 struct ExactAcc {
     KSum<T> s_inv, s_d, s_l;
+    T s_dd;                // sum Delta_k^2 / s_k^2 (bound only, plain sum)
     int K;
     __device__ __forceinline__ void init() {
         s_inv.init();
         s_d.init();
         s_l.init();
+        s_dd = T(0);
         K = 0;
     }
     __device__ __forceinline__ void add(T dk, T sk2, T lk) {
         const T iv = rcp_t<T>(sk2);
+        const T div = dk * iv;
         s_inv.add(iv);
-        s_d.add(dk * iv);
+        s_d.add(div);
+        s_dd = fma(div, dk, s_dd);
         s_l.add(lk);
         ++K;
+    }
+    __device__ __forceinline__ bool cannot_win(double best) const {
+        return nu::cannot_win((double)s_l.s, (double)s_inv.s, (double)s_d.s, (double)s_dd,
+                              best);
     }
 };
 
@@ -337,11 +401,36 @@ struct ExactPen {
     }
 };
 
+// Order-preserving unsigned key of a non-NaN double, for a shared atomic max.
+__device__ __forceinline__ unsigned long long max_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_max_key(unsigned long long k) {
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// A cell that survived the bound after its first pass, queued for the second.
+template <typename T>
+struct QCell {
+    double phi;
+    unsigned long long u0;
+    long long cell;
+    double s_l;
+    T s2, Dl;
+    int d;
+    int kmax;
+};
+
 // One period P of one light curve: every (duration, phase) cell, then the
 // block argmax; results at index p of the outputs.  Called by all threads of
-// the block.
+// the block.  Cells are processed in waves of blockDim: every thread runs the
+// first pass of one cell, the cells whose bound can still beat the block's
+// best are compacted into a shared queue, and the queue's second passes run
+// densely (a warp instruction costs the same however many lanes are active).
 template <typename T, int KC>
-__device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node4<T>* __restrict__ nodes,
+__device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node8<T>* __restrict__ nodes,
                                                int n_D, double P, int64_t p,
                                                double* __restrict__ Q_out,
                                                double* __restrict__ T0_out,
@@ -349,6 +438,9 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node4<T>
                                                double* __restrict__ dep_out,
                                                double* __restrict__ sig_out,
                                                double* __restrict__ lnp_out) {
+    __shared__ QCell<T> sh_q[256];
+    __shared__ int sh_nq;
+    __shared__ unsigned long long sh_best;
     if (bad_period(P, g)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
@@ -362,91 +454,93 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node4<T>
     const double ulast_d = (g.t_last - g.t_ref) * g.inv_dt * SCALE;
     const unsigned long long ulast =
         ulast_d < 4.0e18 ? (unsigned long long)llrint(ulast_d) : 4000000000000000000ull;
-    const float inv_ustep = 1.0f / (float)swk.ustep;
-    double bl = -INFINITY;
-    long long bc = LLONG_MAX;
-    T bD = T(NAN), bs2 = T(NAN);
+    const float inv_ustep32 = (float)(4294967296.0 / (double)swk.ustep);
+    const long long klast = okey(g.t_last);
     // phase j / n_phi: reciprocal plus one FMA correction of the quotient
     // (Markstein 1990), instead of a division per cell
     const double nphi_d = (double)n_phi;
     const double rphi = 1.0 / nphi_d;
+    double bl = -INFINITY;
+    long long bc = LLONG_MAX;
+    T bD = T(NAN), bs2 = T(NAN);
+    if (threadIdx.x == 0) {
+        sh_nq = 0;
+        sh_best = max_key(-INFINITY);
+    }
+    __syncthreads();
     // cells walk (duration, phase) incrementally: no 64-bit division per cell
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
-    for (int64_t cell = threadIdx.x; cell < n_cells;
-         cell += blockDim.x, j += blockDim.x) {
+    for (int64_t base = 0; base < n_cells; base += blockDim.x, j += blockDim.x) {
         while (j >= n_phi) {
             j -= n_phi;
             ++d;
         }
-        const double jd = (double)j;
-        const double q0 = jd * rphi;
-        const double phi = fma(fma(-q0, nphi_d, jd), rphi, q0);
-        const Node4<T>* nd = nodes + (int64_t)d * g.n_t0;
-        const unsigned long long u0 = (unsigned long long)j * swp.u0;
-        // number of epochs with T <= t_last: integer estimate, then the exact
-        // FP64 comparisons of the definition
-        int64_t kk = u0 > ulast ? 0 : (int64_t)((float)(ulast - u0) * inv_ustep) + 1;
-        while (kk > 0 &&
-               __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)(kk - 1)), P)) > g.t_last)
-            --kk;
-        while (__dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)kk), P)) <= g.t_last) ++kk;
-        const int64_t kmax = kk;
-        ExactAcc<T> a1;
-        a1.init();
-        ExactPen<T> a2;
-        if (kmax <= KC) {
-            T cd[KC > 0 ? KC : 1], cs[KC > 0 ? KC : 1];
-            bool ok[KC > 0 ? KC : 1];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                ok[k] = false;
-                if (k < kmax) {
-                    const double Tk =
-                        __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
-                    int64_t i = guess_at(g, u0 + (unsigned long long)k * swk.ustep);
-                    T dk, sk2, lk;
-                    ok[k] = event_exact<T>(g, nd, Tk, i, dk, sk2, lk);
-                    if (ok[k]) {
-                        cd[k] = dk;
-                        cs[k] = sk2;
-                        a1.add(dk, sk2, lk);
-                    }
-                }
-            }
-            if (a1.K == 0) continue;
-            const T s2 = T(1) / a1.s_inv.s;
-            a2.init(s2, s2 * a1.s_d.s);
-#pragma unroll
-            for (int k = 0; k < KC; ++k)
-                if (ok[k]) a2.add(cd[k], cs[k]);
-        } else {
+        const int64_t cell = base + threadIdx.x;
+        if (cell < n_cells) {
+            const double jd = (double)j;
+            const double q0 = jd * rphi;
+            const double phi = fma(fma(-q0, nphi_d, jd), rphi, q0);
+            const Node8<T>* nd = nodes + (int64_t)d * g.n_t0;
+            const unsigned long long u0 = (unsigned long long)j * swp.u0;
+            // number of epochs with T <= t_last: integer estimate, then the
+            // exact comparisons of the definition
+            int64_t kk = u0 > ulast ? 0
+                                    : (int64_t)((float)(unsigned)((ulast - u0) >> 32) *
+                                                inv_ustep32) + 1;
+            while (kk > 0 &&
+                   okey(__dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)(kk - 1)), P))) >
+                       klast)
+                --kk;
+            while (okey(__dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)kk), P))) <= klast)
+                ++kk;
+            const int64_t kmax = kk;
+            ExactAcc<T> a1;
+            a1.init();
             unsigned long long u = u0;
-            for (int64_t k = 0; k < kmax; ++k, u += swk.ustep) {
-                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
+            double kd = 0.0;
+            for (int64_t k = 0; k < kmax; ++k, u += swk.ustep, kd += 1.0) {
+                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, kd), P));
                 T dk, sk2, lk;
                 int64_t i = guess_at(g, u);
                 if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a1.add(dk, sk2, lk);
             }
-            if (a1.K == 0) continue;
-            const T s2 = T(1) / a1.s_inv.s;
-            a2.init(s2, s2 * a1.s_d.s);
-            u = u0;
-            for (int64_t k = 0; k < kmax; ++k, u += swk.ustep) {
-                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)k), P));
+            const double best_now = fmax(bl, from_max_key(sh_best));
+            if (a1.K > 0 && !a1.cannot_win(best_now)) {
+                const T s2 = T(1) / a1.s_inv.s;
+                const int q = atomicAdd(&sh_nq, 1);
+                sh_q[q] = QCell<T>{phi, u0, (long long)cell, (double)a1.s_l.s, s2,
+                                   s2 * a1.s_d.s, d, (int)kmax};
+            }
+        }
+        __syncthreads();
+        const int nq = sh_nq;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            const QCell<T> qc = sh_q[q];
+            const Node8<T>* nd = nodes + (int64_t)qc.d * g.n_t0;
+            ExactPen<T> a2;
+            a2.init(qc.s2, qc.Dl);
+            unsigned long long u = qc.u0;
+            double kd = 0.0;
+            for (int k = 0; k < qc.kmax; ++k, u += swk.ustep, kd += 1.0) {
+                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(qc.phi, kd), P));
                 T dk, sk2, lk;
                 int64_t i = guess_at(g, u);
                 if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a2.add(dk, sk2);
             }
+            const double lnp = qc.s_l - 0.5 * (a2.logsum() + (double)a2.quad.s);
+            if (!(lnp == lnp)) continue;   // NaN never selected
+            if (lnp > bl || (lnp == bl && qc.cell < bc)) {
+                bl = lnp;
+                bc = qc.cell;
+                bD = qc.Dl;
+                bs2 = qc.s2;
+            }
+            atomicMax(&sh_best, max_key(lnp));
         }
-        const double lnp = (double)a1.s_l.s - 0.5 * (a2.logsum() + (double)a2.quad.s);
-        if (!(lnp == lnp)) continue;   // NaN never selected
-        if (lnp > bl || (lnp == bl && cell < bc)) {
-            bl = lnp;
-            bc = cell;
-            bD = a2.Dl;
-            bs2 = a2.s2;
-        }
+        __syncthreads();
+        if (threadIdx.x == 0) sh_nq = 0;
+        __syncthreads();
     }
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (bc != LLONG_MAX) best = Best{bl, bc, (double)bD, sqrt((double)bs2)};
@@ -457,7 +551,7 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node4<T>
 
 template <typename T, int KC>
 __global__ void __launch_bounds__(256)
-k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
+k_fold_exact(FoldGeom g, const Node8<T>* __restrict__ nodes, int n_D,
              const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
              double* __restrict__ T0_out, int* __restrict__ Didx_out,
              double* __restrict__ dep_out, double* __restrict__ sig_out,
@@ -469,17 +563,16 @@ k_fold_exact(FoldGeom g, const Node4<T>* __restrict__ nodes, int n_D,
 }
 
 // ---------------------------------------- slot path (mixed, regular grids)
-// Epochs walk the slot grid in 24.40 fixed point: u = (T - t_ref)/dt =
-// (j/n_phi + k) P/dt.  The interval is (slot, slot+1) and the weight is the
-// fractional part; on a grid whose epochs sit on the slots this is the
-// exact interpolation up to the epochs' offsets from the slot centres.
 struct SlotEvent {
     float d, s, l;
 };
 __device__ __forceinline__ SlotEvent slot_event(const Node4<float>* __restrict__ rd,
                                                 unsigned long long u) {
     const int64_t s = (int64_t)(u >> 40);
-    const float w = (float)((unsigned)((u >> 16) & 0xffffffu)) * 5.9604644775390625e-8f;
+    // weight = fractional slot position: its top 23 bits as the mantissa of a
+    // float in [1, 2), minus 1 (no integer-to-float conversion)
+    const float w =
+        __uint_as_float(0x3f800000u | (unsigned)((u >> 17) & 0x7fffffu)) - 1.0f;
     const Node4<float> a = rd[s];
     const Node4<float> b = rd[s + 1];
     SlotEvent e;
@@ -491,18 +584,22 @@ __device__ __forceinline__ SlotEvent slot_event(const Node4<float>* __restrict__
 
 struct SlotPass1 {
     KSum<float> s_inv, s_d, s_l;
+    float s_dd;            // sum Delta_k^2 / s_k^2 (bound only)
     int K;
     __device__ __forceinline__ void init() {
         s_inv.init();
         s_d.init();
         s_l.init();
+        s_dd = 0.f;
         K = 0;
     }
     __device__ __forceinline__ void add(const SlotEvent& e) {
         if (isnan(e.s)) return;
         const float iv = rcp32(e.s * e.s);
+        const float div = e.d * iv;
         s_inv.add(iv);
-        s_d.add(e.d * iv);
+        s_d.add(div);
+        s_dd = fmaf(div, e.d, s_dd);
         s_l.add(e.l);
         ++K;
     }
@@ -532,8 +629,8 @@ struct SlotPass2 {
 // (j/n_phi + k) P/dt.  The interval is (slot, slot+1) and the weight is the
 // fractional part; on a grid whose epochs sit on the slots this is the
 // interpolation between the bracketing epochs up to their offsets from the
-// slot centres (checked to be below 1e-3 slot).  Cells with at most KC epochs
-// keep their events in registers for the second pass.
+// slot centres (checked to be below 1e-3 slot).  Cells are processed in waves
+// with the second passes of the surviving cells compacted, as in the exact path.
 template <int KC>
 __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ rec,
                                                int64_t n_slots, int n_D, double dt,
@@ -544,6 +641,9 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                                                double* __restrict__ dep_out,
                                                double* __restrict__ sig_out,
                                                double* __restrict__ lnp_out) {
+    __shared__ QCell<float> sh_q[256];
+    __shared__ int sh_nq;
+    __shared__ unsigned int sh_best;
     FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
     if (bad_period(P, gg)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
@@ -559,77 +659,86 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         R * SCALE < 4.0e18 ? (unsigned long long)llrint(R * SCALE) : 4000000000000000000ull;
     // phase j starts at j * (R / n_phi) slots; per-cell work stays integer
     const unsigned long long uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
-    const float inv_ustep = 1.0f / (float)ustep;
-    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    // epochs per cell from the remaining span in units of 2^32 (a 32-bit
+    // integer), corrected exactly below
+    const float inv_ustep32 = (float)(4294967296.0 / (double)ustep);
     float bl = -INFINITY, bD = NAN, bs2 = NAN;
     long long bc = LLONG_MAX;
+    if (threadIdx.x == 0) {
+        sh_nq = 0;
+        sh_best = 0u;                       // key below every finite float
+    }
+    __syncthreads();
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
-    for (int64_t cell = threadIdx.x; cell < n_cells;
-         cell += blockDim.x, j += blockDim.x) {
+    for (int64_t base = 0; base < n_cells; base += blockDim.x, j += blockDim.x) {
         while (j >= n_phi) {
             j -= n_phi;
             ++d;
         }
-        const unsigned long long u0 = (unsigned long long)j * uph;
-        if (u0 > ulast) continue;
-        int64_t kk = (int64_t)((float)(ulast - u0) * inv_ustep);
-        while (kk > 0 && u0 + (unsigned long long)kk * ustep > ulast) --kk;
-        while (u0 + (unsigned long long)(kk + 1) * ustep <= ulast) ++kk;
-        const int64_t kmax = kk + 1;
-        const Node4<float>* rd = rec + (int64_t)d * n_slots;
-        SlotPass1 p1;
-        p1.init();
-        SlotPass2 p2;
-        if (kmax <= KC) {
-            float cd[KC], cs[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                cs[k] = NAN;
-                cd[k] = 0.f;
-                if (k < kmax) {
-                    const SlotEvent e = slot_event(rd, u0 + (unsigned long long)k * ustep);
-                    cd[k] = e.d;
-                    cs[k] = e.s;
-                    p1.add(e);
+        const int64_t cell = base + threadIdx.x;
+        if (cell < n_cells) {
+            const unsigned long long u0 = (unsigned long long)j * uph;
+            if (u0 <= ulast) {
+                int64_t kk = (int64_t)((float)(unsigned)((ulast - u0) >> 32) * inv_ustep32);
+                while (kk > 0 && u0 + (unsigned long long)kk * ustep > ulast) --kk;
+                while (u0 + (unsigned long long)(kk + 1) * ustep <= ulast) ++kk;
+                const int64_t kmax = kk + 1;
+                const Node4<float>* rd = rec + (int64_t)d * n_slots;
+                SlotPass1 p1;
+                p1.init();
+                unsigned long long u = u0;
+                for (int64_t k = 0; k < kmax; ++k, u += ustep) p1.add(slot_event(rd, u));
+                const unsigned int kb = sh_best;
+                const float best_now =
+                    fmaxf(bl, kb ? __uint_as_float((kb >> 31) ? (kb & 0x7fffffffu) : ~kb)
+                                 : -INFINITY);
+                if (p1.K > 0 &&
+                    !cannot_win_f(p1.s_l.s, p1.s_inv.s, p1.s_d.s, p1.s_dd, best_now)) {
+                    const float s2 = 1.0f / p1.s_inv.s;
+                    const int q = atomicAdd(&sh_nq, 1);
+                    sh_q[q] = QCell<float>{0.0, u0, (long long)cell, (double)p1.s_l.s, s2,
+                                           s2 * p1.s_d.s, d, (int)kmax};
                 }
             }
-            if (p1.K == 0) continue;
-            const float s2 = 1.0f / p1.s_inv.s;
-            p2.init(s2, s2 * p1.s_d.s);
-#pragma unroll
-            for (int k = 0; k < KC; ++k) p2.add(cd[k], cs[k]);
-        } else {
-            unsigned long long u = u0;
-            for (int64_t k = 0; k < kmax; ++k, u += ustep) p1.add(slot_event(rd, u));
-            if (p1.K == 0) continue;
-            const float s2 = 1.0f / p1.s_inv.s;
-            p2.init(s2, s2 * p1.s_d.s);
-            u = u0;
-            for (int64_t k = 0; k < kmax; ++k, u += ustep) {
+        }
+        __syncthreads();
+        const int nq = sh_nq;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            const QCell<float> qc = sh_q[q];
+            const Node4<float>* rd = rec + (int64_t)qc.d * n_slots;
+            SlotPass2 p2;
+            p2.init(qc.s2, qc.Dl);
+            unsigned long long u = qc.u0;
+            for (int k = 0; k < qc.kmax; ++k, u += ustep) {
                 const SlotEvent e = slot_event(rd, u);
                 p2.add(e.d, e.s);
             }
+            const float lnp =
+                (float)qc.s_l - 0.5f * (p2.lsum * 0.693147180559945f + p2.quad.s);
+            if (!(lnp == lnp)) continue;
+            if (lnp > bl || (lnp == bl && qc.cell < bc)) {
+                bl = lnp;
+                bc = qc.cell;
+                bD = p2.Dl;
+                bs2 = p2.s2;
+            }
+            const unsigned int b32 = __float_as_uint(lnp);
+            atomicMax(&sh_best, (b32 >> 31) ? ~b32 : (b32 | 0x80000000u));
         }
-        // per-cell bookkeeping stays in FP32 (FP64 here would cost more than
-        // the epochs of a long period)
-        const float lnp = p1.s_l.s - 0.5f * (p2.lsum * 0.693147180559945f + p2.quad.s);
-        if (!(lnp == lnp)) continue;
-        if (lnp > bl || (lnp == bl && cell < bc)) {
-            bl = lnp;
-            bc = cell;
-            bD = p2.Dl;
-            bs2 = p2.s2;
-        }
+        __syncthreads();
+        if (threadIdx.x == 0) sh_nq = 0;
+        __syncthreads();
     }
-    if (bc != LLONG_MAX) best = Best{(double)bl, (long long)bc, (double)bD, sqrt((double)bs2)};
+    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    if (bc != LLONG_MAX) best = Best{(double)bl, bc, (double)bD, sqrt((double)bs2)};
     const Best b = block_argmax(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
 template <int KC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, double dt,
              double t_ref, double t_last, const double* __restrict__ periods, int64_t n_P,
              double* __restrict__ Q_out, double* __restrict__ T0_out,
@@ -678,11 +787,11 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
             FoldGeom gg{t + fs.s_off, fs.n_t0, fs.t_ref, fs.t_last, dt, 1.0 / dt,
                         gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
             if (KIND == 0)
-                fold_exact_one<double, 8>(gg, (const Node4<double>*)nodes + fs.s_off * n_D,
+                fold_exact_one<double, 8>(gg, (const Node8<double>*)nodes + fs.s_off * n_D,
                                           n_D, periods[p], o, Q_out, T0_out, Didx_out,
                                           dep_out, sig_out, lnp_out);
             else
-                fold_exact_one<float, 8>(gg, (const Node4<float>*)nodes + fs.s_off * n_D, n_D,
+                fold_exact_one<float, 8>(gg, (const Node8<float>*)nodes + fs.s_off * n_D, n_D,
                                          periods[p], o, Q_out, T0_out, Didx_out, dep_out,
                                          sig_out, lnp_out);
         }
@@ -695,7 +804,7 @@ __global__ void k_nodes_batch(const T* __restrict__ depth, const T* __restrict__
                               const T* __restrict__ gain, const double* __restrict__ t,
                               const FoldSeg* __restrict__ segs, int n_seg,
                               const int64_t* __restrict__ s_off, int n_D, double gap_max,
-                              Node4<T>* __restrict__ nodes) {
+                              Node8<T>* __restrict__ nodes) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= s_off[n_seg] * (int64_t)n_D) return;
     int lo = 0, hi = n_seg;
@@ -705,18 +814,7 @@ __global__ void k_nodes_batch(const T* __restrict__ depth, const T* __restrict__
     }
     const int64_t s0 = s_off[lo], ng = s_off[lo + 1] - s0;
     const int64_t i = (gid - s0 * n_D) % ng;
-    const T d = depth[gid], v = var[gid], l = gain[gid];
-    Node4<T> r;
-    r.d = d;
-    r.l = l;
-    r.s = (isfinite(d) && isfinite(v) && isfinite(l) && v > T(0)) ? sqrt(v) : T(NAN);
-    T ig = T(NAN);
-    if (i + 1 < ng) {
-        const double gap = t[s0 + i + 1] - t[s0 + i];
-        if (gap <= gap_max && gap > 0.0) ig = (T)(1.0 / gap);
-    }
-    r.ig = ig;
-    nodes[gid] = r;
+    nodes[gid] = make_node8<T>(depth, var, gain, t + s0, gid, i, ng, gap_max);
 }
 
 __global__ void k_buckets_batch(const double* __restrict__ t, const FoldSeg* __restrict__ segs,
@@ -824,11 +922,11 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
         if (fp64)
             k_nodes_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
-                n_seg, s_off_dev, n_D, gap_factor * dt, (Node4<double>*)nodes);
+                n_seg, s_off_dev, n_D, gap_factor * dt, (Node8<double>*)nodes);
         else
             k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
-                s_off_dev, n_D, gap_factor * dt, (Node4<float>*)nodes);
+                s_off_dev, n_D, gap_factor * dt, (Node8<float>*)nodes);
         k_buckets_batch<<<div_up(fb.n_bucket_total, 256), 256, 0, st>>>(
             t, segs_dev, n_seg, fb.n_bucket_total, dt, bucket);
         launched += 2;
@@ -941,7 +1039,7 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
     const int64_t ngrid = n_t0 * (int64_t)n_D;
     const int64_t n_slots = n_bucket + 2;          // slot records, NaN padded
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_nodes = al((size_t)ngrid * 4 * esz);
+    const size_t b_nodes = al((size_t)ngrid * 8 * esz);
     const size_t b_bucket = al((size_t)n_bucket * sizeof(int));
     const size_t b_slot_of = al((size_t)n_t0 * sizeof(int));
     const size_t b_flag = 256;
@@ -993,16 +1091,16 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
         if (fp64) {
             k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node4<double>*)nodes);
+                t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
             k_fold_exact<double, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node4<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                g, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node4<float>*)nodes);
+                t0s_dev, n_t0, n_D, g.gap_max, (Node8<float>*)nodes);
             k_fold_exact<float, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node4<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                g, (const Node8<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         }
         launched += 3;
@@ -1097,7 +1195,7 @@ extern "C" nu_status nu_periodic_search_noalloc(const double* t0s_dev, int64_t n
     const int64_t ngrid = n_t0 * (int64_t)n_D;
     const int64_t n_slots = n_bucket + 2;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_nodes = al((size_t)ngrid * 4 * esz);
+    const size_t b_nodes = al((size_t)ngrid * 8 * esz);
     const size_t b_bucket = al((size_t)n_bucket * sizeof(int));
     const size_t b_slot_of = al((size_t)n_t0 * sizeof(int));
     const size_t b_flag = 256;
@@ -1147,16 +1245,16 @@ extern "C" nu_status nu_periodic_search_noalloc(const double* t0s_dev, int64_t n
         if (fp64) {
             k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node4<double>*)nodes);
+                t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
             k_fold_exact<double, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node4<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                g, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node4<float>*)nodes);
+                t0s_dev, n_t0, n_D, g.gap_max, (Node8<float>*)nodes);
             k_fold_exact<float, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node4<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                g, (const Node8<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         }
         launched += 3;
