@@ -238,6 +238,22 @@ def run_batch(api, torch, w, precision, steps, warmup, flush):
             "failed_curves": int(sum(1 for s_ in r["status"] if s_ != 0))}
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(ms, torch, device):
+    """Slowest rank's time (every rank gets it); identity without a group."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(ms)
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def weak_scaling_value(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processed its own units in <= ms."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- oracle
 def oracle_sample(lc, Ds, periods, n_templates=256, n_periods=8, seed=0):
     """Time the oracle on a bounded sample and extrapolate to one full step."""
@@ -352,13 +368,10 @@ def main():
     if len(w.curves) > 1:
         # survey workload: the batched call is the step
         b = run_batch(api, torch, w, args.precision, args.steps, args.warmup, flush)
-        ms = b["ms_per_step"]
-        if world > 1:
-            tt = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(b["ms_per_step"], torch, dev)
         nt = sum(len(lc.t) for lc in w.curves) * len(w.durations)
-        out = {"metric": METRIC, "value": world * nt / (ms / 1e3), "unit": "(t0,D) fits/s",
+        out = {"metric": METRIC, "value": weak_scaling_value(nt, world, ms),
+               "unit": "(t0,D) fits/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
@@ -388,13 +401,9 @@ def main():
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
     launches = api.launch_count() - n0
-    ms = float(stages.sum(axis=1).mean())
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(float(stages.sum(axis=1).mean()), torch, dev)
     stage_ms = stages.mean(axis=0)
-    value = world * n_templates / (ms / 1e3)
+    value = weak_scaling_value(n_templates, world, ms)
 
     # dominant kernel: the fold (k_fold), FP64 pipe-bound in FP64 mode
     visits = fold_visits(lc.t, w.periods, pipe.dt, len(w.durations))

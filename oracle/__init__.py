@@ -19,8 +19,11 @@ and scipy's LAPACK routines as the only library steps:
                 phase grid, the combination of Eq. result with the biased
                 estimates of Eq. sigma_delta, the argmax of Eq. phi0 and
                 Q(P) = Delta/sigma.
+* ``semisep``   a second, sequential FP64 reference for light curves too long
+                for the dense matrix: the celerite semiseparable Cholesky of
+                the same covariance, pinned to ``linear`` where both run.
 
 Nothing here shares code with the CUDA sources; the two meet only through the
 seeded inputs of ``paper_2402_06835_gb300.synth``.
 """
-from . import gp, linear, periodic  # noqa: F401
+from . import gp, linear, periodic, semisep  # noqa: F401
