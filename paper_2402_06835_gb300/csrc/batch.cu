@@ -198,7 +198,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
                     fbat);
     size_t foff = 0;
     const size_t f_segs = foff;  foff += al(fbat.segs.size() * sizeof(FoldSeg));
-    const size_t f_nodes = foff; foff += fbat.any_exact ? al((size_t)N * n_D * 8 * esz) : 0;
+    const size_t f_nodes = foff; foff += fbat.any_exact ? exact_layout(N, n_D, fp64).total : 0;
     const size_t f_buck = foff;  foff += al((size_t)(fbat.n_bucket_total + 1) * 4);
     const size_t f_rec = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(Node4<float>));
     e = cudaMallocAsync((void**)&fold_mem, foff, st);
@@ -240,7 +240,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         l += launch_fold_prep(fbat, fsegs, s_off_dev, n_lc, N, fp64, t_dev, lin_d, lin_v,
                               lin_l, n_D, phase_step, gap_factor, nodes, bucket, rec, st);
         cudaMemsetAsync(ctr, 0, 16, st);
-        l += launch_fold_batch(fbat, fsegs, n_run, fp64, t_dev, nodes, bucket, rec, n_D,
+        l += launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, nodes, bucket, rec, n_D,
                                phase_step, gap_factor, periods_dev, nP_run, ctr, grid, threads,
                                Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
                                lnP_dev, st);
@@ -268,7 +268,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         for (int c = 0; c < 4; ++c) {
             cudaMemsetAsync(ctr, 0, 16, st);
             cudaEventRecord(e0, st);
-            const int lt = launch_fold_batch(fbat, fsegs, n_run, fp64, t_dev, nodes, bucket,
+            const int lt = launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, nodes, bucket,
                                              rec, n_D, phase_step, gap_factor, periods_dev,
                                              nP_run, ctr, n_sm * cand[c][0], cand[c][1], Q_dev,
                                              T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,

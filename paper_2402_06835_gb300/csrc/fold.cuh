@@ -23,6 +23,34 @@ template <typename T> struct __align__(8 * sizeof(T)) Node8 {
     T d, s, l, ig, dd, ds, dl, pad;
 };
 
+// Screening record of the FP64 path, one per (duration, epoch i): the FP32
+// values and slopes of the interval [t0_i, t0_{i+1}], wsc = 2^-30 dt/gap (the
+// weight per unit of the 2^-30-slot position difference), and flags = 1 when
+// the interval is outside the screen's error model (epochs closer than dt/4,
+// end sigmas more than a factor 3 apart, or values whose FP32 sums could
+// overflow): a cell with an event there is evaluated exactly.  s is NaN on an
+// invalid interval.
+struct __align__(32) ScreenRec {
+    float d, s, l, dd, ds, dl, wsc;
+    unsigned flags;
+};
+
+// Byte layout of the exact path's per-(duration, epoch) arrays for n epochs:
+// Node8 records, then (FP64 only) screening records and pairs of fixed-point
+// epoch positions.
+struct ExactLayout {
+    size_t off_screen, off_vpos, total;
+};
+inline ExactLayout exact_layout(int64_t n, int n_D, bool fp64) {
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    ExactLayout L;
+    const size_t node = al((size_t)n * n_D * 8 * (fp64 ? 8 : 4));
+    L.off_screen = node;
+    L.off_vpos = node + (fp64 ? al((size_t)n * n_D * sizeof(ScreenRec)) : 0);
+    L.total = L.off_vpos + (fp64 ? al((size_t)n * 16) : 0);
+    return L;
+}
+
 // Geometry of one light curve of a batch fold.
 struct FoldSeg {
     int64_t s_off;      // first epoch (= first sample) in the packed arrays
@@ -31,6 +59,7 @@ struct FoldSeg {
     int64_t n_bucket, bucket_off;
     int64_t n_slots, rec_off;
     int use_slots;
+    int screen;         // FP64 path: FP32 screening allowed for this curve
 };
 
 // Host side of the batch fold: per-curve layout and launches.
@@ -49,8 +78,8 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
                      const void* var, const void* gain, int n_D, double dt, double gap_factor,
                      void* nodes, int* bucket, Node4<float>* rec, cudaStream_t st);
 
-int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg, bool fp64,
-                      const double* t, const void* nodes, const int* bucket,
+int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
+                      int64_t n_total, bool fp64, const double* t, const void* nodes, const int* bucket,
                       const Node4<float>* rec, int n_D, double dt, double gap_factor,
                       const double* periods, int64_t n_P, unsigned long long* counter,
                       int grid, int threads, double* Q, double* T0, int* Didx, double* dep,

@@ -19,6 +19,7 @@
 #include <climits>
 #include <cmath>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "fold.cuh"
@@ -243,11 +244,14 @@ __device__ __forceinline__ bool cannot_win(double s_l, double s_inv, double s_d,
     return ub + 1e-6 * fmax(1.0, fabs(ub)) < best;
 }
 
-// FP32 form for the mixed kernel
+// FP32 form for the mixed kernel, with the tighter depth term
+// q / (2 (1 + x_max)), x_max = max_k sigma^2/s_k^2 = ivmax / S_inv <= 1
+// (sigma^2 + s_k^2 = s_k^2 (1 + x_k) <= s_k^2 (1 + x_max)).
 __device__ __forceinline__ bool cannot_win_f(float s_l, float s_inv, float s_d, float s_dd,
-                                             float best) {
+                                             float ivmax, float best) {
     const float q = fmaxf(0.0f, s_dd - s_d * s_d / s_inv - 1e-4f * s_dd);
-    const float ub = s_l + 0.5f - 0.25f * q;
+    const float x = fminf(1.0f, ivmax / s_inv * 1.001f);
+    const float ub = s_l + 0.5f - 0.5f * q / (1.0f + x);
     return ub + 1e-4f * fmaxf(1.0f, fabsf(ub)) < best;
 }
 
@@ -423,6 +427,88 @@ struct QCell {
     int kmax;
 };
 
+// Per-period constants of the exact evaluation of a cell.
+struct CellCtx {
+    double P, nphi_d, rphi;
+    SlotWalk swp, swk;         // per-phase and per-epoch steps of the slot guess
+    unsigned long long ulast;  // t_last on the same fixed-point scale
+    float inv_ustep32;
+    long long klast;           // order key of t_last
+};
+
+__device__ __forceinline__ CellCtx cell_ctx(const FoldGeom& g, double P, int64_t n_phi) {
+    CellCtx c;
+    c.P = P;
+    const double R = P * g.inv_dt;
+    c.swp = slot_walk(1.0 / (double)n_phi, R);
+    c.swk = slot_walk(0.0, R);
+    const double SCALE = 1099511627776.0;   // 2^40
+    const double ulast_d = (g.t_last - g.t_ref) * g.inv_dt * SCALE;
+    c.ulast = ulast_d < 4.0e18 ? (unsigned long long)llrint(ulast_d) : 4000000000000000000ull;
+    c.inv_ustep32 = (float)(4294967296.0 / (double)c.swk.ustep);
+    c.klast = okey(g.t_last);
+    // phase j / n_phi: reciprocal plus one FMA correction of the quotient
+    // (Markstein 1990), instead of a division per cell
+    c.nphi_d = (double)n_phi;
+    c.rphi = 1.0 / c.nphi_d;
+    return c;
+}
+
+__device__ __forceinline__ double cell_phi(const CellCtx& c, int64_t j) {
+    const double jd = (double)j;
+    const double q0 = jd * c.rphi;
+    return fma(fma(-q0, c.nphi_d, jd), c.rphi, q0);
+}
+
+__device__ __forceinline__ double epoch_time(const FoldGeom& g, const CellCtx& c, double phi,
+                                             double kd) {
+    return __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, kd), c.P));
+}
+
+// number of epochs with T <= t_last: integer estimate, then the exact
+// comparisons of the definition
+__device__ __forceinline__ int64_t cell_kmax(const FoldGeom& g, const CellCtx& c, double phi,
+                                             unsigned long long u0) {
+    int64_t kk = u0 > c.ulast ? 0
+                              : (int64_t)((float)(unsigned)((c.ulast - u0) >> 32) *
+                                          c.inv_ustep32) + 1;
+    while (kk > 0 && okey(epoch_time(g, c, phi, (double)(kk - 1))) > c.klast) --kk;
+    while (okey(epoch_time(g, c, phi, (double)kk)) <= c.klast) ++kk;
+    return kk;
+}
+
+// First and second sums of one cell over epochs k0, k0 + ks, ... < kmax.
+template <typename T>
+__device__ __forceinline__ void cell_pass1(const FoldGeom& g, const Node8<T>* __restrict__ nd,
+                                           const CellCtx& c, double phi, unsigned long long u0,
+                                           int64_t kmax, int k0, int ks, ExactAcc<T>& a1) {
+    unsigned long long u = u0 + (unsigned long long)k0 * c.swk.ustep;
+    const unsigned long long us = (unsigned long long)ks * c.swk.ustep;
+    double kd = (double)k0;
+    const double kds = (double)ks;
+    for (int64_t k = k0; k < kmax; k += ks, u += us, kd += kds) {
+        const double Tk = epoch_time(g, c, phi, kd);
+        T dk, sk2, lk;
+        int64_t i = guess_at(g, u);
+        if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a1.add(dk, sk2, lk);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void cell_pass2(const FoldGeom& g, const Node8<T>* __restrict__ nd,
+                                           const CellCtx& c, double phi, unsigned long long u0,
+                                           int64_t kmax, int k0, int ks, ExactPen<T>& a2) {
+    unsigned long long u = u0 + (unsigned long long)k0 * c.swk.ustep;
+    const unsigned long long us = (unsigned long long)ks * c.swk.ustep;
+    double kd = (double)k0;
+    const double kds = (double)ks;
+    for (int64_t k = k0; k < kmax; k += ks, u += us, kd += kds) {
+        const double Tk = epoch_time(g, c, phi, kd);
+        T dk, sk2, lk;
+        int64_t i = guess_at(g, u);
+        if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a2.add(dk, sk2);
+    }
+}
+
 // One period P of one light curve: every (duration, phase) cell, then the
 // block argmax; results at index p of the outputs.  Called by all threads of
 // the block.  Cells are processed in waves of blockDim: every thread runs the
@@ -447,19 +533,7 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node8<T>
     }
     const int64_t n_phi = (int64_t)ceil(P / g.dt);
     const int64_t n_cells = n_phi * n_D;
-    const double R = P * g.inv_dt;
-    const SlotWalk swp = slot_walk(1.0 / (double)n_phi, R);   // per-phase slot step
-    const SlotWalk swk = slot_walk(0.0, R);                   // per-epoch slot step
-    const double SCALE = 1099511627776.0;
-    const double ulast_d = (g.t_last - g.t_ref) * g.inv_dt * SCALE;
-    const unsigned long long ulast =
-        ulast_d < 4.0e18 ? (unsigned long long)llrint(ulast_d) : 4000000000000000000ull;
-    const float inv_ustep32 = (float)(4294967296.0 / (double)swk.ustep);
-    const long long klast = okey(g.t_last);
-    // phase j / n_phi: reciprocal plus one FMA correction of the quotient
-    // (Markstein 1990), instead of a division per cell
-    const double nphi_d = (double)n_phi;
-    const double rphi = 1.0 / nphi_d;
+    const CellCtx c = cell_ctx(g, P, n_phi);
     double bl = -INFINITY;
     long long bc = LLONG_MAX;
     T bD = T(NAN), bs2 = T(NAN);
@@ -478,33 +552,13 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node8<T>
         }
         const int64_t cell = base + threadIdx.x;
         if (cell < n_cells) {
-            const double jd = (double)j;
-            const double q0 = jd * rphi;
-            const double phi = fma(fma(-q0, nphi_d, jd), rphi, q0);
+            const double phi = cell_phi(c, j);
             const Node8<T>* nd = nodes + (int64_t)d * g.n_t0;
-            const unsigned long long u0 = (unsigned long long)j * swp.u0;
-            // number of epochs with T <= t_last: integer estimate, then the
-            // exact comparisons of the definition
-            int64_t kk = u0 > ulast ? 0
-                                    : (int64_t)((float)(unsigned)((ulast - u0) >> 32) *
-                                                inv_ustep32) + 1;
-            while (kk > 0 &&
-                   okey(__dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)(kk - 1)), P))) >
-                       klast)
-                --kk;
-            while (okey(__dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, (double)kk), P))) <= klast)
-                ++kk;
-            const int64_t kmax = kk;
+            const unsigned long long u0 = (unsigned long long)j * c.swp.u0;
+            const int64_t kmax = cell_kmax(g, c, phi, u0);
             ExactAcc<T> a1;
             a1.init();
-            unsigned long long u = u0;
-            double kd = 0.0;
-            for (int64_t k = 0; k < kmax; ++k, u += swk.ustep, kd += 1.0) {
-                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(phi, kd), P));
-                T dk, sk2, lk;
-                int64_t i = guess_at(g, u);
-                if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a1.add(dk, sk2, lk);
-            }
+            cell_pass1<T>(g, nd, c, phi, u0, kmax, 0, 1, a1);
             const double best_now = fmax(bl, from_max_key(sh_best));
             if (a1.K > 0 && !a1.cannot_win(best_now)) {
                 const T s2 = T(1) / a1.s_inv.s;
@@ -520,14 +574,7 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node8<T>
             const Node8<T>* nd = nodes + (int64_t)qc.d * g.n_t0;
             ExactPen<T> a2;
             a2.init(qc.s2, qc.Dl);
-            unsigned long long u = qc.u0;
-            double kd = 0.0;
-            for (int k = 0; k < qc.kmax; ++k, u += swk.ustep, kd += 1.0) {
-                const double Tk = __dadd_rn(g.t_ref, __dmul_rn(__dadd_rn(qc.phi, kd), P));
-                T dk, sk2, lk;
-                int64_t i = guess_at(g, u);
-                if (event_exact<T>(g, nd, Tk, i, dk, sk2, lk)) a2.add(dk, sk2);
-            }
+            cell_pass2<T>(g, nd, c, qc.phi, qc.u0, qc.kmax, 0, 1, a2);
             const double lnp = qc.s_l - 0.5 * (a2.logsum() + (double)a2.quad.s);
             if (!(lnp == lnp)) continue;   // NaN never selected
             if (lnp > bl || (lnp == bl && qc.cell < bc)) {
@@ -562,6 +609,450 @@ k_fold_exact(FoldGeom g, const Node8<T>* __restrict__ nodes, int n_D,
                           sig_out, lnp_out);
 }
 
+// ------------------------------ FP64 path: FP32 screen, exact survivors
+// Every cell is first screened with FP32 events: an upper bound on its ln P
+// (the bound of cannot_win, tightened below) computed from FP32 values with
+// an error term that covers every rounding of the screen, on an epoch set
+// that is provably the exact path's.  Only cells whose bound reaches the
+// best ln P found so far are evaluated exactly (FP64 epochs and values, the
+// same code as the exact path); a skipped cell cannot be the argmax, so the
+// outputs are those of the exact evaluation of every cell.
+//
+// Tighter bound.  With x_k = sigma^2/s_k^2 and x_max = max_k x_k,
+//   sum (Delta_k - Delta)^2/(s_k^2 + sigma^2) >= q / (1 + x_max),
+//   q = sum (Delta_k - Delta)^2 / s_k^2 = S_dd - S_d^2/S_inv,
+// so ln P <= S_L + 1/2 - q / (2 (1 + x_max)).
+//
+// Epoch set.  Epoch positions are walked in 24.40 fixed point of the slot
+// grid (u = (T - t_ref)/dt), the epochs' own positions are stored on the same
+// scale, and the interval of an event is the last epoch position <= u.  The
+// walk differs from the FP64 epochs by at most e_pos (bounded per period
+// from the fixed-point rounding and the FP64 rounding of T), so the interval
+// is the exact path's whenever u is farther than delta >> e_pos from every
+// epoch; within delta of an epoch (or of t_last, for the epoch count) the
+// event's T is computed in FP64 exactly as the exact path does and the
+// interval is taken by the same comparisons.  The screen's epoch set and
+// intervals are therefore the exact path's.
+//
+// Error term.  An FP32 event value x (depth, sigma, gain) differs from the
+// FP64 one by at most cv (|x_i| + |x_{i+1}|) (node and slope rounding,
+// weight rounding and position error, the FMA), with |x_i| + |x_{i+1}| <=
+// 2|x| + |x_{i+1} - x_i| accumulated per cell.  Intervals whose end sigmas
+// differ by more than a factor 3 (or outside the other limits of the
+// screening record) are not screened, so |ds|/s <= 2 and the
+// relative error of each 1/s_k^2 is at most gam = 2.2 cv (2 + 2) + 6u; sums
+// of K positive terms carry at most (K + 2)u.  With these:
+//   S_L     <= sl + (cv + (K+2)u) sum (2|l_k| + |dl_k|)
+//   sqrt(q) >= sqrt(q_fp32_lo / (1 + gam + (K+2)u)) - cv sqrt(sum a_k^2/s_k^2)
+//   x_max   <= min(1, ivmax/sinv (1 + 4 gam + 2(K+2)u))
+// (triangle inequality in the 1/s^2-weighted norm for q).  Overflow or NaN
+// anywhere makes the bound +inf or NaN, which never skips a cell.
+
+struct ScreenGeom {
+    const ScreenRec* rec;              // duration-major rows of n_t0 records
+    const ulonglong2* vpair;           // (position of epoch i, of epoch i+1), 24.40
+                                       // slots from t_ref; the last .y is 2^64 - 1
+    int on;                            // screening allowed for this curve
+};
+
+// Node sigma of one (duration, epoch) in FP64 (NaN when invalid).
+template <typename T>
+__device__ __forceinline__ double sigma_at(const T* depth, const T* var, const T* gain,
+                                           int64_t o) {
+    return (double)node_sigma<T>(depth[o], var[o], gain[o]);
+}
+
+// Screening record (and, for the first duration row, the epoch position) of
+// epoch i of a curve with n epochs; gid indexes the (duration, epoch) arrays.
+template <typename T>
+__device__ __forceinline__ void make_screen(const T* __restrict__ depth,
+                                            const T* __restrict__ var,
+                                            const T* __restrict__ gain,
+                                            const double* __restrict__ t0, int64_t gid,
+                                            int64_t i, int64_t n, double gap_max, double dt,
+                                            ScreenRec* __restrict__ out,
+                                            ulonglong2* __restrict__ vpair,
+                                            bool write_vpos) {
+    // an interval needs both ends valid and a gap in (0, gap_max]
+    bool v0 = i + 1 < n;
+    if (v0) {
+        const double gap = t0[i + 1] - t0[i];
+        v0 = gap > 0.0 && gap <= gap_max && !isnan(sigma_at<T>(depth, var, gain, gid)) &&
+             !isnan(sigma_at<T>(depth, var, gain, gid + 1));
+    }
+    ScreenRec r;
+    unsigned flags = 0u;
+    const double d0 = (double)depth[gid], l0 = (double)gain[gid];
+    r.d = (float)d0;
+    r.l = (float)l0;
+    if (v0) {
+        const double s0 = sigma_at<T>(depth, var, gain, gid);
+        const double s1 = sigma_at<T>(depth, var, gain, gid + 1);
+        const double d1 = (double)depth[gid + 1], l1 = (double)gain[gid + 1];
+        const double gap = t0[i + 1] - t0[i];
+        r.s = (float)s0;
+        r.dd = (float)(d1 - d0);
+        r.ds = (float)(s1 - s0);
+        r.dl = (float)(l1 - l0);
+        r.wsc = (float)(9.313225746154785e-10 * dt / gap);   // 2^-30 dt / gap
+        // outside the error model: very close epochs, or values whose FP32
+        // sums could overflow
+        const bool odd = gap < 0.25 * dt || !(s0 >= 1e-12 && s0 <= 1e12) ||
+                         !(s1 >= 1e-12 && s1 <= 1e12) || !(s1 <= 3.0 * s0) ||
+                         !(s0 <= 3.0 * s1) || !(fabs(d0) <= 1e8 * s0) ||
+                         !(fabs(d1) <= 1e8 * s1) || !(fabs(l0) <= 1e20) || !(fabs(l1) <= 1e20);
+        if (odd) flags = 1u;
+    } else {
+        r.s = NAN;
+        r.dd = 0.f;
+        r.ds = 0.f;
+        r.dl = 0.f;
+        r.wsc = 0.f;
+    }
+    r.flags = flags;
+    out[gid] = r;
+    if (write_vpos) {
+        auto pos = [&](int64_t k) -> unsigned long long {
+            const double v = (t0[k] - t0[0]) / dt * 1099511627776.0;
+            return v < 9.0e18 ? (unsigned long long)llrint(v) : 9000000000000000000ull;
+        };
+        vpair[i] = make_ulonglong2(pos(i), i + 1 < n ? pos(i + 1) : ~0ull);
+    }
+}
+
+template <typename T>
+__global__ void k_screen(const T* __restrict__ depth, const T* __restrict__ var,
+                         const T* __restrict__ gain, const double* __restrict__ t0s,
+                         int64_t n_t0, int n_D, double gap_max, double dt,
+                         ScreenRec* __restrict__ rec, ulonglong2* __restrict__ vpair) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= n_t0 * (int64_t)n_D) return;
+    const int64_t i = gid % n_t0;
+    make_screen<T>(depth, var, gain, t0s, gid, i, n_t0, gap_max, dt, rec, vpair, gid < n_t0);
+}
+
+// Per-period constants of the screen.
+struct ScreenPeriod {
+    unsigned long long uph, ustep, ulast, delta;
+    float inv_ustep32;
+    float cv;       // error coefficient of an FP32 event value
+    float dw;       // delta as an interval weight (dt/gap <= 4)
+    bool on;
+};
+
+__device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const ScreenGeom& sg,
+                                                      double P, int64_t n_phi) {
+    ScreenPeriod sp;
+    const double SCALE = 1099511627776.0;   // 2^40
+    const double R = P * g.inv_dt;
+    const double span = (g.t_last - g.t_ref) * g.inv_dt;
+    sp.on = sg.on != 0 && R * SCALE < 4.0e18 && span < 8388608.0;
+    sp.uph = sp.ustep = sp.ulast = sp.delta = 0;
+    sp.inv_ustep32 = 0.f;
+    sp.cv = 0.f;
+    sp.dw = 0.f;
+    if (!sp.on) return sp;
+    sp.ustep = (unsigned long long)llrint(R * SCALE);
+    sp.uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
+    sp.ulast = sg.vpair[g.n_t0 - 1].x;
+    sp.inv_ustep32 = (float)(4294967296.0 / (double)sp.ustep);
+    // position error of the walk against the FP64 epochs, in 2^-40 slots:
+    // half a unit per phase and epoch step, the rounding of T, t0 and vpos
+    const double kb = span / R + 2.0;
+    const double e_pos = 0.5 * ((double)n_phi + kb) + 4.0 +
+                         8.881784197001252e-16 * (fabs(g.t_ref) + fabs(g.t_last) + P) *
+                             g.inv_dt * SCALE;
+    const double delta = 16.0 * e_pos + 1048576.0;          // + 2^-20 slot
+    sp.on = delta < 1.6e10;                                  // below 2^-6 slot
+    sp.delta = (unsigned long long)delta;
+    sp.dw = (float)(4.04 * delta / SCALE);
+    // weight error: 4 e_pos (dt/gap <= 4) plus 4 x the 2^-30-slot truncation
+    const double e_w = 4.0 * e_pos / SCALE + 3.725290298461914e-09;
+    sp.cv = (float)(8.0 * 5.9604644775390625e-08 + 2.0 * e_w);
+    return sp;
+}
+
+// Upper bound on ln P of cell (j, row rd) whose first epoch is at u0 (see
+// above): -inf when the cell has no event, +inf when an event falls on an
+// interval outside the screen's error model.
+__device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom& sg,
+                                             const ScreenRec* __restrict__ rd,
+                                             const ScreenPeriod& sp, const CellCtx& c,
+                                             int64_t j, unsigned long long u0) {
+    double phi = 0.0;
+    bool have_phi = false;
+    int64_t kmax = 0;
+    if (u0 <= sp.ulast) {
+        int64_t kk = (int64_t)((float)(unsigned)((sp.ulast - u0) >> 32) * sp.inv_ustep32);
+        while (kk > 0 && u0 + (unsigned long long)kk * sp.ustep > sp.ulast) --kk;
+        while (u0 + (unsigned long long)(kk + 1) * sp.ustep <= sp.ulast) ++kk;
+        kmax = kk + 1;
+    }
+    // the count of epochs with T <= t_last, exactly, when an epoch is near t_last
+    const unsigned long long unext = u0 + (unsigned long long)kmax * sp.ustep;
+    if (unext - sp.ulast < sp.delta ||
+        (kmax > 0 && sp.ulast - (unext - sp.ustep) < sp.delta)) {
+        phi = cell_phi(c, j);
+        have_phi = true;
+        kmax = cell_kmax(g, c, phi, u0);
+    }
+    float sinv = 0.f, sd = 0.f, sdd = 0.f, saa = 0.f, sl = 0.f, sabs = 0.f, ivmax = 0.f;
+    int K = 0;
+    unsigned long long u = u0;
+    const int64_t nb1 = g.n_bucket - 1;
+    int bnext = g.bucket[min((int64_t)(u >> 40), nb1)];
+    for (int64_t k = 0; k < kmax; ++k, u += sp.ustep) {
+        // interval guess from the bucket table (the next epoch's entry is
+        // fetched one iteration ahead), verified against the stored positions
+        int64_t i = bnext > 0 ? (int64_t)bnext - 1 : 0;
+        bnext = g.bucket[min((int64_t)((u + sp.ustep) >> 40), nb1)];
+        ulonglong2 v = sg.vpair[i];
+        ScreenRec r = rd[i];
+        if (u >= v.y || u < v.x) {
+            while (u >= v.y) v = sg.vpair[++i];
+            while (u < v.x) v = sg.vpair[--i];
+            r = rd[i];
+        }
+        long long sdu = (long long)(u - v.x);
+        float w = __int2float_rn((int)(sdu >> 10)) * r.wsc;
+        float s = fmaf(w, r.ds, r.s);
+        // within delta of either end (on a valid interval: w within dw of 0
+        // or 1, dw >= 4 delta in slots as dt/gap <= 4): the exact path's
+        // interval from FP64 T
+        const bool near = isnan(s) ? ((unsigned long long)sdu < sp.delta || v.y - u < sp.delta)
+                                   : (w < sp.dw || w > 1.f - sp.dw);
+        if (near) {
+            if (!have_phi) {
+                phi = cell_phi(c, j);
+                have_phi = true;
+            }
+            const int64_t ie = bracket_from(g, okey(epoch_time(g, c, phi, (double)k)), i);
+            if (ie != i) {
+                i = ie;
+                v = sg.vpair[i];
+                r = rd[i];
+                sdu = (long long)(u - v.x);
+                w = __int2float_rn((int)(sdu >> 10)) * r.wsc;
+                s = fmaf(w, r.ds, r.s);
+            }
+        }
+        if (r.flags) return INFINITY;
+        if (isnan(s)) continue;
+        const float dk = fmaf(w, r.dd, r.d);
+        const float lk = fmaf(w, r.dl, r.l);
+        const float iv = rcp32(s * s);
+        const float div = dk * iv;
+        sinv += iv;
+        sd += div;
+        sdd = fmaf(div, dk, sdd);
+        sl += lk;
+        const float ad = fmaf(2.f, fabsf(dk), fabsf(r.dd));
+        saa = fmaf(ad * ad, iv, saa);
+        sabs += fmaf(2.f, fabsf(lk), fabsf(r.dl));
+        ivmax = fmaxf(ivmax, iv);
+        ++K;
+    }
+    if (K == 0) return -INFINITY;
+    const float U = 5.9604645e-8f;                        // 2^-24
+    const float sk = (float)(K + 2) * U;
+    // |ds|/s <= 2 on a screened interval (adjacent sigmas within a factor 3)
+    const float gam = 2.2f * sp.cv * 4.f + 6.f * U;
+    const float qc = sdd - sd * sd / sinv;
+    const float qcl = qc - (float)(4 * K + 16) * U * sdd;
+    float q_lo = 0.f;
+    if (qcl > 0.f) {
+        const float a = sqrtf(qcl / (1.f + gam + sk));
+        const float e = 1.05f * sp.cv * sqrtf(saa * (1.f + 2.f * gam + sk));
+        if (a > e) q_lo = (a - e) * (a - e) * (1.f - 8.f * U);
+    }
+    const float x_hi = fminf(1.f, ivmax / sinv * (1.f + 4.f * gam + 2.f * sk + 8.f * U));
+    const float e_l = 1.05f * (sp.cv + sk) * sabs;
+    return sl + e_l + 0.5f - 0.5f * q_lo / (1.f + x_hi) + 8.f * U * (sabs + q_lo + 1.f);
+}
+
+// Exact ln P of one cell computed by a whole warp (lanes over epochs); used
+// only to seed the pruning threshold.
+__device__ __forceinline__ double exact_cell_warp(const FoldGeom& g,
+                                                  const Node8<double>* __restrict__ nd,
+                                                  const CellCtx& c, int64_t j) {
+    const int lane = threadIdx.x & 31;
+    const double phi = cell_phi(c, j);
+    const unsigned long long u0 = (unsigned long long)j * c.swp.u0;
+    const int64_t kmax = cell_kmax(g, c, phi, u0);
+    ExactAcc<double> a1;
+    a1.init();
+    cell_pass1<double>(g, nd, c, phi, u0, kmax, lane, 32, a1);
+    double s_inv = a1.s_inv.s, s_d = a1.s_d.s, s_l = a1.s_l.s;
+    int K = a1.K;
+    for (int o = 16; o > 0; o >>= 1) {
+        s_inv += __shfl_xor_sync(0xffffffffu, s_inv, o);
+        s_d += __shfl_xor_sync(0xffffffffu, s_d, o);
+        s_l += __shfl_xor_sync(0xffffffffu, s_l, o);
+        K += __shfl_xor_sync(0xffffffffu, K, o);
+    }
+    if (K == 0) return -INFINITY;
+    const double s2 = 1.0 / s_inv;
+    ExactPen<double> a2;
+    a2.init(s2, s2 * s_d);
+    cell_pass2<double>(g, nd, c, phi, u0, kmax, lane, 32, a2);
+    double pen = a2.logsum() + a2.quad.s;
+    for (int o = 16; o > 0; o >>= 1) pen += __shfl_xor_sync(0xffffffffu, pen, o);
+    return s_l - 0.5 * pen;
+}
+
+// One period of the FP64 path with the screen.  Surviving cells are queued
+// and evaluated exactly, one per thread, whenever a full block's worth has
+// gathered (and at the end); the first wave's best bound per warp is
+// evaluated first by the whole warp to seed the threshold.
+__device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const ScreenGeom& sg,
+                                                  const Node8<double>* __restrict__ nodes,
+                                                  int n_D, double P, int64_t p,
+                                                  double* __restrict__ Q_out,
+                                                  double* __restrict__ T0_out,
+                                                  int* __restrict__ Didx_out,
+                                                  double* __restrict__ dep_out,
+                                                  double* __restrict__ sig_out,
+                                                  double* __restrict__ lnp_out) {
+    __shared__ long long sh_qc[512];
+    __shared__ int sh_qd[512];
+    __shared__ int sh_nq;
+    __shared__ unsigned long long sh_sbest;
+    if (bad_period(P, g)) {
+        if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
+        return;
+    }
+    const int64_t n_phi = (int64_t)ceil(P / g.dt);
+    const ScreenPeriod sp = screen_period(g, sg, P, n_phi);
+    if (!sp.on) {
+        fold_exact_one<double, 8>(g, nodes, n_D, P, p, Q_out, T0_out, Didx_out, dep_out,
+                                  sig_out, lnp_out);
+        return;
+    }
+    const int64_t n_cells = n_phi * n_D;
+    const CellCtx c = cell_ctx(g, P, n_phi);
+    double bl = -INFINITY, bD = NAN, bs2 = NAN;
+    long long bc = LLONG_MAX;
+    if (threadIdx.x == 0) {
+        sh_nq = 0;
+        sh_sbest = max_key(-INFINITY);
+    }
+    __syncthreads();
+    int d = (int)(threadIdx.x / n_phi);
+    int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
+    for (int64_t base = 0; base < n_cells; base += blockDim.x, j += blockDim.x) {
+        while (j >= n_phi) {
+            j -= n_phi;
+            ++d;
+        }
+        const int64_t cell = base + threadIdx.x;
+        float ub = -INFINITY;
+        if (cell < n_cells)
+            ub = screen_cell(g, sg, sg.rec + (int64_t)d * g.n_t0, sp, c, j,
+                             (unsigned long long)j * sp.uph);
+        if (base == 0) {
+            // seed: each warp evaluates its lane with the largest finite bound
+            float v = (ub < INFINITY) ? ub : -INFINITY;
+            int src = threadIdx.x & 31;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int s2 = __shfl_xor_sync(0xffffffffu, src, o);
+                if (v2 > v || (v2 == v && s2 < src)) {
+                    v = v2;
+                    src = s2;
+                }
+            }
+            if (v > -INFINITY) {
+                const int pd = __shfl_sync(0xffffffffu, d, src);
+                const long long pj = __shfl_sync(0xffffffffu, (long long)j, src);
+                const double lnp = exact_cell_warp(g, nodes + (int64_t)pd * g.n_t0, c, pj);
+                if ((threadIdx.x & 31) == 0 && lnp == lnp && lnp > -INFINITY)
+                    atomicMax(&sh_sbest, max_key(lnp - 1e-9 * (1.0 + fabs(lnp))));
+            }
+            __syncthreads();
+        }
+        if (cell < n_cells) {
+            const double best_now = fmax(bl, from_max_key(sh_sbest));
+            // a cell without events (bound -inf) is never the argmax; NaN survives
+            if (!(ub == -INFINITY) && !(ub < __double2float_rd(best_now))) {
+                const int q = atomicAdd(&sh_nq, 1);
+                sh_qc[q] = cell;
+                sh_qd[q] = d;
+            }
+        }
+        __syncthreads();
+        const int nq = sh_nq;
+        const bool last = base + blockDim.x >= n_cells;
+        __syncthreads();            // every thread has read nq
+        if (nq >= (int)blockDim.x || (last && nq > 0)) {
+            const int take = last ? nq : (int)blockDim.x;
+            for (int q = threadIdx.x; q < take; q += blockDim.x) {
+                const long long qcell = sh_qc[q];
+                const int qd = sh_qd[q];
+                const int64_t qj = qcell - (int64_t)qd * n_phi;
+                const Node8<double>* nd = nodes + (int64_t)qd * g.n_t0;
+                const double phi = cell_phi(c, qj);
+                const unsigned long long u0 = (unsigned long long)qj * c.swp.u0;
+                const int64_t kmax = cell_kmax(g, c, phi, u0);
+                ExactAcc<double> a1;
+                a1.init();
+                cell_pass1<double>(g, nd, c, phi, u0, kmax, 0, 1, a1);
+                if (a1.K == 0 || a1.cannot_win(fmax(bl, from_max_key(sh_sbest)))) continue;
+                const double s2 = 1.0 / a1.s_inv.s;
+                const double Dl = s2 * a1.s_d.s;
+                ExactPen<double> a2;
+                a2.init(s2, Dl);
+                cell_pass2<double>(g, nd, c, phi, u0, kmax, 0, 1, a2);
+                const double lnp = a1.s_l.s - 0.5 * (a2.logsum() + a2.quad.s);
+                if (!(lnp == lnp)) continue;   // NaN never selected
+                if (lnp > bl || (lnp == bl && qcell < bc)) {
+                    bl = lnp;
+                    bc = qcell;
+                    bD = Dl;
+                    bs2 = s2;
+                }
+                atomicMax(&sh_sbest, max_key(lnp));
+            }
+            __syncthreads();
+            const int rest = nq - take;
+            long long c2 = 0;
+            int d2 = 0;
+            if ((int)threadIdx.x < rest) {
+                c2 = sh_qc[take + threadIdx.x];
+                d2 = sh_qd[take + threadIdx.x];
+            }
+            __syncthreads();
+            if ((int)threadIdx.x < rest) {
+                sh_qc[threadIdx.x] = c2;
+                sh_qd[threadIdx.x] = d2;
+            }
+            if (threadIdx.x == 0) sh_nq = rest;
+            __syncthreads();
+        }
+    }
+    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
+    if (bc != LLONG_MAX) best = Best{bl, bc, bD, sqrt(bs2)};
+    const Best b = block_argmax(best);
+    if (threadIdx.x == 0)
+        write_best(b, p, n_phi, g.t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
+}
+
+// resident blocks per SM the register allocation is sized for
+#ifndef NU_SCREEN_MIN_BLOCKS
+#define NU_SCREEN_MIN_BLOCKS 4
+#endif
+
+__global__ void __launch_bounds__(256, NU_SCREEN_MIN_BLOCKS)
+k_fold_screened(FoldGeom g, ScreenGeom sg, const Node8<double>* __restrict__ nodes, int n_D,
+                const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
+                double* __restrict__ T0_out, int* __restrict__ Didx_out,
+                double* __restrict__ dep_out, double* __restrict__ sig_out,
+                double* __restrict__ lnp_out) {
+    const int64_t p = blockIdx.x;
+    if (p >= n_P) return;
+    fold_screened_one(g, sg, nodes, n_D, periods[p], p, Q_out, T0_out, Didx_out, dep_out,
+                      sig_out, lnp_out);
+}
+
 // ---------------------------------------- slot path (mixed, regular grids)
 struct SlotEvent {
     float d, s, l;
@@ -585,12 +1076,14 @@ __device__ __forceinline__ SlotEvent slot_event(const Node4<float>* __restrict__
 struct SlotPass1 {
     KSum<float> s_inv, s_d, s_l;
     float s_dd;            // sum Delta_k^2 / s_k^2 (bound only)
+    float ivmax;           // max 1/s_k^2 (bound only)
     int K;
     __device__ __forceinline__ void init() {
         s_inv.init();
         s_d.init();
         s_l.init();
         s_dd = 0.f;
+        ivmax = 0.f;
         K = 0;
     }
     __device__ __forceinline__ void add(const SlotEvent& e) {
@@ -600,6 +1093,7 @@ struct SlotPass1 {
         s_inv.add(iv);
         s_d.add(div);
         s_dd = fmaf(div, e.d, s_dd);
+        ivmax = fmaxf(ivmax, iv);
         s_l.add(e.l);
         ++K;
     }
@@ -694,7 +1188,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                     fmaxf(bl, kb ? __uint_as_float((kb >> 31) ? (kb & 0x7fffffffu) : ~kb)
                                  : -INFINITY);
                 if (p1.K > 0 &&
-                    !cannot_win_f(p1.s_l.s, p1.s_inv.s, p1.s_d.s, p1.s_dd, best_now)) {
+                    !cannot_win_f(p1.s_l.s, p1.s_inv.s, p1.s_d.s, p1.s_dd, p1.ivmax, best_now)) {
                     const float s2 = 1.0f / p1.s_inv.s;
                     const int q = atomicAdd(&sh_nq, 1);
                     sh_q[q] = QCell<float>{0.0, u0, (long long)cell, (double)p1.s_l.s, s2,
@@ -760,7 +1254,8 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
 template <int KIND>
 __global__ void __launch_bounds__(256)
 k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restrict__ t,
-             const void* __restrict__ nodes, const int* __restrict__ bucket,
+             const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
+             const ulonglong2* __restrict__ vpair, const int* __restrict__ bucket,
              const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
              const double* __restrict__ periods, int64_t n_P, unsigned long long* counter,
              double* __restrict__ Q_out, double* __restrict__ T0_out,
@@ -786,10 +1281,12 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
         } else {
             FoldGeom gg{t + fs.s_off, fs.n_t0, fs.t_ref, fs.t_last, dt, 1.0 / dt,
                         gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
-            if (KIND == 0)
-                fold_exact_one<double, 8>(gg, (const Node8<double>*)nodes + fs.s_off * n_D,
-                                          n_D, periods[p], o, Q_out, T0_out, Didx_out,
-                                          dep_out, sig_out, lnp_out);
+            if (KIND == 0) {
+                const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off, fs.screen};
+                fold_screened_one(gg, sg, (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
+                                  periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
+                                  lnp_out);
+            }
             else
                 fold_exact_one<float, 8>(gg, (const Node8<float>*)nodes + fs.s_off * n_D, n_D,
                                          periods[p], o, Q_out, T0_out, Didx_out, dep_out,
@@ -815,6 +1312,27 @@ __global__ void k_nodes_batch(const T* __restrict__ depth, const T* __restrict__
     const int64_t s0 = s_off[lo], ng = s_off[lo + 1] - s0;
     const int64_t i = (gid - s0 * n_D) % ng;
     nodes[gid] = make_node8<T>(depth, var, gain, t + s0, gid, i, ng, gap_max);
+}
+
+template <typename T>
+__global__ void k_screen_batch(const T* __restrict__ depth, const T* __restrict__ var,
+                               const T* __restrict__ gain, const double* __restrict__ t,
+                               const FoldSeg* __restrict__ segs, int n_seg,
+                               const int64_t* __restrict__ s_off, int n_D, double gap_max,
+                               double dt, ScreenRec* __restrict__ rec,
+                               ulonglong2* __restrict__ vpair) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= s_off[n_seg] * (int64_t)n_D) return;
+    int lo = 0, hi = n_seg;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] * (int64_t)n_D <= gid) lo = mid; else hi = mid;
+    }
+    if (!segs[lo].screen) return;
+    const int64_t s0 = s_off[lo], ng = s_off[lo + 1] - s0;
+    const int64_t i = (gid - s0 * n_D) % ng;
+    make_screen<T>(depth, var, gain, t + s0, gid, i, ng, gap_max, dt, rec, vpair + s0,
+                   gid - s0 * n_D < ng);
 }
 
 __global__ void k_buckets_batch(const double* __restrict__ t, const FoldSeg* __restrict__ segs,
@@ -903,6 +1421,7 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
         f.n_slots = f.n_bucket + 2;
         f.use_slots = (!fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span < 4.0e6 &&
                        !irregular[g]) ? 1 : 0;
+        f.screen = (fp64 && gap_factor < 2.0 && span < 8.0e6) ? 1 : 0;
         f.bucket_off = fb.n_bucket_total;
         fb.n_bucket_total += f.use_slots ? 0 : f.n_bucket;
         f.rec_off = fb.n_rec_total;
@@ -919,11 +1438,18 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
     int launched = 0;
     const int64_t ngrid = n_total * (int64_t)n_D;
     if (fb.any_exact) {
-        if (fp64)
+        if (fp64) {
+            const ExactLayout L = exact_layout(n_total, n_D, true);
             k_nodes_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
                 n_seg, s_off_dev, n_D, gap_factor * dt, (Node8<double>*)nodes);
-        else
+            k_screen_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
+                n_seg, s_off_dev, n_D, gap_factor * dt, dt,
+                (ScreenRec*)((char*)nodes + L.off_screen),
+                (ulonglong2*)((char*)nodes + L.off_vpos));
+            ++launched;
+        } else
             k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
                 s_off_dev, n_D, gap_factor * dt, (Node8<float>*)nodes);
@@ -943,26 +1469,35 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
 
 // The persistent fold kernels; counter[0..1] must be zero.  blocks_per_sm
 // and threads come from the autotuner.
-int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg, bool fp64,
-                      const double* t, const void* nodes, const int* bucket,
-                      const Node4<float>* rec, int n_D, double dt, double gap_factor,
-                      const double* periods, int64_t n_P, unsigned long long* counter,
-                      int grid, int threads, double* Q, double* T0, int* Didx, double* dep,
-                      double* sig, double* lnp, cudaStream_t st) {
+int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
+                      int64_t n_total, bool fp64, const double* t, const void* nodes,
+                      const int* bucket, const Node4<float>* rec, int n_D, double dt,
+                      double gap_factor, const double* periods, int64_t n_P,
+                      unsigned long long* counter, int grid, int threads, double* Q,
+                      double* T0, int* Didx, double* dep, double* sig, double* lnp,
+                      cudaStream_t st) {
     int launched = 0;
+    const ExactLayout L = exact_layout(n_total, n_D, fp64);
+    const ScreenRec* screen = fp64 ? (const ScreenRec*)((const char*)nodes + L.off_screen)
+                                   : nullptr;
+    const ulonglong2* vpair =
+        fp64 ? (const ulonglong2*)((const char*)nodes + L.off_vpos) : nullptr;
     if (fb.any_exact) {
         if (fp64)
-            k_fold_batch<0><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, bucket, rec,
+            k_fold_batch<0><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, screen, vpair,
+                                                      bucket, rec,
                                                       n_D, dt, gap_factor, periods, n_P,
                                                       counter, Q, T0, Didx, dep, sig, lnp);
         else
-            k_fold_batch<1><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, bucket, rec,
+            k_fold_batch<1><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, screen, vpair,
+                                                      bucket, rec,
                                                       n_D, dt, gap_factor, periods, n_P,
                                                       counter, Q, T0, Didx, dep, sig, lnp);
         ++launched;
     }
     if (fb.any_slots) {
-        k_fold_batch<2><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, bucket, rec, n_D,
+        k_fold_batch<2><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, screen, vpair,
+                                                  bucket, rec, n_D,
                                                   dt, gap_factor, periods, n_P, counter + 1, Q,
                                                   T0, Didx, dep, sig, lnp);
         ++launched;
@@ -979,6 +1514,133 @@ int launch_slots_test(const double* t, const int64_t* s_off_dev, int n_seg, int6
 
 }  // namespace nu
 
+// ------------------------------------------------ single-curve host side
+namespace nu {
+
+// Scratch layout of the single-curve fold.
+struct SingleLayout {
+    ExactLayout el;
+    size_t exact, bucket, slot_of, flag, rec, total;
+};
+
+static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool fp64) {
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    SingleLayout L;
+    L.el = exact_layout(n_t0, n_D, fp64);
+    const int64_t n_slots = n_bucket + 2;          // slot records, NaN padded
+    L.exact = 0;
+    L.bucket = L.exact + L.el.total;
+    L.slot_of = L.bucket + al((size_t)n_bucket * sizeof(int));
+    L.flag = L.slot_of + al((size_t)n_t0 * sizeof(int));
+    L.rec = L.flag + 256;
+    L.total = L.rec + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>)));
+    return L;
+}
+
+// Enqueue the fold of one light curve on st with its scratch at `scratch`
+// (laid out by single_layout).  The mixed-precision slot test reads one flag
+// back (one synchronisation of st).
+static nu_status single_fold(const char* who, char* scratch, const SingleLayout& L,
+                             const double* t0s_dev, int64_t n_t0, int n_D, const void* depth_dev,
+                             const void* var_dev, const void* dlnl_dev, bool fp64,
+                             const double* periods_dev, int64_t n_P, double phase_step,
+                             double gap_factor, double t_ref, double t_last, int64_t n_bucket,
+                             cudaStream_t st, double* Q_dev, double* T0_dev, int32_t* D_idx_dev,
+                             double* depth_out_dev, double* sigma_out_dev, double* lnP_dev) {
+    const double span_steps = (t_last - t_ref) / phase_step;
+    const int64_t ngrid = n_t0 * (int64_t)n_D;
+    const int64_t n_slots = n_bucket + 2;
+    void* nodes = scratch + L.exact;
+    int* bucket = (int*)(scratch + L.bucket);
+    int* slot_of = (int*)(scratch + L.slot_of);
+    int* flag = (int*)(scratch + L.flag);
+    Node4<float>* rec = (Node4<float>*)(scratch + L.rec);
+    int launched = 0;
+    cudaError_t e = cudaSuccess;
+    // the slot path needs a regular grid and a gap rule that only joins
+    // neighbouring slots (1 < gap_factor < 2)
+    bool use_slots = !fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span_steps < 4.0e6;
+    if (use_slots) {
+        int irregular = 0;
+        e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+        k_slots<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, 1.0 / phase_step,
+                                                  slot_of, flag);
+        ++launched;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&irregular, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            count_launches(launched);
+            return cuda_fail(e, (std::string(who) + ": slot test").c_str());
+        }
+        use_slots = irregular == 0;
+    }
+    if (use_slots) {
+        const int64_t nrec = n_slots * n_D;
+        k_fill_nan<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec);
+        k_slot_fill<<<div_up(ngrid, 256), 256, 0, st>>>(
+            (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
+            n_t0, n_D, n_slots, rec);
+        k_fold_slots<8><<<(unsigned)n_P, 256, 0, st>>>(rec, n_slots, n_D, phase_step, t_ref,
+                                                      t_last, periods_dev, n_P, Q_dev, T0_dev,
+                                                      D_idx_dev, depth_out_dev, sigma_out_dev,
+                                                      lnP_dev);
+        launched += 3;
+    } else {
+        k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
+                                                        n_bucket, bucket);
+        FoldGeom g{t0s_dev, n_t0, t_ref, t_last, phase_step, 1.0 / phase_step,
+                   gap_factor * phase_step, bucket, n_bucket};
+        if (fp64) {
+            ScreenRec* srec = (ScreenRec*)(scratch + L.exact + L.el.off_screen);
+            ulonglong2* vpair = (ulonglong2*)(scratch + L.exact + L.el.off_vpos);
+            const ScreenGeom sg{srec, vpair, (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0};
+            k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
+                t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
+            k_screen<double><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
+                t0s_dev, n_t0, n_D, g.gap_max, phase_step, srec, vpair);
+            k_fold_screened<<<(unsigned)n_P, 256, 0, st>>>(
+                g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+            launched += 4;
+        } else {
+            k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
+                (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
+                t0s_dev, n_t0, n_D, g.gap_max, (Node8<float>*)nodes);
+            k_fold_exact<float, 8><<<(unsigned)n_P, 256, 0, st>>>(
+                g, (const Node8<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+            launched += 3;
+        }
+    }
+    count_launches(launched);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, (std::string(who) + ": launch").c_str());
+    return NU_OK;
+}
+
+static nu_status check_args(const char* who, const double* t0s_dev, int64_t n_t0, int n_D,
+                            const void* depth_dev, const void* var_dev, const void* dlnl_dev,
+                            nu_precision prec, const double* periods_dev, int64_t n_P,
+                            double gap_factor, double* Q_dev, double* T0_dev,
+                            int32_t* D_idx_dev, double* depth_out_dev, double* sigma_out_dev,
+                            double* lnP_dev) {
+    if (!t0s_dev || !depth_dev || !var_dev || !dlnl_dev || !periods_dev || !Q_dev ||
+        !T0_dev || !D_idx_dev || !depth_out_dev || !sigma_out_dev || !lnP_dev)
+        return fail(NU_EINVAL, "%s: null array", who);
+    if (n_t0 < 2 || n_D < 1 || n_P < 1)
+        return fail(NU_EINVAL, "%s: need n_t0 >= 2, n_D >= 1, n_P >= 1", who);
+    if (prec != NU_FP64 && prec != NU_MIXED) return fail(NU_EINVAL, "%s: unknown precision", who);
+    if (!(gap_factor > 0.0)) return fail(NU_EINVAL, "%s: gap_factor <= 0", who);
+    if (n_t0 > 2000000000LL) return fail(NU_EINVAL, "%s: n_t0 too large", who);
+    if (n_P > 2147483647LL) return fail(NU_EINVAL, "%s: n_P too large", who);
+    return NU_OK;
+}
+
+}  // namespace nu
+
 using namespace nu;
 
 extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
@@ -990,21 +1652,17 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
                                         double* Q_dev, double* T0_dev, int32_t* D_idx_dev,
                                         double* depth_out_dev, double* sigma_out_dev,
                                         double* lnP_dev) {
-    if (!t0s_dev || !depth_dev || !var_dev || !dlnl_dev || !periods_dev || !Q_dev ||
-        !T0_dev || !D_idx_dev || !depth_out_dev || !sigma_out_dev || !lnP_dev)
-        return fail(NU_EINVAL, "nu_periodic_search: null array");
+    const char* who = "nu_periodic_search";
     (void)Ds_host;
-    if (n_t0 < 2 || n_D < 1 || n_P < 1)
-        return fail(NU_EINVAL, "nu_periodic_search: need n_t0 >= 2, n_D >= 1, n_P >= 1");
-    if (prec != NU_FP64 && prec != NU_MIXED)
-        return fail(NU_EINVAL, "nu_periodic_search: unknown precision");
-    if (!(gap_factor > 0.0)) return fail(NU_EINVAL, "nu_periodic_search: gap_factor <= 0");
-    if (n_t0 > 2000000000LL) return fail(NU_EINVAL, "nu_periodic_search: n_t0 too large");
+    nu_status s = check_args(who, t0s_dev, n_t0, n_D, depth_dev, var_dev, dlnl_dev, prec,
+                             periods_dev, n_P, gap_factor, Q_dev, T0_dev, D_idx_dev,
+                             depth_out_dev, sigma_out_dev, lnP_dev);
+    if (s != NU_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     // grid end points (host copies; the step, when not given, is the median
     // spacing of the epochs)
-    std::vector<double> ends(2);
+    double ends[2];
     double t_ref, t_last;
     if (!(phase_step > 0.0)) {
         std::vector<double> h(n_t0);
@@ -1035,89 +1693,25 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
     if (span_steps > 1.0e9) return fail(NU_EINVAL, "nu_periodic_search: phase grid too fine");
     const int64_t n_bucket = (int64_t)span_steps + 2;
     const bool fp64 = prec == NU_FP64;
-    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
-    const int64_t ngrid = n_t0 * (int64_t)n_D;
-    const int64_t n_slots = n_bucket + 2;          // slot records, NaN padded
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_nodes = al((size_t)ngrid * 8 * esz);
-    const size_t b_bucket = al((size_t)n_bucket * sizeof(int));
-    const size_t b_slot_of = al((size_t)n_t0 * sizeof(int));
-    const size_t b_flag = 256;
-    const size_t b_rec = fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>));
+    const SingleLayout L = single_layout(n_t0, n_D, n_bucket, fp64);
     pool_keep_memory();
     char* scratch = nullptr;
-    e = cudaMallocAsync((void**)&scratch, b_nodes + b_bucket + b_slot_of + b_flag + b_rec, st);
+    e = cudaMallocAsync((void**)&scratch, L.total, st);
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: cudaMallocAsync");
-    void* nodes = scratch;
-    int* bucket = (int*)(scratch + b_nodes);
-    int* slot_of = (int*)(scratch + b_nodes + b_bucket);
-    int* flag = (int*)(scratch + b_nodes + b_bucket + b_slot_of);
-    Node4<float>* rec = (Node4<float>*)(scratch + b_nodes + b_bucket + b_slot_of + b_flag);
-    int launched = 0;
-    // the slot path needs a regular grid and a gap rule that only joins
-    // neighbouring slots (1 < gap_factor < 2)
-    bool use_slots = !fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span_steps < 4.0e6;
-    if (use_slots) {
-        int irregular = 0;
-        e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-        k_slots<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, 1.0 / phase_step,
-                                                  slot_of, flag);
-        ++launched;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&irregular, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(scratch, st);
-            return cuda_fail(e, "nu_periodic_search: slot test");
-        }
-        use_slots = irregular == 0;
-    }
-    if (use_slots) {
-        const int64_t nrec = n_slots * n_D;
-        k_fill_nan<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec);
-        k_slot_fill<<<div_up(ngrid, 256), 256, 0, st>>>(
-            (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
-            n_t0, n_D, n_slots, rec);
-        k_fold_slots<8><<<(unsigned)n_P, 256, 0, st>>>(rec, n_slots, n_D, phase_step, t_ref,
-                                                      t_last, periods_dev, n_P, Q_dev, T0_dev,
-                                                      D_idx_dev, depth_out_dev, sigma_out_dev,
-                                                      lnP_dev);
-        launched += 3;
-    } else {
-        k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
-                                                        n_bucket, bucket);
-        FoldGeom g{t0s_dev, n_t0, t_ref, t_last, phase_step, 1.0 / phase_step,
-                   gap_factor * phase_step, bucket, n_bucket};
-        if (fp64) {
-            k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
-                (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
-            k_fold_exact<double, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
-                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-        } else {
-            k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
-                (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node8<float>*)nodes);
-            k_fold_exact<float, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node8<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
-                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-        }
-        launched += 3;
-    }
-    count_launches(launched);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: launch");
+    s = single_fold(who, scratch, L, t0s_dev, n_t0, n_D, depth_dev, var_dev, dlnl_dev, fp64,
+                    periods_dev, n_P, phase_step, gap_factor, t_ref, t_last, n_bucket, st,
+                    Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
     e = cudaFreeAsync(scratch, st);
+    if (s != NU_OK) return s;
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search: cudaFreeAsync");
     return NU_OK;
 }
 
 // ------------------------------------------------ allocation-free variant
 // nu_periodic_search_noalloc runs the same kernels as nu_periodic_search but
-// takes its scratch (packed epoch records, bucket table, slot table, flag)
-// from the file-scope device array below instead of the stream-ordered pool,
-// for callers that must not allocate device memory.  The array is part of the
+// takes its scratch (epoch records, bucket table, slot table, flag) from the
+// file-scope device array below instead of the stream-ordered pool, for
+// callers that must not allocate device memory.  The array is part of the
 // library image: every GPU that loads the library holds it until the process
 // exits.  Its address is looked up once per device (cudaGetSymbolAddress with
 // that device current) on the first call made on the device.
@@ -1159,23 +1753,17 @@ extern "C" nu_status nu_periodic_search_noalloc(const double* t0s_dev, int64_t n
                                                 void* stream, double* Q_dev, double* T0_dev,
                                                 int32_t* D_idx_dev, double* depth_out_dev,
                                                 double* sigma_out_dev, double* lnP_dev) {
+    const char* who = "nu_periodic_search_noalloc";
     (void)Ds_host;
-    if (!t0s_dev || !depth_dev || !var_dev || !dlnl_dev || !periods_dev || !Q_dev ||
-        !T0_dev || !D_idx_dev || !depth_out_dev || !sigma_out_dev || !lnP_dev)
-        return fail(NU_EINVAL, "nu_periodic_search_noalloc: null array");
-    if (n_t0 < 2 || n_D < 1 || n_P < 1)
-        return fail(NU_EINVAL, "nu_periodic_search_noalloc: need n_t0 >= 2, n_D >= 1, n_P >= 1");
-    if (prec != NU_FP64 && prec != NU_MIXED)
-        return fail(NU_EINVAL, "nu_periodic_search_noalloc: unknown precision");
-    if (!(gap_factor > 0.0))
-        return fail(NU_EINVAL, "nu_periodic_search_noalloc: gap_factor <= 0");
+    nu_status s = check_args(who, t0s_dev, n_t0, n_D, depth_dev, var_dev, dlnl_dev, prec,
+                             periods_dev, n_P, gap_factor, Q_dev, T0_dev, D_idx_dev,
+                             depth_out_dev, sigma_out_dev, lnP_dev);
+    if (s != NU_OK) return s;
     if (!(phase_step > 0.0) || !std::isfinite(phase_step))
         return fail(NU_EINVAL, "nu_periodic_search_noalloc: phase_step must be given (> 0)");
-    if (n_t0 > 2000000000LL)
-        return fail(NU_EINVAL, "nu_periodic_search_noalloc: n_t0 too large");
     void* base = nullptr;
-    nu_status ss = noalloc_scratch(&base);
-    if (ss != NU_OK) return ss;
+    s = noalloc_scratch(&base);
+    if (s != NU_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     double ends[2];
     cudaError_t e = cudaMemcpyAsync(&ends[0], t0s_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1191,76 +1779,13 @@ extern "C" nu_status nu_periodic_search_noalloc(const double* t0s_dev, int64_t n
         return fail(NU_EINVAL, "nu_periodic_search_noalloc: phase grid too fine");
     const int64_t n_bucket = (int64_t)span_steps + 2;
     const bool fp64 = prec == NU_FP64;
-    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
-    const int64_t ngrid = n_t0 * (int64_t)n_D;
-    const int64_t n_slots = n_bucket + 2;
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_nodes = al((size_t)ngrid * 8 * esz);
-    const size_t b_bucket = al((size_t)n_bucket * sizeof(int));
-    const size_t b_slot_of = al((size_t)n_t0 * sizeof(int));
-    const size_t b_flag = 256;
-    const size_t b_rec = fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>));
-    const size_t need = b_nodes + b_bucket + b_slot_of + b_flag + b_rec;
-    if (need > NU_NOALLOC_SCRATCH_BYTES)
+    const SingleLayout L = single_layout(n_t0, n_D, n_bucket, fp64);
+    if (L.total > NU_NOALLOC_SCRATCH_BYTES)
         return fail(NU_EINVAL,
                     "nu_periodic_search_noalloc: this grid needs %zu bytes of scratch, more "
                     "than the fixed %llu bytes; use nu_periodic_search",
-                    need, (unsigned long long)NU_NOALLOC_SCRATCH_BYTES);
-    char* scratch = (char*)base;
-    void* nodes = scratch;
-    int* bucket = (int*)(scratch + b_nodes);
-    int* slot_of = (int*)(scratch + b_nodes + b_bucket);
-    int* flag = (int*)(scratch + b_nodes + b_bucket + b_slot_of);
-    Node4<float>* rec = (Node4<float>*)(scratch + b_nodes + b_bucket + b_slot_of + b_flag);
-    int launched = 0;
-    bool use_slots = !fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span_steps < 4.0e6;
-    if (use_slots) {
-        int irregular = 0;
-        e = cudaMemsetAsync(flag, 0, sizeof(int), st);   // the array keeps old contents
-        k_slots<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, 1.0 / phase_step,
-                                                  slot_of, flag);
-        ++launched;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&irregular, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: slot test");
-        use_slots = irregular == 0;
-    }
-    if (use_slots) {
-        const int64_t nrec = n_slots * n_D;
-        k_fill_nan<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec);
-        k_slot_fill<<<div_up(ngrid, 256), 256, 0, st>>>(
-            (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
-            n_t0, n_D, n_slots, rec);
-        k_fold_slots<8><<<(unsigned)n_P, 256, 0, st>>>(rec, n_slots, n_D, phase_step, t_ref,
-                                                      t_last, periods_dev, n_P, Q_dev, T0_dev,
-                                                      D_idx_dev, depth_out_dev, sigma_out_dev,
-                                                      lnP_dev);
-        launched += 3;
-    } else {
-        k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
-                                                        n_bucket, bucket);
-        FoldGeom g{t0s_dev, n_t0, t_ref, t_last, phase_step, 1.0 / phase_step,
-                   gap_factor * phase_step, bucket, n_bucket};
-        if (fp64) {
-            k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
-                (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
-            k_fold_exact<double, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
-                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-        } else {
-            k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
-                (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, (Node8<float>*)nodes);
-            k_fold_exact<float, 8><<<(unsigned)n_P, 256, 0, st>>>(
-                g, (const Node8<float>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
-                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-        }
-        launched += 3;
-    }
-    count_launches(launched);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: launch");
-    return NU_OK;
+                    L.total, (unsigned long long)NU_NOALLOC_SCRATCH_BYTES);
+    return single_fold(who, (char*)base, L, t0s_dev, n_t0, n_D, depth_dev, var_dev, dlnl_dev,
+                       fp64, periods_dev, n_P, phase_step, gap_factor, t_ref, t_last, n_bucket,
+                       st, Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
 }

@@ -159,3 +159,37 @@ def test_fold_invalid_periods_are_nan():
         gpu = _gpu_fold(t0s, np.ones(1), g, periods, prec, phase_step=synth.CADENCE_DAYS)
         assert np.isnan(gpu["Q"][1:4]).all() and (gpu["D_idx"][1:4] == -1).all()
         assert np.isfinite(gpu["Q"][[0, 4]]).all()
+
+
+@pytest.mark.parametrize("offset", [0.0, 2000.0])
+def test_fold_fp64_screen_hard_cases(offset):
+    """FP64 fold on grids built to stress the FP32 screen of the exact path:
+    periods that are whole multiples of the step (epochs land on samples and
+    on the edges of gaps and NaN holes), epochs far from zero, irregular
+    epochs with near-coincident pairs, neighbours whose variances differ by
+    orders of magnitude, and gains consistent with the depths (strong
+    pruning) next to unrelated ones.  Every period is compared."""
+    rng = np.random.default_rng(41)
+    dt = synth.CADENCE_DAYS
+    base = np.concatenate([np.arange(600), np.arange(640, 1300), np.arange(1302, 1500)])
+    t0s = offset + base * dt
+    t0s[5::97] += 0.9 * dt          # near-coincident pairs (gap 0.1 dt)
+    t0s = np.sort(t0s)
+    n = len(t0s)
+    var = rng.uniform(1e-8, 5e-8, (4, n))
+    var[1, ::53] *= 1e4             # isolated very noisy samples
+    depth = rng.normal(0, 1e-4, (4, n))
+    depth[:, 300:310] += 2e-3       # one strong event
+    dlnl = depth ** 2 / (2 * var)
+    dlnl[3] = rng.uniform(0, 8, n)  # unrelated gains in the last row
+    depth[2, 100:110] = np.nan
+    var[0, 598:603] = np.nan        # hole next to the first gap
+    g = dict(depth=depth, var=var, dlnl=dlnl)
+    periods = np.concatenate([np.arange(37, 400, 3) * dt,
+                              np.linspace(0.05, 1.2, 150), [1.9, 2.05]])
+    ora = periodic.periodic_search(t0s, depth, var, dlnl, periods, dt)
+    gpu = _gpu_fold(t0s, np.ones(4), g, periods, "fp64", phase_step=dt)
+    wl, wq, differ = periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, dt,
+                                      FP64_TOL, FP64_TOL, periodic.fold_period)
+    print(f"fp64 screen hard cases offset={offset}: lnP err {wl:.2e}, Q err {wq:.2e}, "
+          f"ties {differ}")
