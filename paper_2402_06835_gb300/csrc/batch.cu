@@ -201,6 +201,9 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t f_nodes = foff; foff += fbat.any_exact ? exact_layout(N, n_D, fp64).total : 0;
     const size_t f_buck = foff;  foff += al((size_t)(fbat.n_bucket_total + 1) * 4);
     const size_t f_rec = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(Node4<float>));
+    const size_t f_srec = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(ScreenRec));
+    const size_t f_slot = foff;  foff += fp64 ? al((size_t)N * sizeof(int)) : 0;
+    const size_t f_reg = foff;   foff += al((size_t)n_lc * 2 * sizeof(unsigned));
     e = cudaMallocAsync((void**)&fold_mem, foff, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(fold_mem + f_segs, fbat.segs.data(), fbat.segs.size() * sizeof(FoldSeg),
@@ -211,9 +214,9 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         return cuda_fail(e, "nu_batch_search: fold setup");
     }
     const FoldSeg* fsegs = (const FoldSeg*)(fold_mem + f_segs);
-    void* nodes = fold_mem + f_nodes;
-    int* bucket = (int*)(fold_mem + f_buck);
-    Node4<float>* rec = (Node4<float>*)(fold_mem + f_rec);
+    const FoldScratch fsc{fold_mem + f_nodes, (int*)(fold_mem + f_buck),
+                          (Node4<float>*)(fold_mem + f_rec), (ScreenRec*)(fold_mem + f_srec),
+                          (int*)(fold_mem + f_slot), (unsigned*)(fold_mem + f_reg)};
     unsigned long long* ctr = (unsigned long long*)(mem + o_ctr);
     const double* Ds_dev = (const double*)(mem + o_Ds);
     int dev = 0, n_sm = 152;
@@ -238,9 +241,9 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
                                      lin_d, lin_v, lin_l, st);
         }
         l += launch_fold_prep(fbat, fsegs, s_off_dev, n_lc, N, fp64, t_dev, lin_d, lin_v,
-                              lin_l, n_D, phase_step, gap_factor, nodes, bucket, rec, st);
+                              lin_l, n_D, phase_step, gap_factor, fsc, st);
         cudaMemsetAsync(ctr, 0, 16, st);
-        l += launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, nodes, bucket, rec, n_D,
+        l += launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, fsc, n_D,
                                phase_step, gap_factor, periods_dev, nP_run, ctr, grid, threads,
                                Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
                                lnP_dev, st);
@@ -268,8 +271,8 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         for (int c = 0; c < 4; ++c) {
             cudaMemsetAsync(ctr, 0, 16, st);
             cudaEventRecord(e0, st);
-            const int lt = launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, nodes, bucket,
-                                             rec, n_D, phase_step, gap_factor, periods_dev,
+            const int lt = launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, fsc,
+                                             n_D, phase_step, gap_factor, periods_dev,
                                              nP_run, ctr, n_sm * cand[c][0], cand[c][1], Q_dev,
                                              T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
                                              lnP_dev, st);

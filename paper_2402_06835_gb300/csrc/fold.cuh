@@ -60,12 +60,23 @@ struct FoldSeg {
     int64_t n_slots, rec_off;
     int use_slots;
     int screen;         // FP64 path: FP32 screening allowed for this curve
+    int64_t srec_off;   // FP64 path: first slot-indexed screening record
+};
+
+// Device scratch of the batch fold.
+struct FoldScratch {
+    void* nodes;            // exact-path records (exact_layout of all samples)
+    int* bucket;            // bucket tables
+    Node4<float>* rec;      // mixed slot records
+    ScreenRec* srec;        // FP64 slot-indexed screening records
+    int* slot_of;           // FP64: slot of every sample
+    unsigned* reg;          // FP64: two words per curve (zeroed by the prep)
 };
 
 // Host side of the batch fold: per-curve layout and launches.
 struct FoldBatch {
     std::vector<FoldSeg> segs;
-    int64_t n_bucket_total = 0, n_rec_total = 0;
+    int64_t n_bucket_total = 0, n_rec_total = 0, n_srec_total = 0;
     bool any_slots = false, any_exact = false;
 };
 
@@ -76,14 +87,14 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
 int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t* s_off_dev,
                      int n_seg, int64_t n_total, bool fp64, const double* t, const void* depth,
                      const void* var, const void* gain, int n_D, double dt, double gap_factor,
-                     void* nodes, int* bucket, Node4<float>* rec, cudaStream_t st);
+                     const FoldScratch& fs, cudaStream_t st);
 
 int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
-                      int64_t n_total, bool fp64, const double* t, const void* nodes, const int* bucket,
-                      const Node4<float>* rec, int n_D, double dt, double gap_factor,
-                      const double* periods, int64_t n_P, unsigned long long* counter,
-                      int grid, int threads, double* Q, double* T0, int* Didx, double* dep,
-                      double* sig, double* lnp, cudaStream_t st);
+                      int64_t n_total, bool fp64, const double* t, const FoldScratch& fs,
+                      int n_D, double dt, double gap_factor, const double* periods,
+                      int64_t n_P, unsigned long long* counter, int grid, int threads,
+                      double* Q, double* T0, int* Didx, double* dep, double* sig, double* lnp,
+                      cudaStream_t st);
 
 int launch_slots_test(const double* t, const int64_t* s_off_dev, int n_seg, int64_t n_total,
                       double dt, int* irregular, cudaStream_t st);

@@ -43,6 +43,11 @@ __device__ __forceinline__ float rcp32(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float rsqrt32(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float lg2_32(float x) {
     float y;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -652,6 +657,11 @@ struct ScreenGeom {
     const ScreenRec* rec;              // duration-major rows of n_t0 records
     const ulonglong2* vpair;           // (position of epoch i, of epoch i+1), 24.40
                                        // slots from t_ref; the last .y is 2^64 - 1
+    const ScreenRec* srec;             // the same records placed at their epochs'
+                                       // slots: duration-major rows of n_slots
+    int64_t n_slots;
+    const unsigned* reg;               // [0]: an epoch is off the slot grid,
+                                       // [1]: max |offset from its slot| (float bits)
     int on;                            // screening allowed for this curve
 };
 
@@ -662,17 +672,43 @@ __device__ __forceinline__ double sigma_at(const T* depth, const T* var, const T
     return (double)node_sigma<T>(depth[o], var[o], gain[o]);
 }
 
-// Screening record (and, for the first duration row, the epoch position) of
-// epoch i of a curve with n epochs; gid indexes the (duration, epoch) arrays.
+// Slot of every epoch on the regular grid u = (t0 - t_ref)/dt and the largest
+// offset from it; reg[0] is set when the slots are not strictly increasing
+// or fall outside [0, n_slots).  reg must be zero on entry.
+__device__ __forceinline__ void slot_offset(const double* __restrict__ t0, int64_t i,
+                                            double inv_dt, int64_t n_slots,
+                                            int* __restrict__ slot_of,
+                                            unsigned* __restrict__ reg) {
+    const double u = (t0[i] - t0[0]) * inv_dt;
+    const double s = rint(u);
+    bool bad = !(s >= 0.0) || !(s < (double)n_slots);
+    if (i > 0) bad = bad || !(s > rint((t0[i - 1] - t0[0]) * inv_dt));
+    slot_of[i] = bad ? -1 : (int)s;
+    if (bad) atomicOr(&reg[0], 1u);
+    atomicMax(&reg[1], __float_as_uint((float)fabs(u - s) * 1.0001f));
+}
+
+__global__ void k_slot_offsets(const double* __restrict__ t0s, int64_t n_t0, double inv_dt,
+                               int64_t n_slots, int* __restrict__ slot_of,
+                               unsigned* __restrict__ reg) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_t0) return;
+    slot_offset(t0s, i, inv_dt, n_slots, slot_of, reg);
+}
+
+// Screening record of epoch i of a curve with n epochs (gid indexes the
+// (duration, epoch) arrays; d is the duration), also placed at the epoch's
+// slot, and for the first duration row the pair of epoch positions.
 template <typename T>
 __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
                                             const T* __restrict__ var,
                                             const T* __restrict__ gain,
                                             const double* __restrict__ t0, int64_t gid,
-                                            int64_t i, int64_t n, double gap_max, double dt,
-                                            ScreenRec* __restrict__ out,
-                                            ulonglong2* __restrict__ vpair,
-                                            bool write_vpos) {
+                                            int64_t i, int64_t n, int64_t d, double gap_max,
+                                            double dt, ScreenRec* __restrict__ out,
+                                            ScreenRec* __restrict__ sout, int64_t n_slots,
+                                            const int* __restrict__ slot_of,
+                                            ulonglong2* __restrict__ vpair) {
     // an interval needs both ends valid and a gap in (0, gap_max]
     bool v0 = i + 1 < n;
     if (v0) {
@@ -711,7 +747,9 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
     }
     r.flags = flags;
     out[gid] = r;
-    if (write_vpos) {
+    const int sl = slot_of[i];
+    if (sl >= 0 && sl < n_slots) sout[d * n_slots + sl] = r;
+    if (d == 0) {
         auto pos = [&](int64_t k) -> unsigned long long {
             const double v = (t0[k] - t0[0]) / dt * 1099511627776.0;
             return v < 9.0e18 ? (unsigned long long)llrint(v) : 9000000000000000000ull;
@@ -720,24 +758,36 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
     }
 }
 
+// Slot records start as invalid intervals (slots without an epoch).
+__global__ void k_fill_screen(ScreenRec* __restrict__ rec, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rec[i] = ScreenRec{0.f, NAN, 0.f, 0.f, 0.f, 0.f, 0.f, 0u};
+}
+
 template <typename T>
 __global__ void k_screen(const T* __restrict__ depth, const T* __restrict__ var,
                          const T* __restrict__ gain, const double* __restrict__ t0s,
                          int64_t n_t0, int n_D, double gap_max, double dt,
-                         ScreenRec* __restrict__ rec, ulonglong2* __restrict__ vpair) {
+                         ScreenRec* __restrict__ rec, ScreenRec* __restrict__ srec,
+                         int64_t n_slots, const int* __restrict__ slot_of,
+                         ulonglong2* __restrict__ vpair) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= n_t0 * (int64_t)n_D) return;
-    const int64_t i = gid % n_t0;
-    make_screen<T>(depth, var, gain, t0s, gid, i, n_t0, gap_max, dt, rec, vpair, gid < n_t0);
+    const int64_t d = gid / n_t0, i = gid - d * n_t0;
+    make_screen<T>(depth, var, gain, t0s, gid, i, n_t0, d, gap_max, dt, rec, srec, n_slots,
+                   slot_of, vpair);
 }
 
 // Per-period constants of the screen.
 struct ScreenPeriod {
     unsigned long long uph, ustep, ulast, delta;
+    unsigned long long uend;   // epochs walk while u < uend = ulast + delta
     float inv_ustep32;
     float cv;       // error coefficient of an FP32 event value
-    float dw;       // delta as an interval weight (dt/gap <= 4)
+    float dw;       // half-width of the band around an epoch, as an interval weight
     bool on;
+    bool slots;     // regular grid: events from the slot records
 };
 
 __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const ScreenGeom& sg,
@@ -747,7 +797,8 @@ __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const S
     const double R = P * g.inv_dt;
     const double span = (g.t_last - g.t_ref) * g.inv_dt;
     sp.on = sg.on != 0 && R * SCALE < 4.0e18 && span < 8388608.0;
-    sp.uph = sp.ustep = sp.ulast = sp.delta = 0;
+    sp.slots = false;
+    sp.uph = sp.ustep = sp.ulast = sp.delta = sp.uend = 0;
     sp.inv_ustep32 = 0.f;
     sp.cv = 0.f;
     sp.dw = 0.f;
@@ -765,43 +816,140 @@ __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const S
     const double delta = 16.0 * e_pos + 1048576.0;          // + 2^-20 slot
     sp.on = delta < 1.6e10;                                  // below 2^-6 slot
     sp.delta = (unsigned long long)delta;
-    sp.dw = (float)(4.04 * delta / SCALE);
-    // weight error: 4 e_pos (dt/gap <= 4) plus 4 x the 2^-30-slot truncation
-    const double e_w = 4.0 * e_pos / SCALE + 3.725290298461914e-09;
+    sp.uend = sp.ulast + sp.delta;
+    // regular grid: every epoch within 2^-26 slot of its own slot
+    const float off = sg.srec ? __uint_as_float(sg.reg[1]) : 1.f;
+    sp.slots = sg.srec && sg.reg[0] == 0u && off <= 1.4901161193847656e-08f;
+    double e_w;
+    if (sp.slots) {
+        // the weight is the fraction of the slot: position error, the
+        // epochs' offsets (3 x, both ends), 24-bit truncation
+        sp.dw = (float)(1.01 * (delta / SCALE + (double)off) + 1.2e-7);
+        e_w = e_pos / SCALE + 3.0 * (double)off + 5.9604644775390625e-08;
+    } else {
+        // dt/gap <= 4 on a screened interval; 2^-30-slot truncation
+        sp.dw = (float)(4.04 * delta / SCALE);
+        e_w = 4.0 * e_pos / SCALE + 3.725290298461914e-09;
+    }
     sp.cv = (float)(8.0 * 5.9604644775390625e-08 + 2.0 * e_w);
     return sp;
 }
 
-// Upper bound on ln P of cell (j, row rd) whose first epoch is at u0 (see
-// above): -inf when the cell has no event, +inf when an event falls on an
-// interval outside the screen's error model.
+// Sums of the screen (see above) and the bound they give.
+struct ScreenAcc {
+    float sinv, sd, sdd, saa, sl, sabs, ivmax;
+    int K;
+    __device__ __forceinline__ void init() {
+        sinv = sd = sdd = saa = sl = sabs = ivmax = 0.f;
+        K = 0;
+    }
+    // event (depth dk, sigma s, gain lk) on an interval with depth and gain
+    // differences dd, dl
+    __device__ __forceinline__ void add(float dk, float s, float lk, float dd, float dl) {
+        const float iv = rcp32(s * s);
+        const float div = dk * iv;
+        sinv += iv;
+        sd += div;
+        sdd = fmaf(div, dk, sdd);
+        sl += lk;
+        const float ad = fmaf(2.f, fabsf(dk), fabsf(dd));
+        saa = fmaf(ad * ad, iv, saa);
+        sabs += fmaf(2.f, fabsf(lk), fabsf(dl));
+        ivmax = fmaxf(ivmax, iv);
+        ++K;
+    }
+    // Hardware reciprocal / reciprocal square root (relative error below
+    // 2^-21, counted as 8u per use) with every term rounded the safe way.
+    __device__ __forceinline__ float bound(float cv) const {
+        if (K == 0) return -INFINITY;
+        const float U = 5.9604645e-8f;                        // 2^-24
+        const float sk = (float)(K + 2) * U;
+        // |ds|/s <= 2 on a screened interval (adjacent sigmas within a factor 3)
+        const float gam = 2.2f * cv * 4.f + 6.f * U;
+        const float r = rcp32(sinv);
+        const float qc = fmaf(-sd * sd, r, sdd);
+        const float qcl = qc - (float)(4 * K + 32) * U * sdd;
+        float q_lo = 0.f;
+        if (qcl > 0.f) {
+            const float x1 = qcl * rcp32(1.f + gam + sk) * (1.f - 16.f * U);
+            const float a = x1 * rsqrt32(x1) * (1.f - 16.f * U);
+            const float y = saa * (1.f + 2.f * gam + sk) * (1.f + 4.f * U);
+            const float e = y > 0.f ? 1.05f * cv * (y * rsqrt32(y)) * (1.f + 16.f * U) : 0.f;
+            if (a > e) q_lo = (a - e) * (a - e) * (1.f - 8.f * U);
+        }
+        const float x_hi = fminf(1.f, ivmax * r * (1.f + 4.f * gam + 2.f * sk + 24.f * U));
+        const float e_l = 1.05f * (cv + sk) * sabs;
+        return sl + e_l + 0.5f - 0.5f * q_lo * rcp32(1.f + x_hi) * (1.f - 16.f * U) +
+               8.f * U * (sabs + q_lo + 1.f);
+    }
+};
+
+// The event at epoch k computed as the exact path does (FP64 epoch, interval
+// and values), rounded to FP32 for the screen.  Returns 0 when the epoch is
+// dropped, 1 for an event, 2 when its interval is outside the error model.
+__device__ __forceinline__ int screen_exact_event(const FoldGeom& g,
+                                                  const Node8<double>* __restrict__ nd,
+                                                  const ScreenRec* __restrict__ rd,
+                                                  const CellCtx& c, double phi, int64_t k,
+                                                  unsigned long long u, ScreenAcc& acc) {
+    const double Tk = epoch_time(g, c, phi, (double)k);
+    const long long kT = okey(Tk);
+    if (kT > c.klast) return 0;                 // after the last epoch
+    const int64_t i = bracket_from(g, kT, guess_at(g, u));
+    const Node8<double> a = nd[i];
+    const double w = (Tk - g.t0s[i]) * a.ig;
+    const double s = fma(w, a.ds, a.s);
+    if (nan64(s)) return 0;
+    if (rd[i].flags) return 2;
+    acc.add((float)fma(w, a.dd, a.d), (float)s, (float)fma(w, a.dl, a.l), (float)a.dd,
+            (float)a.dl);
+    return 1;
+}
+
+// Upper bound on ln P of cell (j, duration rows nd / rd / rs) whose first
+// epoch is at u0 (see above): -inf when the cell has no event, +inf when an
+// event falls on an interval outside the screen's error model.
 __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom& sg,
+                                             const Node8<double>* __restrict__ nd,
                                              const ScreenRec* __restrict__ rd,
+                                             const ScreenRec* __restrict__ rs,
                                              const ScreenPeriod& sp, const CellCtx& c,
                                              int64_t j, unsigned long long u0) {
+    // epochs up to u < ulast + delta: those within delta of t_last (the last
+    // epoch's position) fall in the band around it and take the exact event,
+    // which drops T > t_last
     double phi = 0.0;
     bool have_phi = false;
-    int64_t kmax = 0;
-    if (u0 <= sp.ulast) {
-        int64_t kk = (int64_t)((float)(unsigned)((sp.ulast - u0) >> 32) * sp.inv_ustep32);
-        while (kk > 0 && u0 + (unsigned long long)kk * sp.ustep > sp.ulast) --kk;
-        while (u0 + (unsigned long long)(kk + 1) * sp.ustep <= sp.ulast) ++kk;
-        kmax = kk + 1;
-    }
-    // the count of epochs with T <= t_last, exactly, when an epoch is near t_last
-    const unsigned long long unext = u0 + (unsigned long long)kmax * sp.ustep;
-    if (unext - sp.ulast < sp.delta ||
-        (kmax > 0 && sp.ulast - (unext - sp.ustep) < sp.delta)) {
-        phi = cell_phi(c, j);
-        have_phi = true;
-        kmax = cell_kmax(g, c, phi, u0);
-    }
-    float sinv = 0.f, sd = 0.f, sdd = 0.f, saa = 0.f, sl = 0.f, sabs = 0.f, ivmax = 0.f;
-    int K = 0;
+    ScreenAcc acc;
+    acc.init();
     unsigned long long u = u0;
+    if (sp.slots) {
+        // regular grid: the interval is the slot's, the weight its fraction
+        const int64_t ns1 = sg.n_slots - 1;
+        ScreenRec rn = rs[min((int64_t)(u >> 40), ns1)];
+        for (int64_t k = 0; u < sp.uend; ++k, u += sp.ustep) {
+            const ScreenRec r = rn;
+            rn = rs[min((int64_t)((u + sp.ustep) >> 40), ns1)];
+            const float w =
+                __uint2float_rn((unsigned)((u >> 16) & 0xffffffu)) * 5.9604644775390625e-08f;
+            if (w < sp.dw || w > 1.f - sp.dw) {
+                if (!have_phi) {
+                    phi = cell_phi(c, j);
+                    have_phi = true;
+                }
+                if (screen_exact_event(g, nd, rd, c, phi, k, u, acc) == 2) return INFINITY;
+                continue;
+            }
+            if (r.flags) return INFINITY;
+            const float s = fmaf(w, r.ds, r.s);
+            if (isnan(s)) continue;
+            acc.add(fmaf(w, r.dd, r.d), s, fmaf(w, r.dl, r.l), r.dd, r.dl);
+        }
+        return acc.bound(sp.cv);
+    }
     const int64_t nb1 = g.n_bucket - 1;
     int bnext = g.bucket[min((int64_t)(u >> 40), nb1)];
-    for (int64_t k = 0; k < kmax; ++k, u += sp.ustep) {
+    for (int64_t k = 0; u < sp.uend; ++k, u += sp.ustep) {
         // interval guess from the bucket table (the next epoch's entry is
         // fetched one iteration ahead), verified against the stored positions
         int64_t i = bnext > 0 ? (int64_t)bnext - 1 : 0;
@@ -813,12 +961,11 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
             while (u < v.x) v = sg.vpair[--i];
             r = rd[i];
         }
-        long long sdu = (long long)(u - v.x);
-        float w = __int2float_rn((int)(sdu >> 10)) * r.wsc;
-        float s = fmaf(w, r.ds, r.s);
+        const long long sdu = (long long)(u - v.x);
+        const float w = __int2float_rn((int)(sdu >> 10)) * r.wsc;
+        const float s = fmaf(w, r.ds, r.s);
         // within delta of either end (on a valid interval: w within dw of 0
-        // or 1, dw >= 4 delta in slots as dt/gap <= 4): the exact path's
-        // interval from FP64 T
+        // or 1, dw >= 4 delta in slots as dt/gap <= 4): the exact event
         const bool near = isnan(s) ? ((unsigned long long)sdu < sp.delta || v.y - u < sp.delta)
                                    : (w < sp.dw || w > 1.f - sp.dw);
         if (near) {
@@ -826,48 +973,14 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
                 phi = cell_phi(c, j);
                 have_phi = true;
             }
-            const int64_t ie = bracket_from(g, okey(epoch_time(g, c, phi, (double)k)), i);
-            if (ie != i) {
-                i = ie;
-                v = sg.vpair[i];
-                r = rd[i];
-                sdu = (long long)(u - v.x);
-                w = __int2float_rn((int)(sdu >> 10)) * r.wsc;
-                s = fmaf(w, r.ds, r.s);
-            }
+            if (screen_exact_event(g, nd, rd, c, phi, k, u, acc) == 2) return INFINITY;
+            continue;
         }
         if (r.flags) return INFINITY;
         if (isnan(s)) continue;
-        const float dk = fmaf(w, r.dd, r.d);
-        const float lk = fmaf(w, r.dl, r.l);
-        const float iv = rcp32(s * s);
-        const float div = dk * iv;
-        sinv += iv;
-        sd += div;
-        sdd = fmaf(div, dk, sdd);
-        sl += lk;
-        const float ad = fmaf(2.f, fabsf(dk), fabsf(r.dd));
-        saa = fmaf(ad * ad, iv, saa);
-        sabs += fmaf(2.f, fabsf(lk), fabsf(r.dl));
-        ivmax = fmaxf(ivmax, iv);
-        ++K;
+        acc.add(fmaf(w, r.dd, r.d), s, fmaf(w, r.dl, r.l), r.dd, r.dl);
     }
-    if (K == 0) return -INFINITY;
-    const float U = 5.9604645e-8f;                        // 2^-24
-    const float sk = (float)(K + 2) * U;
-    // |ds|/s <= 2 on a screened interval (adjacent sigmas within a factor 3)
-    const float gam = 2.2f * sp.cv * 4.f + 6.f * U;
-    const float qc = sdd - sd * sd / sinv;
-    const float qcl = qc - (float)(4 * K + 16) * U * sdd;
-    float q_lo = 0.f;
-    if (qcl > 0.f) {
-        const float a = sqrtf(qcl / (1.f + gam + sk));
-        const float e = 1.05f * sp.cv * sqrtf(saa * (1.f + 2.f * gam + sk));
-        if (a > e) q_lo = (a - e) * (a - e) * (1.f - 8.f * U);
-    }
-    const float x_hi = fminf(1.f, ivmax / sinv * (1.f + 4.f * gam + 2.f * sk + 8.f * U));
-    const float e_l = 1.05f * (sp.cv + sk) * sabs;
-    return sl + e_l + 0.5f - 0.5f * q_lo / (1.f + x_hi) + 8.f * U * (sabs + q_lo + 1.f);
+    return acc.bound(sp.cv);
 }
 
 // Exact ln P of one cell computed by a whole warp (lanes over epochs); used
@@ -917,6 +1030,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     __shared__ int sh_qd[512];
     __shared__ int sh_nq;
     __shared__ unsigned long long sh_sbest;
+    __shared__ float sh_bf;          // sh_sbest rounded down to FP32
     if (bad_period(P, g)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
@@ -935,6 +1049,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     if (threadIdx.x == 0) {
         sh_nq = 0;
         sh_sbest = max_key(-INFINITY);
+        sh_bf = -INFINITY;
     }
     __syncthreads();
     int d = (int)(threadIdx.x / n_phi);
@@ -947,7 +1062,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         const int64_t cell = base + threadIdx.x;
         float ub = -INFINITY;
         if (cell < n_cells)
-            ub = screen_cell(g, sg, sg.rec + (int64_t)d * g.n_t0, sp, c, j,
+            ub = screen_cell(g, sg, nodes + (int64_t)d * g.n_t0, sg.rec + (int64_t)d * g.n_t0,
+                             sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c, j,
                              (unsigned long long)j * sp.uph);
         if (base == 0) {
             // seed: each warp evaluates its lane with the largest finite bound
@@ -969,11 +1085,13 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                     atomicMax(&sh_sbest, max_key(lnp - 1e-9 * (1.0 + fabs(lnp))));
             }
             __syncthreads();
+            if (threadIdx.x == 0) sh_bf = __double2float_rd(from_max_key(sh_sbest));
+            __syncthreads();
         }
         if (cell < n_cells) {
-            const double best_now = fmax(bl, from_max_key(sh_sbest));
-            // a cell without events (bound -inf) is never the argmax; NaN survives
-            if (!(ub == -INFINITY) && !(ub < __double2float_rd(best_now))) {
+            // a cell without events (bound -inf) is never the argmax; NaN
+            // survives.  sh_bf <= every evaluated best (each is in sh_sbest).
+            if (!(ub == -INFINITY) && !(ub < sh_bf)) {
                 const int q = atomicAdd(&sh_nq, 1);
                 sh_qc[q] = cell;
                 sh_qd[q] = d;
@@ -1025,7 +1143,10 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                 sh_qc[threadIdx.x] = c2;
                 sh_qd[threadIdx.x] = d2;
             }
-            if (threadIdx.x == 0) sh_nq = rest;
+            if (threadIdx.x == 0) {
+                sh_nq = rest;
+                sh_bf = __double2float_rd(from_max_key(sh_sbest));
+            }
             __syncthreads();
         }
     }
@@ -1255,7 +1376,8 @@ template <int KIND>
 __global__ void __launch_bounds__(256)
 k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restrict__ t,
              const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
-             const ulonglong2* __restrict__ vpair, const int* __restrict__ bucket,
+             const ulonglong2* __restrict__ vpair, const ScreenRec* __restrict__ srec,
+             const unsigned* __restrict__ reg, const int* __restrict__ bucket,
              const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
              const double* __restrict__ periods, int64_t n_P, unsigned long long* counter,
              double* __restrict__ Q_out, double* __restrict__ T0_out,
@@ -1282,7 +1404,8 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
             FoldGeom gg{t + fs.s_off, fs.n_t0, fs.t_ref, fs.t_last, dt, 1.0 / dt,
                         gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
             if (KIND == 0) {
-                const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off, fs.screen};
+                const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off,
+                                    srec + fs.srec_off, fs.n_slots, reg + 2 * g, fs.screen};
                 fold_screened_one(gg, sg, (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
                                   periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                                   lnp_out);
@@ -1320,7 +1443,8 @@ __global__ void k_screen_batch(const T* __restrict__ depth, const T* __restrict_
                                const FoldSeg* __restrict__ segs, int n_seg,
                                const int64_t* __restrict__ s_off, int n_D, double gap_max,
                                double dt, ScreenRec* __restrict__ rec,
-                               ulonglong2* __restrict__ vpair) {
+                               ulonglong2* __restrict__ vpair, ScreenRec* __restrict__ srec,
+                               const int* __restrict__ slot_of) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= s_off[n_seg] * (int64_t)n_D) return;
     int lo = 0, hi = n_seg;
@@ -1328,11 +1452,31 @@ __global__ void k_screen_batch(const T* __restrict__ depth, const T* __restrict_
         const int mid = (lo + hi) >> 1;
         if (s_off[mid] * (int64_t)n_D <= gid) lo = mid; else hi = mid;
     }
-    if (!segs[lo].screen) return;
+    const FoldSeg fs = segs[lo];
+    if (!fs.screen) return;
     const int64_t s0 = s_off[lo], ng = s_off[lo + 1] - s0;
-    const int64_t i = (gid - s0 * n_D) % ng;
-    make_screen<T>(depth, var, gain, t + s0, gid, i, ng, gap_max, dt, rec, vpair + s0,
-                   gid - s0 * n_D < ng);
+    const int64_t w = gid - s0 * n_D;
+    const int64_t d = w / ng, i = w - d * ng;
+    make_screen<T>(depth, var, gain, t + s0, gid, i, ng, d, gap_max, dt, rec,
+                   srec + fs.srec_off, fs.n_slots, slot_of + s0, vpair + s0);
+}
+
+// Slots of every sample of the screened curves (reg: two words per curve).
+__global__ void k_slot_offsets_batch(const double* __restrict__ t,
+                                     const FoldSeg* __restrict__ segs, int n_seg,
+                                     const int64_t* __restrict__ s_off, double inv_dt,
+                                     int* __restrict__ slot_of, unsigned* __restrict__ reg) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= s_off[n_seg]) return;
+    int lo = 0, hi = n_seg;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    const FoldSeg fs = segs[lo];
+    if (!fs.screen) return;
+    const int64_t s0 = s_off[lo];
+    slot_offset(t + s0, i - s0, inv_dt, fs.n_slots, slot_of + s0, reg + 2 * lo);
 }
 
 __global__ void k_buckets_batch(const double* __restrict__ t, const FoldSeg* __restrict__ segs,
@@ -1422,6 +1566,8 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
         f.use_slots = (!fp64 && gap_factor > 1.0 && gap_factor < 2.0 && span < 4.0e6 &&
                        !irregular[g]) ? 1 : 0;
         f.screen = (fp64 && gap_factor < 2.0 && span < 8.0e6) ? 1 : 0;
+        f.srec_off = fb.n_srec_total;
+        fb.n_srec_total += f.screen ? f.n_slots * n_D : 0;
         f.bucket_off = fb.n_bucket_total;
         fb.n_bucket_total += f.use_slots ? 0 : f.n_bucket;
         f.rec_off = fb.n_rec_total;
@@ -1434,7 +1580,7 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
 int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t* s_off_dev,
                      int n_seg, int64_t n_total, bool fp64, const double* t, const void* depth,
                      const void* var, const void* gain, int n_D, double dt, double gap_factor,
-                     void* nodes, int* bucket, Node4<float>* rec, cudaStream_t st) {
+                     const FoldScratch& fs, cudaStream_t st) {
     int launched = 0;
     const int64_t ngrid = n_total * (int64_t)n_D;
     if (fb.any_exact) {
@@ -1442,26 +1588,31 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
             const ExactLayout L = exact_layout(n_total, n_D, true);
             k_nodes_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
-                n_seg, s_off_dev, n_D, gap_factor * dt, (Node8<double>*)nodes);
+                n_seg, s_off_dev, n_D, gap_factor * dt, (Node8<double>*)fs.nodes);
+            cudaMemsetAsync(fs.reg, 0, (size_t)n_seg * 2 * sizeof(unsigned), st);
+            k_slot_offsets_batch<<<div_up(n_total, 256), 256, 0, st>>>(
+                t, segs_dev, n_seg, s_off_dev, 1.0 / dt, fs.slot_of, fs.reg);
+            k_fill_screen<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(
+                fs.srec, fb.n_srec_total);
             k_screen_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
                 n_seg, s_off_dev, n_D, gap_factor * dt, dt,
-                (ScreenRec*)((char*)nodes + L.off_screen),
-                (ulonglong2*)((char*)nodes + L.off_vpos));
-            ++launched;
+                (ScreenRec*)((char*)fs.nodes + L.off_screen),
+                (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.slot_of);
+            launched += 3;
         } else
             k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
-                s_off_dev, n_D, gap_factor * dt, (Node8<float>*)nodes);
+                s_off_dev, n_D, gap_factor * dt, (Node8<float>*)fs.nodes);
         k_buckets_batch<<<div_up(fb.n_bucket_total, 256), 256, 0, st>>>(
-            t, segs_dev, n_seg, fb.n_bucket_total, dt, bucket);
+            t, segs_dev, n_seg, fb.n_bucket_total, dt, fs.bucket);
         launched += 2;
     }
     if (fb.any_slots) {
-        k_fill_nan<<<div_up(fb.n_rec_total, 256), 256, 0, st>>>(rec, fb.n_rec_total);
+        k_fill_nan<<<div_up(fb.n_rec_total, 256), 256, 0, st>>>(fs.rec, fb.n_rec_total);
         k_slot_fill_batch<<<div_up(ngrid, 256), 256, 0, st>>>(
             (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
-            s_off_dev, n_D, 1.0 / dt, rec);
+            s_off_dev, n_D, 1.0 / dt, fs.rec);
         launched += 2;
     }
     return launched;
@@ -1470,36 +1621,32 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
 // The persistent fold kernels; counter[0..1] must be zero.  blocks_per_sm
 // and threads come from the autotuner.
 int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
-                      int64_t n_total, bool fp64, const double* t, const void* nodes,
-                      const int* bucket, const Node4<float>* rec, int n_D, double dt,
-                      double gap_factor, const double* periods, int64_t n_P,
-                      unsigned long long* counter, int grid, int threads, double* Q,
-                      double* T0, int* Didx, double* dep, double* sig, double* lnp,
+                      int64_t n_total, bool fp64, const double* t, const FoldScratch& fs,
+                      int n_D, double dt, double gap_factor, const double* periods,
+                      int64_t n_P, unsigned long long* counter, int grid, int threads,
+                      double* Q, double* T0, int* Didx, double* dep, double* sig, double* lnp,
                       cudaStream_t st) {
     int launched = 0;
     const ExactLayout L = exact_layout(n_total, n_D, fp64);
-    const ScreenRec* screen = fp64 ? (const ScreenRec*)((const char*)nodes + L.off_screen)
-                                   : nullptr;
+    const ScreenRec* screen =
+        fp64 ? (const ScreenRec*)((const char*)fs.nodes + L.off_screen) : nullptr;
     const ulonglong2* vpair =
-        fp64 ? (const ulonglong2*)((const char*)nodes + L.off_vpos) : nullptr;
+        fp64 ? (const ulonglong2*)((const char*)fs.nodes + L.off_vpos) : nullptr;
     if (fb.any_exact) {
         if (fp64)
-            k_fold_batch<0><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, screen, vpair,
-                                                      bucket, rec,
-                                                      n_D, dt, gap_factor, periods, n_P,
-                                                      counter, Q, T0, Didx, dep, sig, lnp);
+            k_fold_batch<0><<<grid, threads, 0, st>>>(
+                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.reg, fs.bucket, fs.rec,
+                n_D, dt, gap_factor, periods, n_P, counter, Q, T0, Didx, dep, sig, lnp);
         else
-            k_fold_batch<1><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, screen, vpair,
-                                                      bucket, rec,
-                                                      n_D, dt, gap_factor, periods, n_P,
-                                                      counter, Q, T0, Didx, dep, sig, lnp);
+            k_fold_batch<1><<<grid, threads, 0, st>>>(
+                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.reg, fs.bucket, fs.rec,
+                n_D, dt, gap_factor, periods, n_P, counter, Q, T0, Didx, dep, sig, lnp);
         ++launched;
     }
     if (fb.any_slots) {
-        k_fold_batch<2><<<grid, threads, 0, st>>>(segs_dev, n_seg, t, nodes, screen, vpair,
-                                                  bucket, rec, n_D,
-                                                  dt, gap_factor, periods, n_P, counter + 1, Q,
-                                                  T0, Didx, dep, sig, lnp);
+        k_fold_batch<2><<<grid, threads, 0, st>>>(
+            segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.reg, fs.bucket, fs.rec, n_D,
+            dt, gap_factor, periods, n_P, counter + 1, Q, T0, Didx, dep, sig, lnp);
         ++launched;
     }
     return launched;
@@ -1520,7 +1667,7 @@ namespace nu {
 // Scratch layout of the single-curve fold.
 struct SingleLayout {
     ExactLayout el;
-    size_t exact, bucket, slot_of, flag, rec, total;
+    size_t exact, bucket, slot_of, flag, rec, srec, total;
 };
 
 static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool fp64) {
@@ -1533,7 +1680,8 @@ static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool 
     L.slot_of = L.bucket + al((size_t)n_bucket * sizeof(int));
     L.flag = L.slot_of + al((size_t)n_t0 * sizeof(int));
     L.rec = L.flag + 256;
-    L.total = L.rec + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>)));
+    L.srec = L.rec + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>)));
+    L.total = L.srec + (fp64 ? al((size_t)n_slots * n_D * sizeof(ScreenRec)) : 0);
     return L;
 }
 
@@ -1592,19 +1740,30 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
         FoldGeom g{t0s_dev, n_t0, t_ref, t_last, phase_step, 1.0 / phase_step,
                    gap_factor * phase_step, bucket, n_bucket};
         if (fp64) {
-            ScreenRec* srec = (ScreenRec*)(scratch + L.exact + L.el.off_screen);
+            ScreenRec* nrec = (ScreenRec*)(scratch + L.exact + L.el.off_screen);
             ulonglong2* vpair = (ulonglong2*)(scratch + L.exact + L.el.off_vpos);
-            const ScreenGeom sg{srec, vpair, (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0};
+            ScreenRec* srec = (ScreenRec*)(scratch + L.srec);
+            unsigned* reg = (unsigned*)(flag + 1);
+            const ScreenGeom sg{nrec, vpair, srec, n_slots, reg,
+                                (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0};
+            e = cudaMemsetAsync(flag, 0, 256, st);
+            if (e != cudaSuccess) {
+                count_launches(launched);
+                return cuda_fail(e, (std::string(who) + ": memset").c_str());
+            }
+            k_slot_offsets<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, 1.0 / phase_step,
+                                                              n_slots, slot_of, reg);
+            k_fill_screen<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(srec, n_slots * n_D);
             k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
                 t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
             k_screen<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, phase_step, srec, vpair);
+                t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, n_slots, slot_of, vpair);
             k_fold_screened<<<(unsigned)n_P, 256, 0, st>>>(
                 g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-            launched += 4;
+            launched += 6;
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,

@@ -162,19 +162,22 @@ def test_fold_invalid_periods_are_nan():
 
 
 @pytest.mark.parametrize("offset", [0.0, 2000.0])
-def test_fold_fp64_screen_hard_cases(offset):
+@pytest.mark.parametrize("regular", [True, False])
+def test_fold_fp64_screen_hard_cases(offset, regular):
     """FP64 fold on grids built to stress the FP32 screen of the exact path:
     periods that are whole multiples of the step (epochs land on samples and
-    on the edges of gaps and NaN holes), epochs far from zero, irregular
-    epochs with near-coincident pairs, neighbours whose variances differ by
-    orders of magnitude, and gains consistent with the depths (strong
-    pruning) next to unrelated ones.  Every period is compared."""
+    on the edges of gaps and NaN holes), epochs far from zero, regular
+    epochs (slot-indexed screen) or irregular ones with near-coincident pairs
+    (position search), neighbours whose variances differ by orders of
+    magnitude, and gains consistent with the depths (strong pruning) next to
+    unrelated ones.  Every period is compared."""
     rng = np.random.default_rng(41)
     dt = synth.CADENCE_DAYS
     base = np.concatenate([np.arange(600), np.arange(640, 1300), np.arange(1302, 1500)])
     t0s = offset + base * dt
-    t0s[5::97] += 0.9 * dt          # near-coincident pairs (gap 0.1 dt)
-    t0s = np.sort(t0s)
+    if not regular:
+        t0s[5::97] += 0.9 * dt      # near-coincident pairs (gap 0.1 dt)
+        t0s = np.sort(t0s)
     n = len(t0s)
     var = rng.uniform(1e-8, 5e-8, (4, n))
     var[1, ::53] *= 1e4             # isolated very noisy samples
@@ -191,5 +194,5 @@ def test_fold_fp64_screen_hard_cases(offset):
     gpu = _gpu_fold(t0s, np.ones(4), g, periods, "fp64", phase_step=dt)
     wl, wq, differ = periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, dt,
                                       FP64_TOL, FP64_TOL, periodic.fold_period)
-    print(f"fp64 screen hard cases offset={offset}: lnP err {wl:.2e}, Q err {wq:.2e}, "
-          f"ties {differ}")
+    print(f"fp64 screen hard cases offset={offset} regular={regular}: lnP err {wl:.2e}, "
+          f"Q err {wq:.2e}, ties {differ}")
