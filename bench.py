@@ -298,23 +298,21 @@ def blas_threads():
 
 # ---------------------------------------------------------------- main
 def profile_case(args):
-    """Small cases for ncu: one nu_periodic_search per precision on the
-    sector grid (19 440 epochs with the mid-sector gap, 10 durations), seeded
-    random single-event values, 300 periods over 0.2-13.5 d."""
+    """Small cases for ncu: the sector light curve (19 440 epochs with the
+    mid-sector gap, 10 durations) through nu_gp_factor and nu_linear_search,
+    then one nu_periodic_search per precision over 600 of its 20 000 periods
+    (every 33rd, 0.2-13.5 d)."""
     import torch
     from paper_2402_06835_gb300 import api
     w = synth.sector_19440()
-    t = w.curves[0].t
-    n = len(t)
-    rng = np.random.default_rng(5)
-    g = dict(depth=rng.normal(0, 5e-4, (10, n)), var=rng.uniform(2e-8, 9e-8, (10, n)),
-             dlnl=rng.uniform(0, 6, (10, n)))
-    per = torch.tensor(np.linspace(0.2, 13.5, 300), dtype=torch.float64, device="cuda")
-    tt = torch.tensor(t, device="cuda")
-    dt = float(np.median(np.diff(t)))
-    for prec, dty in (("mixed", torch.float32), ("fp64", torch.float64)):
-        arr = [torch.tensor(g[k], dtype=dty, device="cuda") for k in ("depth", "var", "dlnl")]
-        r = api.nu_periodic_search(tt, w.durations, *arr, per, precision=prec, phase_step=dt)
+    lc = w.curves[0]
+    cu = lambda a: torch.as_tensor(a, device="cuda")
+    t = cu(lc.t)
+    f = api.nu_gp_factor(t, cu(lc.diag_var), lc.terms, cu(lc.X), cu(lc.y))
+    per = cu(np.ascontiguousarray(w.periods[::33]))
+    for prec in ("mixed", "fp64"):
+        d, v, l = api.nu_linear_search(f, t, w.durations, precision=prec)
+        r = api.nu_periodic_search(t, w.durations, d, v, l, per, precision=prec)
         torch.cuda.synchronize()
         print(prec, float(r["Q"].max()))
 
@@ -466,11 +464,14 @@ def main():
             out["mixed"] = {"error": repr(exc)}
 
     if not args.no_batch and args.precision == "fp64":
-        try:
-            out["batch_mixed"] = run_batch(api, torch, synth.survey_438(), "mixed",
-                                           max(1, min(args.steps, 2)), 1, flush)
-        except Exception as exc:
-            out["batch_mixed"] = {"error": repr(exc)}
+        # the survey in one batched call, mixed precision and FP64 side by side
+        survey = synth.survey_438()
+        for key, prec, n in (("batch_mixed", "mixed", max(1, min(args.steps, 2))),
+                             ("batch_fp64", "fp64", 1)):
+            try:
+                out[key] = run_batch(api, torch, survey, prec, n, 1, flush)
+            except Exception as exc:
+                out[key] = {"error": repr(exc)}
 
     if world > 1:
         torch.distributed.barrier()

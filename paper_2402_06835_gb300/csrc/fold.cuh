@@ -24,8 +24,8 @@ template <typename T> struct __align__(8 * sizeof(T)) Node8 {
 };
 
 // Screening record of the FP64 path, one per (duration, epoch i): the FP32
-// values and slopes of the interval [t0_i, t0_{i+1}], wsc = 2^-30 dt/gap (the
-// weight per unit of the 2^-30-slot position difference), and flags = 1 when
+// values and slopes of the interval [t0_i, t0_{i+1}], wsc = 2^-22 dt/gap (the
+// weight per unit of the 2^-22-slot position difference), and flags = 1 when
 // the interval is outside the screen's error model (epochs closer than dt/4,
 // end sigmas more than a factor 3 apart, or values whose FP32 sums could
 // overflow): a cell with an event there is evaluated exactly.  s is NaN on an

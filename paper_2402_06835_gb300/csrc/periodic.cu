@@ -730,14 +730,20 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
         r.dd = (float)(d1 - d0);
         r.ds = (float)(s1 - s0);
         r.dl = (float)(l1 - l0);
-        r.wsc = (float)(9.313225746154785e-10 * dt / gap);   // 2^-30 dt / gap
+        r.wsc = (float)(2.384185791015625e-07 * dt / gap);   // 2^-22 dt / gap
         // outside the error model: very close epochs, or values whose FP32
         // sums could overflow
         const bool odd = gap < 0.25 * dt || !(s0 >= 1e-12 && s0 <= 1e12) ||
                          !(s1 >= 1e-12 && s1 <= 1e12) || !(s1 <= 3.0 * s0) ||
                          !(s0 <= 3.0 * s1) || !(fabs(d0) <= 1e8 * s0) ||
                          !(fabs(d1) <= 1e8 * s1) || !(fabs(l0) <= 1e20) || !(fabs(l1) <= 1e20);
-        if (odd) flags = 1u;
+        if (odd) {
+            // sigma +inf marks the interval for the screen (flags for the
+            // exact events)
+            flags = 1u;
+            r.s = INFINITY;
+            r.ds = 0.f;
+        }
     } else {
         r.s = NAN;
         r.dd = 0.f;
@@ -786,6 +792,7 @@ struct ScreenPeriod {
     float inv_ustep32;
     float cv;       // error coefficient of an FP32 event value
     float dw;       // half-width of the band around an epoch, as an interval weight
+    float hw;       // 1/2 - dw: an event is in a band when |w - 1/2| > hw
     bool on;
     bool slots;     // regular grid: events from the slot records
 };
@@ -802,6 +809,7 @@ __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const S
     sp.inv_ustep32 = 0.f;
     sp.cv = 0.f;
     sp.dw = 0.f;
+    sp.hw = 0.5f;
     if (!sp.on) return sp;
     sp.ustep = (unsigned long long)llrint(R * SCALE);
     sp.uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
@@ -824,27 +832,31 @@ __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const S
     if (sp.slots) {
         // the weight is the fraction of the slot: position error, the
         // epochs' offsets (3 x, both ends), 24-bit truncation
-        sp.dw = (float)(1.01 * (delta / SCALE + (double)off) + 1.2e-7);
-        e_w = e_pos / SCALE + 3.0 * (double)off + 5.9604644775390625e-08;
+        sp.dw = (float)(1.01 * (delta / SCALE + (double)off) + 2.4e-7);
+        e_w = e_pos / SCALE + 3.0 * (double)off + 1.1920928955078125e-07;
     } else {
-        // dt/gap <= 4 on a screened interval; 2^-30-slot truncation
-        sp.dw = (float)(4.04 * delta / SCALE);
-        e_w = 4.0 * e_pos / SCALE + 3.725290298461914e-09;
+        // dt/gap <= 4 on a screened interval; 2^-22-slot truncation
+        sp.dw = (float)(4.04 * delta / SCALE + 2.0e-6);
+        e_w = 4.0 * e_pos / SCALE + 9.5367431640625e-07;
     }
     sp.cv = (float)(8.0 * 5.9604644775390625e-08 + 2.0 * e_w);
+    sp.hw = 0.5f - sp.dw;
     return sp;
 }
 
 // Sums of the screen (see above) and the bound they give.
+// Integer-to-float conversions run on the FP64 pipe of this GPU, so the
+// screen counts events in a float and builds weights from bit patterns.
 struct ScreenAcc {
-    float sinv, sd, sdd, saa, sl, sabs, ivmax;
-    int K;
+    float sinv, sd, sdd, sdd2, sl, sabs, ivmax;
+    float K;                 // number of events (exact in FP32 below 2^24)
     __device__ __forceinline__ void init() {
-        sinv = sd = sdd = saa = sl = sabs = ivmax = 0.f;
-        K = 0;
+        sinv = sd = sdd = sdd2 = sl = sabs = ivmax = 0.f;
+        K = 0.f;
     }
     // event (depth dk, sigma s, gain lk) on an interval with depth and gain
-    // differences dd, dl
+    // differences dd, dl.  The error budget of the depths uses
+    // (|Delta_i| + |Delta_{i+1}|)^2 <= (2|dk| + |dd|)^2 <= 8 dk^2 + 2 dd^2.
     __device__ __forceinline__ void add(float dk, float s, float lk, float dd, float dl) {
         const float iv = rcp32(s * s);
         const float div = dk * iv;
@@ -852,33 +864,36 @@ struct ScreenAcc {
         sd += div;
         sdd = fmaf(div, dk, sdd);
         sl += lk;
-        const float ad = fmaf(2.f, fabsf(dk), fabsf(dd));
-        saa = fmaf(ad * ad, iv, saa);
+        sdd2 = fmaf(dd * dd, iv, sdd2);
         sabs += fmaf(2.f, fabsf(lk), fabsf(dl));
         ivmax = fmaxf(ivmax, iv);
-        ++K;
+        K += 1.f;
     }
     // Hardware reciprocal / reciprocal square root (relative error below
     // 2^-21, counted as 8u per use) with every term rounded the safe way.
-    __device__ __forceinline__ float bound(float cv) const {
-        if (K == 0) return -INFINITY;
+    // The q term only lowers the bound, so the cheaper S_L + 1/2 + margins
+    // is returned when it already falls below the threshold bf.
+    __device__ __forceinline__ float bound(float cv, float bf) const {
+        if (K == 0.f) return -INFINITY;
         const float U = 5.9604645e-8f;                        // 2^-24
-        const float sk = (float)(K + 2) * U;
+        const float sk = (K + 2.f) * U;
+        const float e_l = 1.05f * (cv + sk) * sabs;
+        const float ub0 = sl + e_l + 0.5f + 8.f * U * (sabs + 1.f);
+        if (ub0 < bf) return ub0;
         // |ds|/s <= 2 on a screened interval (adjacent sigmas within a factor 3)
         const float gam = 2.2f * cv * 4.f + 6.f * U;
         const float r = rcp32(sinv);
         const float qc = fmaf(-sd * sd, r, sdd);
-        const float qcl = qc - (float)(4 * K + 32) * U * sdd;
+        const float qcl = qc - fmaf(4.f, K, 32.f) * U * sdd;
         float q_lo = 0.f;
         if (qcl > 0.f) {
             const float x1 = qcl * rcp32(1.f + gam + sk) * (1.f - 16.f * U);
             const float a = x1 * rsqrt32(x1) * (1.f - 16.f * U);
-            const float y = saa * (1.f + 2.f * gam + sk) * (1.f + 4.f * U);
+            const float y = fmaf(8.f, sdd, 2.f * sdd2) * (1.f + 2.f * gam + sk) * (1.f + 8.f * U);
             const float e = y > 0.f ? 1.05f * cv * (y * rsqrt32(y)) * (1.f + 16.f * U) : 0.f;
             if (a > e) q_lo = (a - e) * (a - e) * (1.f - 8.f * U);
         }
         const float x_hi = fminf(1.f, ivmax * r * (1.f + 4.f * gam + 2.f * sk + 24.f * U));
-        const float e_l = 1.05f * (cv + sk) * sabs;
         return sl + e_l + 0.5f - 0.5f * q_lo * rcp32(1.f + x_hi) * (1.f - 16.f * U) +
                8.f * U * (sabs + q_lo + 1.f);
     }
@@ -908,13 +923,14 @@ __device__ __forceinline__ int screen_exact_event(const FoldGeom& g,
 
 // Upper bound on ln P of cell (j, duration rows nd / rd / rs) whose first
 // epoch is at u0 (see above): -inf when the cell has no event, +inf when an
-// event falls on an interval outside the screen's error model.
+// event falls on an interval outside the screen's error model; any value
+// below bf when the cell is already known not to reach bf.
 __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom& sg,
                                              const Node8<double>* __restrict__ nd,
                                              const ScreenRec* __restrict__ rd,
                                              const ScreenRec* __restrict__ rs,
                                              const ScreenPeriod& sp, const CellCtx& c,
-                                             int64_t j, unsigned long long u0) {
+                                             int64_t j, unsigned long long u0, float bf) {
     // epochs up to u < ulast + delta: those within delta of t_last (the last
     // epoch's position) fall in the band around it and take the exact event,
     // which drops T > t_last
@@ -923,33 +939,46 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
     ScreenAcc acc;
     acc.init();
     unsigned long long u = u0;
+    // the exact event of the epoch at u (rare: within the band of an epoch);
+    // false when the cell must be evaluated exactly
+    auto exact = [&]() -> bool {
+        if (!have_phi) {
+            phi = cell_phi(c, j);
+            have_phi = true;
+        }
+        const int64_t k = (int64_t)((u - u0) / sp.ustep);
+        return screen_exact_event(g, nd, rd, c, phi, k, u, acc) != 2;
+    };
     if (sp.slots) {
         // regular grid: the interval is the slot's, the weight its fraction
-        const int64_t ns1 = sg.n_slots - 1;
-        ScreenRec rn = rs[min((int64_t)(u >> 40), ns1)];
-        for (int64_t k = 0; u < sp.uend; ++k, u += sp.ustep) {
-            const ScreenRec r = rn;
-            rn = rs[min((int64_t)((u + sp.ustep) >> 40), ns1)];
+        const unsigned ns1 = (unsigned)(sg.n_slots - 1);
+        auto slot = [&](unsigned long long x) { return min((unsigned)(x >> 40), ns1); };
+        auto visit = [&](const ScreenRec& r) -> bool {
+            // fraction of the slot: its top 23 bits as the mantissa of a float in [1, 2)
             const float w =
-                __uint2float_rn((unsigned)((u >> 16) & 0xffffffu)) * 5.9604644775390625e-08f;
-            if (w < sp.dw || w > 1.f - sp.dw) {
-                if (!have_phi) {
-                    phi = cell_phi(c, j);
-                    have_phi = true;
-                }
-                if (screen_exact_event(g, nd, rd, c, phi, k, u, acc) == 2) return INFINITY;
-                continue;
-            }
-            if (r.flags) return INFINITY;
+                __uint_as_float(0x3f800000u | (unsigned)((u >> 17) & 0x7fffffu)) - 1.0f;
+            if (fabsf(w - 0.5f) > sp.hw) return exact();
             const float s = fmaf(w, r.ds, r.s);
-            if (isnan(s)) continue;
+            if (!(s < INFINITY)) return s != s;   // NaN: no event; +inf: not screened
             acc.add(fmaf(w, r.dd, r.d), s, fmaf(w, r.dl, r.l), r.dd, r.dl);
+            return true;
+        };
+        // two records in flight, alternating (no register moves)
+        ScreenRec ra = rs[slot(u)], rb;
+        while (u < sp.uend) {
+            rb = rs[slot(u + sp.ustep)];
+            if (!visit(ra)) return INFINITY;
+            u += sp.ustep;
+            if (!(u < sp.uend)) break;
+            ra = rs[slot(u + sp.ustep)];
+            if (!visit(rb)) return INFINITY;
+            u += sp.ustep;
         }
-        return acc.bound(sp.cv);
+        return acc.bound(sp.cv, bf);
     }
     const int64_t nb1 = g.n_bucket - 1;
     int bnext = g.bucket[min((int64_t)(u >> 40), nb1)];
-    for (int64_t k = 0; u < sp.uend; ++k, u += sp.ustep) {
+    for (; u < sp.uend; u += sp.ustep) {
         // interval guess from the bucket table (the next epoch's entry is
         // fetched one iteration ahead), verified against the stored positions
         int64_t i = bnext > 0 ? (int64_t)bnext - 1 : 0;
@@ -962,25 +991,25 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
             r = rd[i];
         }
         const long long sdu = (long long)(u - v.x);
-        const float w = __int2float_rn((int)(sdu >> 10)) * r.wsc;
+        // position in units of 2^-22 slot (23 bits for du < 2 slots) as a float
+        const float w = (__uint_as_float(0x4b000000u | ((unsigned)(sdu >> 18) & 0x7fffffu)) -
+                         8388608.0f) * r.wsc;
         const float s = fmaf(w, r.ds, r.s);
         // within delta of either end (on a valid interval: w within dw of 0
         // or 1, dw >= 4 delta in slots as dt/gap <= 4): the exact event
         const bool near = isnan(s) ? ((unsigned long long)sdu < sp.delta || v.y - u < sp.delta)
-                                   : (w < sp.dw || w > 1.f - sp.dw);
+                                   : fabsf(w - 0.5f) > sp.hw;
         if (near) {
-            if (!have_phi) {
-                phi = cell_phi(c, j);
-                have_phi = true;
-            }
-            if (screen_exact_event(g, nd, rd, c, phi, k, u, acc) == 2) return INFINITY;
+            if (!exact()) return INFINITY;
             continue;
         }
-        if (r.flags) return INFINITY;
-        if (isnan(s)) continue;
+        if (!(s < INFINITY)) {
+            if (s != s) continue;                  // no event
+            return INFINITY;                       // not screened
+        }
         acc.add(fmaf(w, r.dd, r.d), s, fmaf(w, r.dl, r.l), r.dd, r.dl);
     }
-    return acc.bound(sp.cv);
+    return acc.bound(sp.cv, bf);
 }
 
 // Exact ln P of one cell computed by a whole warp (lanes over epochs); used
@@ -1031,6 +1060,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     __shared__ int sh_nq;
     __shared__ unsigned long long sh_sbest;
     __shared__ float sh_bf;          // sh_sbest rounded down to FP32
+    __shared__ Best sh_tb[256];      // each thread's best evaluated cell (kept out of
+                                     // registers during the screen)
     if (bad_period(P, g)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
@@ -1044,8 +1075,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     }
     const int64_t n_cells = n_phi * n_D;
     const CellCtx c = cell_ctx(g, P, n_phi);
-    double bl = -INFINITY, bD = NAN, bs2 = NAN;
-    long long bc = LLONG_MAX;
+    sh_tb[threadIdx.x] = Best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (threadIdx.x == 0) {
         sh_nq = 0;
         sh_sbest = max_key(-INFINITY);
@@ -1064,7 +1094,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         if (cell < n_cells)
             ub = screen_cell(g, sg, nodes + (int64_t)d * g.n_t0, sg.rec + (int64_t)d * g.n_t0,
                              sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c, j,
-                             (unsigned long long)j * sp.uph);
+                             (unsigned long long)j * sp.uph, sh_bf);
         if (base == 0) {
             // seed: each warp evaluates its lane with the largest finite bound
             float v = (ub < INFINITY) ? ub : -INFINITY;
@@ -1114,7 +1144,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                 ExactAcc<double> a1;
                 a1.init();
                 cell_pass1<double>(g, nd, c, phi, u0, kmax, 0, 1, a1);
-                if (a1.K == 0 || a1.cannot_win(fmax(bl, from_max_key(sh_sbest)))) continue;
+                if (a1.K == 0 || a1.cannot_win(from_max_key(sh_sbest))) continue;
                 const double s2 = 1.0 / a1.s_inv.s;
                 const double Dl = s2 * a1.s_d.s;
                 ExactPen<double> a2;
@@ -1122,12 +1152,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                 cell_pass2<double>(g, nd, c, phi, u0, kmax, 0, 1, a2);
                 const double lnp = a1.s_l.s - 0.5 * (a2.logsum() + a2.quad.s);
                 if (!(lnp == lnp)) continue;   // NaN never selected
-                if (lnp > bl || (lnp == bl && qcell < bc)) {
-                    bl = lnp;
-                    bc = qcell;
-                    bD = Dl;
-                    bs2 = s2;
-                }
+                const Best cand{lnp, qcell, Dl, s2};
+                if (better(cand, sh_tb[threadIdx.x])) sh_tb[threadIdx.x] = cand;
                 atomicMax(&sh_sbest, max_key(lnp));
             }
             __syncthreads();
@@ -1150,8 +1176,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
             __syncthreads();
         }
     }
-    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
-    if (bc != LLONG_MAX) best = Best{bl, bc, bD, sqrt(bs2)};
+    Best best = sh_tb[threadIdx.x];
+    if (best.cell != LLONG_MAX) best.sigma = sqrt(best.sigma);   // held sigma^2
     const Best b = block_argmax(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, g.t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
@@ -1159,7 +1185,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
 
 // resident blocks per SM the register allocation is sized for
 #ifndef NU_SCREEN_MIN_BLOCKS
-#define NU_SCREEN_MIN_BLOCKS 4
+#define NU_SCREEN_MIN_BLOCKS 3
 #endif
 
 __global__ void __launch_bounds__(256, NU_SCREEN_MIN_BLOCKS)
@@ -1274,9 +1300,6 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         R * SCALE < 4.0e18 ? (unsigned long long)llrint(R * SCALE) : 4000000000000000000ull;
     // phase j starts at j * (R / n_phi) slots; per-cell work stays integer
     const unsigned long long uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
-    // epochs per cell from the remaining span in units of 2^32 (a 32-bit
-    // integer), corrected exactly below
-    const float inv_ustep32 = (float)(4294967296.0 / (double)ustep);
     float bl = -INFINITY, bD = NAN, bs2 = NAN;
     long long bc = LLONG_MAX;
     if (threadIdx.x == 0) {
@@ -1295,15 +1318,13 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         if (cell < n_cells) {
             const unsigned long long u0 = (unsigned long long)j * uph;
             if (u0 <= ulast) {
-                int64_t kk = (int64_t)((float)(unsigned)((ulast - u0) >> 32) * inv_ustep32);
-                while (kk > 0 && u0 + (unsigned long long)kk * ustep > ulast) --kk;
-                while (u0 + (unsigned long long)(kk + 1) * ustep <= ulast) ++kk;
-                const int64_t kmax = kk + 1;
+                // epochs with u <= ulast, counted as they are walked
                 const Node4<float>* rd = rec + (int64_t)d * n_slots;
                 SlotPass1 p1;
                 p1.init();
-                unsigned long long u = u0;
-                for (int64_t k = 0; k < kmax; ++k, u += ustep) p1.add(slot_event(rd, u));
+                int kmax = 0;
+                for (unsigned long long u = u0; u <= ulast; u += ustep, ++kmax)
+                    p1.add(slot_event(rd, u));
                 const unsigned int kb = sh_best;
                 const float best_now =
                     fmaxf(bl, kb ? __uint_as_float((kb >> 31) ? (kb & 0x7fffffffu) : ~kb)
@@ -1313,7 +1334,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                     const float s2 = 1.0f / p1.s_inv.s;
                     const int q = atomicAdd(&sh_nq, 1);
                     sh_q[q] = QCell<float>{0.0, u0, (long long)cell, (double)p1.s_l.s, s2,
-                                           s2 * p1.s_d.s, d, (int)kmax};
+                                           s2 * p1.s_d.s, d, kmax};
                 }
             }
         }
