@@ -1066,22 +1066,29 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
     }
+    // the period's constants live in shared memory: registers are kept for
+    // the screen loop (most of these are read only on rare paths)
+    __shared__ ScreenPeriod sh_sp;
+    __shared__ CellCtx sh_cc;
     const int64_t n_phi = (int64_t)ceil(P / g.dt);
-    const ScreenPeriod sp = screen_period(g, sg, P, n_phi);
-    if (!sp.on) {
+    if (threadIdx.x == 0) sh_sp = screen_period(g, sg, P, n_phi);
+    __syncthreads();
+    if (!sh_sp.on) {
         fold_exact_one<double, 8>(g, nodes, n_D, P, p, Q_out, T0_out, Didx_out, dep_out,
                                   sig_out, lnp_out);
         return;
     }
     const int64_t n_cells = n_phi * n_D;
-    const CellCtx c = cell_ctx(g, P, n_phi);
     sh_tb[threadIdx.x] = Best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (threadIdx.x == 0) {
+        sh_cc = cell_ctx(g, P, n_phi);
         sh_nq = 0;
         sh_sbest = max_key(-INFINITY);
         sh_bf = -INFINITY;
     }
     __syncthreads();
+    const ScreenPeriod& sp = sh_sp;
+    const CellCtx& c = sh_cc;
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
     for (int64_t base = 0; base < n_cells; base += blockDim.x, j += blockDim.x) {
@@ -1185,7 +1192,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
 
 // resident blocks per SM the register allocation is sized for
 #ifndef NU_SCREEN_MIN_BLOCKS
-#define NU_SCREEN_MIN_BLOCKS 3
+#define NU_SCREEN_MIN_BLOCKS 4
 #endif
 
 __global__ void __launch_bounds__(256, NU_SCREEN_MIN_BLOCKS)
