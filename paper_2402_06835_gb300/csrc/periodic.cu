@@ -1042,10 +1042,53 @@ __device__ __forceinline__ double exact_cell_warp(const FoldGeom& g,
     return s_l - 0.5 * pen;
 }
 
-// One period of the FP64 path with the screen.  Surviving cells are queued
-// and evaluated exactly, one per thread, whenever a full block's worth has
-// gathered (and at the end); the first wave's best bound per warp is
-// evaluated first by the whole warp to seed the threshold.
+// Order-preserving unsigned key of a float (for a shared atomic max).
+__device__ __forceinline__ unsigned fkey(float x) {
+    const unsigned b = __float_as_uint(x);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_fkey(unsigned k) {
+    return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Exact evaluation of a queued cell by one thread; the thread's best is kept
+// in shared memory and the block's thresholds are raised.
+__device__ __forceinline__ void evaluate_queued(const FoldGeom& g,
+                                               const Node8<double>* __restrict__ nodes,
+                                               const CellCtx& c, int64_t n_phi, long long qcell,
+                                               int qd, unsigned long long* sh_sbest,
+                                               unsigned* sh_bfk, Best* tb) {
+    const int64_t qj = qcell - (int64_t)qd * n_phi;
+    const Node8<double>* nd = nodes + (int64_t)qd * g.n_t0;
+    const double phi = cell_phi(c, qj);
+    const unsigned long long u0 = (unsigned long long)qj * c.swp.u0;
+    const int64_t kmax = cell_kmax(g, c, phi, u0);
+    ExactAcc<double> a1;
+    a1.init();
+    cell_pass1<double>(g, nd, c, phi, u0, kmax, 0, 1, a1);
+    if (a1.K == 0 || a1.cannot_win(from_max_key(*sh_sbest))) return;
+    const double s2 = 1.0 / a1.s_inv.s;
+    const double Dl = s2 * a1.s_d.s;
+    ExactPen<double> a2;
+    a2.init(s2, Dl);
+    cell_pass2<double>(g, nd, c, phi, u0, kmax, 0, 1, a2);
+    const double lnp = a1.s_l.s - 0.5 * (a2.logsum() + a2.quad.s);
+    if (!(lnp == lnp)) return;   // NaN never selected
+    const Best cand{lnp, qcell, Dl, s2};
+    if (better(cand, *tb)) *tb = cand;
+    if (lnp > from_max_key(*sh_sbest)) {
+        atomicMax(sh_sbest, max_key(lnp));
+        atomicMax(sh_bfk, fkey(__double2float_rd(lnp)));
+    }
+}
+
+// One period of the FP64 path with the screen.  Each warp screens its own
+// cells (the block's cells in strides of blockDim) and queues the survivors
+// in its own shared queue; a full queue (32 cells) is evaluated exactly, one
+// cell per lane, by that warp alone, so the screen needs no block barriers.
+// In its first round each warp evaluates its best-bounded cell with all its
+// lanes to seed the threshold.  The thresholds (best ln P, and its FP32
+// lower bound) are shared by the block through atomic maxima.
 __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const ScreenGeom& sg,
                                                   const Node8<double>* __restrict__ nodes,
                                                   int n_D, double P, int64_t p,
@@ -1055,13 +1098,12 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                                                   double* __restrict__ dep_out,
                                                   double* __restrict__ sig_out,
                                                   double* __restrict__ lnp_out) {
-    __shared__ long long sh_qc[512];
-    __shared__ int sh_qd[512];
-    __shared__ int sh_nq;
-    __shared__ unsigned long long sh_sbest;
-    __shared__ float sh_bf;          // sh_sbest rounded down to FP32
-    __shared__ Best sh_tb[256];      // each thread's best evaluated cell (kept out of
-                                     // registers during the screen)
+    __shared__ long long sh_qc[8][64];      // per-warp survivor queues
+    __shared__ int sh_qd[8][64];
+    __shared__ unsigned long long sh_sbest; // best ln P evaluated (max key)
+    __shared__ unsigned sh_bfk;             // its FP32 lower bound (float key)
+    __shared__ Best sh_tb[256];             // each thread's best evaluated cell (kept
+                                            // out of registers during the screen)
     if (bad_period(P, g)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
@@ -1082,30 +1124,36 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     sh_tb[threadIdx.x] = Best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (threadIdx.x == 0) {
         sh_cc = cell_ctx(g, P, n_phi);
-        sh_nq = 0;
         sh_sbest = max_key(-INFINITY);
-        sh_bf = -INFINITY;
+        sh_bfk = fkey(-INFINITY);
     }
     __syncthreads();
     const ScreenPeriod& sp = sh_sp;
     const CellCtx& c = sh_cc;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long* qc = sh_qc[wid];
+    int* qd = sh_qd[wid];
+    int nq = 0;                              // warp-uniform queue length
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
-    for (int64_t base = 0; base < n_cells; base += blockDim.x, j += blockDim.x) {
+    bool first = true;
+    for (int64_t base = (int64_t)wid * 32; base < n_cells; base += blockDim.x,
+                 j += blockDim.x) {
         while (j >= n_phi) {
             j -= n_phi;
             ++d;
         }
-        const int64_t cell = base + threadIdx.x;
+        const int64_t cell = base + lane;
         float ub = -INFINITY;
         if (cell < n_cells)
             ub = screen_cell(g, sg, nodes + (int64_t)d * g.n_t0, sg.rec + (int64_t)d * g.n_t0,
                              sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c, j,
-                             (unsigned long long)j * sp.uph, sh_bf);
-        if (base == 0) {
-            // seed: each warp evaluates its lane with the largest finite bound
+                             (unsigned long long)j * sp.uph, from_fkey(sh_bfk));
+        if (first) {
+            // seed: the warp evaluates its lane with the largest finite bound
+            first = false;
             float v = (ub < INFINITY) ? ub : -INFINITY;
-            int src = threadIdx.x & 31;
+            int src = lane;
             for (int o = 16; o > 0; o >>= 1) {
                 const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
                 const int s2 = __shfl_xor_sync(0xffffffffu, src, o);
@@ -1118,71 +1166,51 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                 const int pd = __shfl_sync(0xffffffffu, d, src);
                 const long long pj = __shfl_sync(0xffffffffu, (long long)j, src);
                 const double lnp = exact_cell_warp(g, nodes + (int64_t)pd * g.n_t0, c, pj);
-                if ((threadIdx.x & 31) == 0 && lnp == lnp && lnp > -INFINITY)
-                    atomicMax(&sh_sbest, max_key(lnp - 1e-9 * (1.0 + fabs(lnp))));
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) sh_bf = __double2float_rd(from_max_key(sh_sbest));
-            __syncthreads();
-        }
-        if (cell < n_cells) {
-            // a cell without events (bound -inf) is never the argmax; NaN
-            // survives.  sh_bf <= every evaluated best (each is in sh_sbest).
-            if (!(ub == -INFINITY) && !(ub < sh_bf)) {
-                const int q = atomicAdd(&sh_nq, 1);
-                sh_qc[q] = cell;
-                sh_qd[q] = d;
+                if (lane == 0 && lnp == lnp && lnp > -INFINITY) {
+                    // a 1e-9 margin: the seeding cell itself stays above the
+                    // threshold and is evaluated again by the thread code
+                    const double seed = lnp - 1e-9 * (1.0 + fabs(lnp));
+                    atomicMax(&sh_sbest, max_key(seed));
+                    atomicMax(&sh_bfk, fkey(__double2float_rd(seed)));
+                }
+                __syncwarp();
             }
         }
-        __syncthreads();
-        const int nq = sh_nq;
-        const bool last = base + blockDim.x >= n_cells;
-        __syncthreads();            // every thread has read nq
-        if (nq >= (int)blockDim.x || (last && nq > 0)) {
-            const int take = last ? nq : (int)blockDim.x;
-            for (int q = threadIdx.x; q < take; q += blockDim.x) {
-                const long long qcell = sh_qc[q];
-                const int qd = sh_qd[q];
-                const int64_t qj = qcell - (int64_t)qd * n_phi;
-                const Node8<double>* nd = nodes + (int64_t)qd * g.n_t0;
-                const double phi = cell_phi(c, qj);
-                const unsigned long long u0 = (unsigned long long)qj * c.swp.u0;
-                const int64_t kmax = cell_kmax(g, c, phi, u0);
-                ExactAcc<double> a1;
-                a1.init();
-                cell_pass1<double>(g, nd, c, phi, u0, kmax, 0, 1, a1);
-                if (a1.K == 0 || a1.cannot_win(from_max_key(sh_sbest))) continue;
-                const double s2 = 1.0 / a1.s_inv.s;
-                const double Dl = s2 * a1.s_d.s;
-                ExactPen<double> a2;
-                a2.init(s2, Dl);
-                cell_pass2<double>(g, nd, c, phi, u0, kmax, 0, 1, a2);
-                const double lnp = a1.s_l.s - 0.5 * (a2.logsum() + a2.quad.s);
-                if (!(lnp == lnp)) continue;   // NaN never selected
-                const Best cand{lnp, qcell, Dl, s2};
-                if (better(cand, sh_tb[threadIdx.x])) sh_tb[threadIdx.x] = cand;
-                atomicMax(&sh_sbest, max_key(lnp));
-            }
-            __syncthreads();
-            const int rest = nq - take;
+        // a cell without events (bound -inf) is never the argmax; NaN survives.
+        // The FP32 threshold is at most every evaluated ln P.
+        const bool keep =
+            cell < n_cells && !(ub == -INFINITY) && !(ub < from_fkey(sh_bfk));
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int pos = nq + __popc(m & ((1u << lane) - 1u));
+            qc[pos] = cell;
+            qd[pos] = d;
+        }
+        nq += __popc(m);
+        __syncwarp();
+        if (nq >= 32) {
+            evaluate_queued(g, nodes, c, n_phi, qc[lane], qd[lane], &sh_sbest, &sh_bfk,
+                            &sh_tb[threadIdx.x]);
+            __syncwarp();
+            nq -= 32;
             long long c2 = 0;
             int d2 = 0;
-            if ((int)threadIdx.x < rest) {
-                c2 = sh_qc[take + threadIdx.x];
-                d2 = sh_qd[take + threadIdx.x];
+            if (lane < nq) {
+                c2 = qc[32 + lane];
+                d2 = qd[32 + lane];
             }
-            __syncthreads();
-            if ((int)threadIdx.x < rest) {
-                sh_qc[threadIdx.x] = c2;
-                sh_qd[threadIdx.x] = d2;
+            __syncwarp();
+            if (lane < nq) {
+                qc[lane] = c2;
+                qd[lane] = d2;
             }
-            if (threadIdx.x == 0) {
-                sh_nq = rest;
-                sh_bf = __double2float_rd(from_max_key(sh_sbest));
-            }
-            __syncthreads();
+            __syncwarp();
         }
     }
+    if (lane < nq)
+        evaluate_queued(g, nodes, c, n_phi, qc[lane], qd[lane], &sh_sbest, &sh_bfk,
+                        &sh_tb[threadIdx.x]);
+    __syncthreads();
     Best best = sh_tb[threadIdx.x];
     if (best.cell != LLONG_MAX) best.sigma = sqrt(best.sigma);   // held sigma^2
     const Best b = block_argmax(best);
@@ -1192,7 +1220,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
 
 // resident blocks per SM the register allocation is sized for
 #ifndef NU_SCREEN_MIN_BLOCKS
-#define NU_SCREEN_MIN_BLOCKS 4
+#define NU_SCREEN_MIN_BLOCKS 3
 #endif
 
 __global__ void __launch_bounds__(256, NU_SCREEN_MIN_BLOCKS)
