@@ -252,11 +252,14 @@ __device__ __forceinline__ bool cannot_win(double s_l, double s_inv, double s_d,
 // FP32 form for the mixed kernel, with the tighter depth term
 // q / (2 (1 + x_max)), x_max = max_k sigma^2/s_k^2 = ivmax / S_inv <= 1
 // (sigma^2 + s_k^2 = s_k^2 (1 + x_k) <= s_k^2 (1 + x_max)).
+// The reciprocals are the hardware approximation (2^-21 relative, far inside
+// the margins).
 __device__ __forceinline__ bool cannot_win_f(float s_l, float s_inv, float s_d, float s_dd,
                                              float ivmax, float best) {
-    const float q = fmaxf(0.0f, s_dd - s_d * s_d / s_inv - 1e-4f * s_dd);
-    const float x = fminf(1.0f, ivmax / s_inv * 1.001f);
-    const float ub = s_l + 0.5f - 0.5f * q / (1.0f + x);
+    const float r = rcp32(s_inv);
+    const float q = fmaxf(0.0f, s_dd - s_d * s_d * r - 1e-4f * s_dd);
+    const float x = fminf(1.0f, ivmax * r * 1.001f);
+    const float ub = s_l + 0.5f - 0.5f * q * rcp32(1.0f + x) * 0.9999f;
     return ub + 1e-4f * fmaxf(1.0f, fabsf(ub)) < best;
 }
 
@@ -1301,12 +1304,22 @@ struct SlotPass2 {
     }
 };
 
+// A cell of the slot path that passed the bound, queued for its second pass.
+struct SCell {
+    unsigned long long u0;
+    long long cell;
+    float s_l, s2, Dl;
+    int d, kmax, pad;
+};
+
 // Epochs walk the slot grid in 24.40 fixed point: u = (T - t_ref)/dt =
 // (j/n_phi + k) P/dt.  The interval is (slot, slot+1) and the weight is the
 // fractional part; on a grid whose epochs sit on the slots this is the
 // interpolation between the bracketing epochs up to their offsets from the
-// slot centres (checked to be below 1e-3 slot).  Cells are processed in waves
-// with the second passes of the surviving cells compacted, as in the exact path.
+// slot centres (checked to be below 1e-3 slot).  Each warp runs the first
+// pass of its cells and queues those the bound keeps in its own shared
+// queue; 32 queued cells get their second passes, one per lane, from that
+// warp alone (no block barriers until the final argmax).
 template <int KC>
 __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ rec,
                                                int64_t n_slots, int n_D, double dt,
@@ -1317,8 +1330,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                                                double* __restrict__ dep_out,
                                                double* __restrict__ sig_out,
                                                double* __restrict__ lnp_out) {
-    __shared__ QCell<float> sh_q[256];
-    __shared__ int sh_nq;
+    __shared__ SCell sh_q[8][64];
     __shared__ unsigned int sh_best;
     FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
     if (bad_period(P, gg)) {
@@ -1337,19 +1349,43 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     const unsigned long long uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
     float bl = -INFINITY, bD = NAN, bs2 = NAN;
     long long bc = LLONG_MAX;
-    if (threadIdx.x == 0) {
-        sh_nq = 0;
-        sh_best = 0u;                       // key below every finite float
-    }
+    if (threadIdx.x == 0) sh_best = 0u;     // key below every finite float
     __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    SCell* q = sh_q[wid];
+    int nq = 0;                              // warp-uniform queue length
+    // second pass of queued cell e, by one lane
+    auto pass2 = [&](const SCell& e) {
+        const Node4<float>* rd = rec + (int64_t)e.d * n_slots;
+        SlotPass2 p2;
+        p2.init(e.s2, e.Dl);
+        unsigned long long u = e.u0;
+        for (int k = 0; k < e.kmax; ++k, u += ustep) {
+            const SlotEvent ev = slot_event(rd, u);
+            p2.add(ev.d, ev.s);
+        }
+        const float lnp = e.s_l - 0.5f * (p2.lsum * 0.693147180559945f + p2.quad.s);
+        if (!(lnp == lnp)) return;
+        if (lnp > bl || (lnp == bl && e.cell < bc)) {
+            bl = lnp;
+            bc = e.cell;
+            bD = p2.Dl;
+            bs2 = p2.s2;
+        }
+        const unsigned int b32 = __float_as_uint(lnp);
+        atomicMax(&sh_best, (b32 >> 31) ? ~b32 : (b32 | 0x80000000u));
+    };
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
-    for (int64_t base = 0; base < n_cells; base += blockDim.x, j += blockDim.x) {
+    for (int64_t base = (int64_t)wid * 32; base < n_cells; base += blockDim.x,
+                 j += blockDim.x) {
         while (j >= n_phi) {
             j -= n_phi;
             ++d;
         }
-        const int64_t cell = base + threadIdx.x;
+        const int64_t cell = base + lane;
+        bool keep = false;
+        SCell e;
         if (cell < n_cells) {
             const unsigned long long u0 = (unsigned long long)j * uph;
             if (u0 <= ulast) {
@@ -1367,40 +1403,27 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                 if (p1.K > 0 &&
                     !cannot_win_f(p1.s_l.s, p1.s_inv.s, p1.s_d.s, p1.s_dd, p1.ivmax, best_now)) {
                     const float s2 = 1.0f / p1.s_inv.s;
-                    const int q = atomicAdd(&sh_nq, 1);
-                    sh_q[q] = QCell<float>{0.0, u0, (long long)cell, (double)p1.s_l.s, s2,
-                                           s2 * p1.s_d.s, d, kmax};
+                    keep = true;
+                    e = SCell{u0, (long long)cell, p1.s_l.s, s2, s2 * p1.s_d.s, d, kmax, 0};
                 }
             }
         }
-        __syncthreads();
-        const int nq = sh_nq;
-        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-            const QCell<float> qc = sh_q[q];
-            const Node4<float>* rd = rec + (int64_t)qc.d * n_slots;
-            SlotPass2 p2;
-            p2.init(qc.s2, qc.Dl);
-            unsigned long long u = qc.u0;
-            for (int k = 0; k < qc.kmax; ++k, u += ustep) {
-                const SlotEvent e = slot_event(rd, u);
-                p2.add(e.d, e.s);
-            }
-            const float lnp =
-                (float)qc.s_l - 0.5f * (p2.lsum * 0.693147180559945f + p2.quad.s);
-            if (!(lnp == lnp)) continue;
-            if (lnp > bl || (lnp == bl && qc.cell < bc)) {
-                bl = lnp;
-                bc = qc.cell;
-                bD = p2.Dl;
-                bs2 = p2.s2;
-            }
-            const unsigned int b32 = __float_as_uint(lnp);
-            atomicMax(&sh_best, (b32 >> 31) ? ~b32 : (b32 | 0x80000000u));
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) q[nq + __popc(m & ((1u << lane) - 1u))] = e;
+        nq += __popc(m);
+        __syncwarp();
+        if (nq >= 32) {
+            pass2(q[lane]);
+            __syncwarp();
+            nq -= 32;
+            SCell e2;
+            if (lane < nq) e2 = q[32 + lane];
+            __syncwarp();
+            if (lane < nq) q[lane] = e2;
+            __syncwarp();
         }
-        __syncthreads();
-        if (threadIdx.x == 0) sh_nq = 0;
-        __syncthreads();
     }
+    if (lane < nq) pass2(q[lane]);
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (bc != LLONG_MAX) best = Best{(double)bl, bc, (double)bD, sqrt((double)bs2)};
     const Best b = block_argmax(best);
@@ -1408,8 +1431,12 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
+#ifndef NU_SLOTS_MIN_BLOCKS
+#define NU_SLOTS_MIN_BLOCKS 4
+#endif
+
 template <int KC>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, NU_SLOTS_MIN_BLOCKS)
 k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, double dt,
              double t_ref, double t_last, const double* __restrict__ periods, int64_t n_P,
              double* __restrict__ Q_out, double* __restrict__ T0_out,
