@@ -39,9 +39,10 @@ MEASURED_FP64_TFLOPS = 1.197   # DFMA microbenchmark on this machine's GB300 (2 DFM
 # FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FOLD_FLOPS_PER_VISIT = 55.0    # 25 in pass 1 + 30 in pass 2 (one log per visit)
-# DRAM bytes (read + write) of one fold launch on the bench workload, from an
-# ncu capture of the kernel as it stands (None until captured)
-FOLD_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one fold launch on the bench workload (sector_19440,
+# FP64), from an ncu capture of the kernel as it stands
+# (profiles/k_fold_screened_sector_19440.md); other workloads report None
+FOLD_TRAFFIC_BYTES = {"sector_19440": 26306048}
 FLUSH_BYTES = 512 << 20        # > 129 MB L2
 
 
@@ -418,7 +419,8 @@ def main():
     roofline = {"kernel": ("k_fold_screened" if args.precision == "fp64" else "k_fold_slots")
                 + " (nu_periodic_search stage, CUDA events)", "bound": "alu",
                 "achieved": fold_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fold_tflops / FP32_PEAK_TFLOPS, "traffic": FOLD_TRAFFIC_BYTES,
+                "frac": fold_tflops / FP32_PEAK_TFLOPS, "traffic": (FOLD_TRAFFIC_BYTES.get(args.workload)
+                            if args.precision == "fp64" else None),
                 "peak_source": "FP32 pipe from unit counts and clocks (152 SM x 128 lanes x "
                                "2 flops x 2.07 GHz)",
                 "algorithmic": f"{visits} visits x {FOLD_FLOPS_PER_VISIT:.0f} flops",
