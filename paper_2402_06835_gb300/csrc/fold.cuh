@@ -71,6 +71,8 @@ struct FoldScratch {
     ScreenRec* srec;        // FP64 slot-indexed screening records
     int* slot_of;           // FP64: slot of every sample
     unsigned* reg;          // FP64: two words per curve (zeroed by the prep)
+    float* lslot;           // FP64: gain at each slot (rounded up), then
+    float* lwin;            //       its windowed maximum (group bound)
 };
 
 // Host side of the batch fold: per-curve layout and launches.

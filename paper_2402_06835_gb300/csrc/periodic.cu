@@ -656,12 +656,20 @@ k_fold_exact(FoldGeom g, const Node8<T>* __restrict__ nodes, int n_D,
 // (triangle inequality in the 1/s^2-weighted norm for q).  Overflow or NaN
 // anywhere makes the bound +inf or NaN, which never skips a cell.
 
+// Width (slots) of the gain windows of the group bound: the events of 32
+// consecutive phases at one epoch step lie in at most 36 consecutive slots
+// (31 phase steps of at most one slot, the interval's right epoch, and the
+// interval before it, which an event taken exactly may use).
+#define NU_LWIN 40
+
 struct ScreenGeom {
     const ScreenRec* rec;              // duration-major rows of n_t0 records
     const ulonglong2* vpair;           // (position of epoch i, of epoch i+1), 24.40
                                        // slots from t_ref; the last .y is 2^64 - 1
     const ScreenRec* srec;             // the same records placed at their epochs'
                                        // slots: duration-major rows of n_slots
+    const float* lwin;                 // rows of n_slots: max(0, largest gain of the
+                                       // epochs in slots [s, s + NU_LWIN)), rounded up
     int64_t n_slots;
     const unsigned* reg;               // [0]: an epoch is off the slot grid,
                                        // [1]: max |offset from its slot| (float bits)
@@ -709,7 +717,8 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
                                             const double* __restrict__ t0, int64_t gid,
                                             int64_t i, int64_t n, int64_t d, double gap_max,
                                             double dt, ScreenRec* __restrict__ out,
-                                            ScreenRec* __restrict__ sout, int64_t n_slots,
+                                            ScreenRec* __restrict__ sout,
+                                            float* __restrict__ lslot, int64_t n_slots,
                                             const int* __restrict__ slot_of,
                                             ulonglong2* __restrict__ vpair) {
     // an interval needs both ends valid and a gap in (0, gap_max]
@@ -757,7 +766,12 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
     r.flags = flags;
     out[gid] = r;
     const int sl = slot_of[i];
-    if (sl >= 0 && sl < n_slots) sout[d * n_slots + sl] = r;
+    if (sl >= 0 && sl < n_slots) {
+        sout[d * n_slots + sl] = r;
+        // gain at the slot, rounded up (an invalid epoch never adds to S_L)
+        const bool ok = !isnan(sigma_at<T>(depth, var, gain, gid));
+        lslot[d * n_slots + sl] = ok ? fmaxf(0.f, __double2float_ru(l0)) : 0.f;
+    }
     if (d == 0) {
         auto pos = [&](int64_t k) -> unsigned long long {
             const double v = (t0[k] - t0[0]) / dt * 1099511627776.0;
@@ -779,13 +793,24 @@ __global__ void k_screen(const T* __restrict__ depth, const T* __restrict__ var,
                          const T* __restrict__ gain, const double* __restrict__ t0s,
                          int64_t n_t0, int n_D, double gap_max, double dt,
                          ScreenRec* __restrict__ rec, ScreenRec* __restrict__ srec,
-                         int64_t n_slots, const int* __restrict__ slot_of,
-                         ulonglong2* __restrict__ vpair) {
+                         float* __restrict__ lslot, int64_t n_slots,
+                         const int* __restrict__ slot_of, ulonglong2* __restrict__ vpair) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= n_t0 * (int64_t)n_D) return;
     const int64_t d = gid / n_t0, i = gid - d * n_t0;
-    make_screen<T>(depth, var, gain, t0s, gid, i, n_t0, d, gap_max, dt, rec, srec, n_slots,
-                   slot_of, vpair);
+    make_screen<T>(depth, var, gain, t0s, gid, i, n_t0, d, gap_max, dt, rec, srec, lslot,
+                   n_slots, slot_of, vpair);
+}
+
+// lwin[x] = max(0, lslot[x .. x + NU_LWIN)) over the flat array (a window that
+// runs into the next row only raises the bound).
+__global__ void k_lwin(const float* __restrict__ lslot, int64_t n, float* __restrict__ lwin) {
+    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    float m = 0.f;
+    const int64_t e = x + NU_LWIN < n ? x + NU_LWIN : n;
+    for (int64_t t = x; t < e; ++t) m = fmaxf(m, lslot[t]);
+    lwin[x] = m;
 }
 
 // Per-period constants of the screen.
@@ -1148,7 +1173,38 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         }
         const int64_t cell = base + lane;
         float ub = -INFINITY;
-        if (cell < n_cells)
+        bool skip = false;
+        if (!first && sp.slots && sp.ustep < (1ull << 58)) {
+            // Group bound: the warp's 32 cells, when they are consecutive
+            // phases of one duration, all have S_L <= sum over epoch steps of
+            // the largest gain in the window their events can touch, and
+            // ln P <= S_L + 1/2; if that is below the threshold, none of the
+            // 32 cells is screened.
+            const int d0 = __shfl_sync(0xffffffffu, d, 0);
+            const long long j0 = __shfl_sync(0xffffffffu, (long long)j, 0);
+            if (__all_sync(0xffffffffu, d == d0 && cell < n_cells)) {
+                const float* lw = sg.lwin + (int64_t)d0 * sg.n_slots;
+                const unsigned ns1 = (unsigned)(sg.n_slots - 1);
+                const unsigned long long st32 = 32ull * sp.ustep;
+                float sum = 0.f, cnt = 0.f;
+                for (unsigned long long u = (unsigned long long)j0 * sp.uph +
+                                            (unsigned long long)lane * sp.ustep;
+                     u < sp.uend; u += st32) {
+                    const unsigned s0 = (unsigned)(u >> 40);
+                    sum += lw[min(s0 > 0u ? s0 - 1u : 0u, ns1)];
+                    cnt += 1.f;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                }
+                // the window maxima are rounded up and non-negative: the FP32
+                // sum errs by far less than (cnt + 64) 2^-23 of itself
+                const float ubg = sum * fmaf(cnt + 64.f, 1.1920929e-7f, 1.f) + 0.5f + 1e-6f;
+                skip = ubg < from_fkey(sh_bfk);
+            }
+        }
+        if (cell < n_cells && !skip)
             ub = screen_cell(g, sg, nodes + (int64_t)d * g.n_t0, sg.rec + (int64_t)d * g.n_t0,
                              sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c, j,
                              (unsigned long long)j * sp.uph, from_fkey(sh_bfk));
@@ -1460,7 +1516,8 @@ __global__ void __launch_bounds__(256)
 k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restrict__ t,
              const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
              const ulonglong2* __restrict__ vpair, const ScreenRec* __restrict__ srec,
-             const unsigned* __restrict__ reg, const int* __restrict__ bucket,
+             const float* __restrict__ lwin, const unsigned* __restrict__ reg,
+             const int* __restrict__ bucket,
              const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
              const double* __restrict__ periods, int64_t n_P, unsigned long long* counter,
              double* __restrict__ Q_out, double* __restrict__ T0_out,
@@ -1488,7 +1545,8 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
                         gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
             if (KIND == 0) {
                 const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off,
-                                    srec + fs.srec_off, fs.n_slots, reg + 2 * g, fs.screen};
+                                    srec + fs.srec_off, lwin + fs.srec_off, fs.n_slots,
+                                    reg + 2 * g, fs.screen};
                 fold_screened_one(gg, sg, (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
                                   periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                                   lnp_out);
@@ -1527,7 +1585,7 @@ __global__ void k_screen_batch(const T* __restrict__ depth, const T* __restrict_
                                const int64_t* __restrict__ s_off, int n_D, double gap_max,
                                double dt, ScreenRec* __restrict__ rec,
                                ulonglong2* __restrict__ vpair, ScreenRec* __restrict__ srec,
-                               const int* __restrict__ slot_of) {
+                               float* __restrict__ lslot, const int* __restrict__ slot_of) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= s_off[n_seg] * (int64_t)n_D) return;
     int lo = 0, hi = n_seg;
@@ -1541,7 +1599,8 @@ __global__ void k_screen_batch(const T* __restrict__ depth, const T* __restrict_
     const int64_t w = gid - s0 * n_D;
     const int64_t d = w / ng, i = w - d * ng;
     make_screen<T>(depth, var, gain, t + s0, gid, i, ng, d, gap_max, dt, rec,
-                   srec + fs.srec_off, fs.n_slots, slot_of + s0, vpair + s0);
+                   srec + fs.srec_off, lslot + fs.srec_off, fs.n_slots, slot_of + s0,
+                   vpair + s0);
 }
 
 // Slots of every sample of the screened curves (reg: two words per curve).
@@ -1677,12 +1736,15 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
                 t, segs_dev, n_seg, s_off_dev, 1.0 / dt, fs.slot_of, fs.reg);
             k_fill_screen<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(
                 fs.srec, fb.n_srec_total);
+            cudaMemsetAsync(fs.lslot, 0, (size_t)(fb.n_srec_total + 1) * sizeof(float), st);
             k_screen_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
                 n_seg, s_off_dev, n_D, gap_factor * dt, dt,
                 (ScreenRec*)((char*)fs.nodes + L.off_screen),
-                (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.slot_of);
-            launched += 3;
+                (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.lslot, fs.slot_of);
+            k_lwin<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(fs.lslot, fb.n_srec_total,
+                                                                    fs.lwin);
+            launched += 4;
         } else
             k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
@@ -1718,17 +1780,17 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
     if (fb.any_exact) {
         if (fp64)
             k_fold_batch<0><<<grid, threads, 0, st>>>(
-                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.reg, fs.bucket, fs.rec,
+                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket, fs.rec,
                 n_D, dt, gap_factor, periods, n_P, counter, Q, T0, Didx, dep, sig, lnp);
         else
             k_fold_batch<1><<<grid, threads, 0, st>>>(
-                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.reg, fs.bucket, fs.rec,
+                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket, fs.rec,
                 n_D, dt, gap_factor, periods, n_P, counter, Q, T0, Didx, dep, sig, lnp);
         ++launched;
     }
     if (fb.any_slots) {
         k_fold_batch<2><<<grid, threads, 0, st>>>(
-            segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.reg, fs.bucket, fs.rec, n_D,
+            segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket, fs.rec, n_D,
             dt, gap_factor, periods, n_P, counter + 1, Q, T0, Didx, dep, sig, lnp);
         ++launched;
     }
@@ -1750,7 +1812,7 @@ namespace nu {
 // Scratch layout of the single-curve fold.
 struct SingleLayout {
     ExactLayout el;
-    size_t exact, bucket, slot_of, flag, rec, srec, total;
+    size_t exact, bucket, slot_of, flag, rec, srec, lslot, lwin, total;
 };
 
 static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool fp64) {
@@ -1764,7 +1826,9 @@ static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool 
     L.flag = L.slot_of + al((size_t)n_t0 * sizeof(int));
     L.rec = L.flag + 256;
     L.srec = L.rec + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>)));
-    L.total = L.srec + (fp64 ? al((size_t)n_slots * n_D * sizeof(ScreenRec)) : 0);
+    L.lslot = L.srec + (fp64 ? al((size_t)n_slots * n_D * sizeof(ScreenRec)) : 0);
+    L.lwin = L.lslot + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
+    L.total = L.lwin + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
     return L;
 }
 
@@ -1826,8 +1890,10 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             ScreenRec* nrec = (ScreenRec*)(scratch + L.exact + L.el.off_screen);
             ulonglong2* vpair = (ulonglong2*)(scratch + L.exact + L.el.off_vpos);
             ScreenRec* srec = (ScreenRec*)(scratch + L.srec);
+            float* lslot = (float*)(scratch + L.lslot);
+            float* lwin = (float*)(scratch + L.lwin);
             unsigned* reg = (unsigned*)(flag + 1);
-            const ScreenGeom sg{nrec, vpair, srec, n_slots, reg,
+            const ScreenGeom sg{nrec, vpair, srec, lwin, n_slots, reg,
                                 (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0};
             e = cudaMemsetAsync(flag, 0, 256, st);
             if (e != cudaSuccess) {
@@ -1837,16 +1903,23 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             k_slot_offsets<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, 1.0 / phase_step,
                                                               n_slots, slot_of, reg);
             k_fill_screen<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(srec, n_slots * n_D);
+            e = cudaMemsetAsync(lslot, 0, (size_t)n_slots * n_D * sizeof(float), st);
+            if (e != cudaSuccess) {
+                count_launches(launched + 2);
+                return cuda_fail(e, (std::string(who) + ": memset").c_str());
+            }
             k_nodes<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
                 t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
             k_screen<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, n_slots, slot_of, vpair);
+                t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, lslot, n_slots, slot_of,
+                vpair);
+            k_lwin<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(lslot, n_slots * n_D, lwin);
             k_fold_screened<<<(unsigned)n_P, 256, 0, st>>>(
                 g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                 D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-            launched += 6;
+            launched += 7;
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
