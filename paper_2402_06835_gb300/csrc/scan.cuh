@@ -32,19 +32,32 @@ namespace nu {
 // level l+1 element q composes the level-l elements [child_begin, child_end)
 // of the same segment; the top level holds, per segment, the elements
 // [top_begin, top_end).  A single light curve is one segment.
+// Work item of a thread when each warp uses only its first L lanes: the
+// scan's work per item is a sequential FP64 recursion, and this GPU issues
+// one FP64 warp instruction per 64 cycles per sub-partition however many
+// lanes are active, so a scan with few items spreads them over many warps
+// (L = 1 puts one item on each sub-partition) and a large one packs them.
+__device__ __forceinline__ int64_t spread_item(int L) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = (int)(t & 31);
+    return lane < L ? (t >> 5) * L + lane : -1;
+}
+
 template <class Op>
-__global__ void k_scan_elem(Op op, int64_t n_chunks, typename Op::Elem* __restrict__ E) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= n_chunks) return;
+__global__ void k_scan_elem(Op op, int64_t n_chunks, typename Op::Elem* __restrict__ E,
+                            int L) {
+    const int64_t c = spread_item(L);
+    if (c < 0 || c >= n_chunks) return;
     op.elem(c, E[c]);
 }
 
 template <class Op>
 __global__ void k_scan_combine(Op op, const typename Op::Elem* __restrict__ Ein,
                                const int64_t* __restrict__ cb, const int64_t* __restrict__ ce,
-                               int64_t n_out, typename Op::Elem* __restrict__ Eout) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= n_out) return;
+                               int64_t n_out, typename Op::Elem* __restrict__ Eout,
+                               int L) {
+    const int64_t q = spread_item(L);
+    if (q < 0 || q >= n_out) return;
     typename Op::Elem acc = Ein[cb[q]];
     for (int64_t r = cb[q] + 1; r < ce[q]; ++r) op.combine(acc, Ein[r]);
     Eout[q] = acc;
@@ -68,9 +81,9 @@ template <class Op>
 __global__ void k_scan_down(Op op, const typename Op::Elem* __restrict__ E,
                             const int64_t* __restrict__ cb, const int64_t* __restrict__ ce,
                             int64_t n_parent, const typename Op::State* __restrict__ Sparent,
-                            typename Op::State* __restrict__ S) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= n_parent) return;
+                            typename Op::State* __restrict__ S, int L) {
+    const int64_t q = spread_item(L);
+    if (q < 0 || q >= n_parent) return;
     typename Op::State s = Sparent[q];
     for (int64_t r = cb[q]; r < ce[q]; ++r) {
         S[r] = s;
@@ -79,9 +92,10 @@ __global__ void k_scan_down(Op op, const typename Op::Elem* __restrict__ E,
 }
 
 template <class Op>
-__global__ void k_scan_final(Op op, int64_t n_chunks, const typename Op::State* __restrict__ S) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= n_chunks) return;
+__global__ void k_scan_final(Op op, int64_t n_chunks, const typename Op::State* __restrict__ S,
+                             int L) {
+    const int64_t c = spread_item(L);
+    if (c < 0 || c >= n_chunks) return;
     op.final(c, S[c]);
 }
 
@@ -175,15 +189,27 @@ inline int run_scan(const Op& op, const ScanShape& sh, const int64_t* idx_dev, c
         Sp[l] = (S*)(ws + off);
         off += al((size_t)sh.count[l] * sizeof(S));
     }
-    const int TH = 64;
+    const int TH = 128;
+    // lanes per warp for n items: about 2 warps per sub-partition of 152 SMs
+    // before lanes are packed
+    auto lanes = [](int64_t n) {
+        int L = 1;
+        while (L < 32 && n > (int64_t)L * 1216) L *= 2;
+        return L;
+    };
+    auto grid = [&](int64_t n, int L) { return div_up(div_up(n, L) * 32, TH); };
     int launches = 0;
-    k_scan_elem<Op><<<div_up(sh.count[0], TH), TH, 0, st>>>(op, sh.count[0], Ep[0]);
-    ++launches;
+    {
+        const int L = lanes(sh.count[0]);
+        k_scan_elem<Op><<<grid(sh.count[0], L), TH, 0, st>>>(op, sh.count[0], Ep[0], L);
+        ++launches;
+    }
     for (int l = 1; l <= sh.levels; ++l) {
         const int64_t* cb = idx_dev + sh.child_off[l];
         const int64_t* ce = cb + sh.count[l];
-        k_scan_combine<Op><<<div_up(sh.count[l], TH), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
-                                                                 sh.count[l], Ep[l]);
+        const int L = lanes(sh.count[l]);
+        k_scan_combine<Op><<<grid(sh.count[l], L), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
+                                                               sh.count[l], Ep[l], L);
         ++launches;
     }
     const int64_t* tb = idx_dev + sh.top_off;
@@ -193,12 +219,16 @@ inline int run_scan(const Op& op, const ScanShape& sh, const int64_t* idx_dev, c
     for (int l = sh.levels; l >= 1; --l) {
         const int64_t* cb = idx_dev + sh.child_off[l];
         const int64_t* ce = cb + sh.count[l];
-        k_scan_down<Op><<<div_up(sh.count[l], TH), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
-                                                              sh.count[l], Sp[l], Sp[l - 1]);
+        const int L = lanes(sh.count[l]);
+        k_scan_down<Op><<<grid(sh.count[l], L), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
+                                                           sh.count[l], Sp[l], Sp[l - 1], L);
         ++launches;
     }
-    k_scan_final<Op><<<div_up(sh.count[0], TH), TH, 0, st>>>(op, sh.count[0], Sp[0]);
-    ++launches;
+    {
+        const int L = lanes(sh.count[0]);
+        k_scan_final<Op><<<grid(sh.count[0], L), TH, 0, st>>>(op, sh.count[0], Sp[0], L);
+        ++launches;
+    }
     return launches;
 }
 
