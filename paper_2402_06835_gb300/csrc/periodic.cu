@@ -1110,6 +1110,54 @@ __device__ __forceinline__ void evaluate_queued(const FoldGeom& g,
     }
 }
 
+// The same evaluation by a whole warp (lanes over epochs, fixed reduction
+// order); called by all lanes with the same cell.  Used for every evaluation
+// of a period whose cells have 32 or more epochs, where one cell per lane
+// would leave most lanes idle whenever fewer than 32 cells are queued.
+__device__ __forceinline__ void evaluate_queued_warp(const FoldGeom& g,
+                                                    const Node8<double>* __restrict__ nodes,
+                                                    const CellCtx& c, int64_t n_phi,
+                                                    long long qcell, int qd,
+                                                    unsigned long long* sh_sbest,
+                                                    unsigned* sh_bfk, Best* tb) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t qj = qcell - (int64_t)qd * n_phi;
+    const Node8<double>* nd = nodes + (int64_t)qd * g.n_t0;
+    const double phi = cell_phi(c, qj);
+    const unsigned long long u0 = (unsigned long long)qj * c.swp.u0;
+    const int64_t kmax = cell_kmax(g, c, phi, u0);
+    ExactAcc<double> a1;
+    a1.init();
+    cell_pass1<double>(g, nd, c, phi, u0, kmax, lane, 32, a1);
+    double s_inv = a1.s_inv.s, s_d = a1.s_d.s, s_l = a1.s_l.s, s_dd = a1.s_dd;
+    int K = a1.K;
+    for (int o = 16; o > 0; o >>= 1) {
+        s_inv += __shfl_xor_sync(FULL, s_inv, o);
+        s_d += __shfl_xor_sync(FULL, s_d, o);
+        s_l += __shfl_xor_sync(FULL, s_l, o);
+        s_dd += __shfl_xor_sync(FULL, s_dd, o);
+        K += __shfl_xor_sync(FULL, K, o);
+    }
+    const double best_now = __shfl_sync(FULL, from_max_key(*sh_sbest), 0);
+    if (K == 0 || cannot_win(s_l, s_inv, s_d, s_dd, best_now)) return;
+    const double s2 = 1.0 / s_inv;
+    const double Dl = s2 * s_d;
+    ExactPen<double> a2;
+    a2.init(s2, Dl);
+    cell_pass2<double>(g, nd, c, phi, u0, kmax, lane, 32, a2);
+    double pen = a2.logsum() + a2.quad.s;
+    for (int o = 16; o > 0; o >>= 1) pen += __shfl_xor_sync(FULL, pen, o);
+    const double lnp = s_l - 0.5 * pen;
+    if (lane != 0 || !(lnp == lnp)) return;      // NaN never selected
+    const Best cand{lnp, qcell, Dl, s2};
+    if (better(cand, *tb)) *tb = cand;
+    if (lnp > from_max_key(*sh_sbest)) {
+        atomicMax(sh_sbest, max_key(lnp));
+        atomicMax(sh_bfk, fkey(__double2float_rd(lnp)));
+    }
+}
+
 // One period of the FP64 path with the screen.  Each warp screens its own
 // cells (the block's cells in strides of blockDim) and queues the survivors
 // in its own shared queue; a full queue (32 cells) is evaluated exactly, one
@@ -1162,6 +1210,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     long long* qc = sh_qc[wid];
     int* qd = sh_qd[wid];
     int nq = 0;                              // warp-uniform queue length
+    // cells of 32 or more epochs are evaluated warp-cooperatively
+    const bool coop = g.t_last - g.t_ref >= 32.0 * P;
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
     bool first = true;
@@ -1248,8 +1298,14 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         nq += __popc(m);
         __syncwarp();
         if (nq >= 32) {
-            evaluate_queued(g, nodes, c, n_phi, qc[lane], qd[lane], &sh_sbest, &sh_bfk,
-                            &sh_tb[threadIdx.x]);
+            if (coop) {
+                for (int q = 0; q < 32; ++q)
+                    evaluate_queued_warp(g, nodes, c, n_phi, qc[q], qd[q], &sh_sbest, &sh_bfk,
+                                         &sh_tb[threadIdx.x]);
+            } else {
+                evaluate_queued(g, nodes, c, n_phi, qc[lane], qd[lane], &sh_sbest, &sh_bfk,
+                                &sh_tb[threadIdx.x]);
+            }
             __syncwarp();
             nq -= 32;
             long long c2 = 0;
@@ -1266,9 +1322,14 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
             __syncwarp();
         }
     }
-    if (lane < nq)
+    if (coop) {
+        for (int q = 0; q < nq; ++q)
+            evaluate_queued_warp(g, nodes, c, n_phi, qc[q], qd[q], &sh_sbest, &sh_bfk,
+                                 &sh_tb[threadIdx.x]);
+    } else if (lane < nq) {
         evaluate_queued(g, nodes, c, n_phi, qc[lane], qd[lane], &sh_sbest, &sh_bfk,
                         &sh_tb[threadIdx.x]);
+    }
     __syncthreads();
     Best best = sh_tb[threadIdx.x];
     if (best.cell != LLONG_MAX) best.sigma = sqrt(best.sigma);   // held sigma^2
