@@ -190,11 +190,12 @@ inline int run_scan(const Op& op, const ScanShape& sh, const int64_t* idx_dev, c
         off += al((size_t)sh.count[l] * sizeof(S));
     }
     const int TH = 128;
-    // lanes per warp for n items: about 2 warps per sub-partition of 152 SMs
-    // before lanes are packed
+    // lanes per warp for n items: at most one warp per sub-partition (608 on
+    // 152 SMs) — more warps would share a sub-partition's FP64 pipe — with
+    // as few lanes per warp as that allows
     auto lanes = [](int64_t n) {
         int L = 1;
-        while (L < 32 && n > (int64_t)L * 1216) L *= 2;
+        while (L < 32 && n > (int64_t)L * 608) L *= 2;
         return L;
     };
     auto grid = [&](int64_t n, int L) { return div_up(div_up(n, L) * 32, TH); };
