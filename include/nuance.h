@@ -180,6 +180,27 @@ nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
                              double* depth_out_dev, double* sigma_out_dev,
                              double* lnP_dev);
 
+/* Masking of a found transit for the next search of a multi-planet system
+ * (Sect. 3.5 and the TOI-540 comparison, Sect. 4.3: after a periodic search,
+ * the linear-search products of the trial epochs in windows of width 2 D
+ * centred on the detected transits are masked and the periodic search is
+ * run again on the same grid).
+ *
+ * Marks every grid entry (all durations) whose epoch t0_i lies within
+ * half_width of a transit of the candidate (P, T0) as invalid, in place:
+ * with n = rint((t0_i - T0) / P), the entry is masked when
+ * |t0_i - (T0 + n P)| < half_width (each operation rounded once, in FP64);
+ * depth, var and dlnl of a masked entry become NaN, which the periodic
+ * search treats as a missing epoch.  half_width = D of the candidate gives
+ * the paper's window of width 2 D.
+ *   depth/var/dlnl  [n_D][n_t0], element type by prec (as nu_linear_search)
+ * Enqueued on `stream`; no synchronisation.  Errors: NU_EINVAL (null array,
+ * n_t0 < 1, n_D < 1, P not finite and > 0, T0 or half_width not finite),
+ * NU_ECUDA. */
+nu_status nu_mask_transits(const double* t0s_dev, int64_t n_t0, int n_D, void* depth_dev,
+                           void* var_dev, void* dlnl_dev, nu_precision prec, double P,
+                           double T0, double half_width, void* stream);
+
 /* Periodic search without device allocation (no counterpart in the paper).
  *
  * Same inputs, outputs and results as nu_periodic_search, for callers that

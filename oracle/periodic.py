@@ -160,3 +160,22 @@ def best(res, periods):
     return dict(period=float(periods[p]), T0=float(res["T0"][p]),
                 D_idx=int(res["D_idx"][p]), depth=float(res["depth"][p]),
                 sigma=float(res["sigma"][p]), Q=float(res["Q"][p]), index=p)
+
+
+def mask_transits(t0s, depth, var, dlnl, P, T0, half_width):
+    """Masking of a found candidate before the next search (Sect. 3.5, and
+    the TOI-540 comparison of Sect. 4.3: trial epochs in windows of width
+    2 D centred on the detected transits are masked in the linear-search
+    products).  Entries of every duration whose epoch lies within
+    half_width of T0 + n P (n the nearest integer, each operation rounded
+    once in FP64) become NaN.  Returns masked copies and the epoch mask."""
+    t0s = np.asarray(t0s, dtype=np.float64)
+    n = np.rint((t0s - T0) / P)
+    dist = np.abs(t0s - (T0 + n * P))
+    m = dist < half_width
+    out = []
+    for a in (depth, var, dlnl):
+        b = np.array(a, copy=True)
+        b[:, m] = np.nan
+        out.append(b)
+    return out[0], out[1], out[2], m

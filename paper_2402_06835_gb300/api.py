@@ -56,6 +56,8 @@ def _load():
     lib.nu_linear_search.argtypes = [P, P, I64, P, I, I, D, I, P, P, P, P]
     lib.nu_periodic_search.argtypes = [P, I64, P, I, P, P, P, I, P, I64, D, D, P,
                                        P, P, P, P, P, P]
+    lib.nu_mask_transits.argtypes = [P, I64, I, P, P, P, I, D, D, D, P]
+    lib.nu_mask_transits.restype = I
     lib.nu_periodic_search_noalloc.argtypes = lib.nu_periodic_search.argtypes
     lib.nu_periodic_search_noalloc.restype = I
     lib.nu_periodic_search_noalloc_limit.restype = ctypes.c_uint64
@@ -225,6 +227,25 @@ def nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision="fp64",
                                 _p(res["sigma"]), _p(res["lnP"]))
     _check(st, "nu_periodic_search")
     return res
+
+
+def nu_mask_transits(t0s, depth, var, dlnl, period, T0, half_width, precision="fp64",
+                     stream=None):
+    """Mask, in place, the grid entries within half_width of the transits of
+    (period, T0) (see nu_mask_transits in the header); returns the arrays."""
+    t0s = _dev(t0s, "t0s")
+    dt = torch.float64 if _PREC[precision] == NU_FP64 else torch.float32
+    for a, nm in ((depth, "depth"), (var, "var"), (dlnl, "dlnl")):
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == dt
+                and a.is_contiguous() and a.numel() % max(1, t0s.numel()) == 0):
+            raise ValueError(f"{nm} must be a contiguous CUDA tensor of the precision's dtype "
+                             "with n_D * n_t0 elements (masked in place)")
+    n_D = depth.numel() // t0s.numel()
+    st = LIB.nu_mask_transits(_p(t0s), t0s.numel(), n_D, _p(depth), _p(var), _p(dlnl),
+                              _PREC[precision], float(period), float(T0), float(half_width),
+                              _stream_ptr(stream))
+    _check(st, "nu_mask_transits")
+    return depth, var, dlnl
 
 
 def nu_periodic_search_noalloc(t0s, Ds, depth, var, dlnl, periods, precision="fp64",

@@ -2083,6 +2083,54 @@ extern "C" nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
     return NU_OK;
 }
 
+// ------------------------------------------------ transit masking
+// One thread per epoch: the distance to the nearest transit of (P, T0),
+// each operation rounded once (no contraction), decides for all durations.
+template <typename T>
+__global__ void k_mask_transits(const double* __restrict__ t0s, int64_t n_t0, int n_D,
+                                T* __restrict__ depth, T* __restrict__ var,
+                                T* __restrict__ dlnl, double P, double T0, double hw) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_t0) return;
+    const double t = t0s[i];
+    const double n = rint(__ddiv_rn(__dsub_rn(t, T0), P));
+    const double dist = fabs(__dsub_rn(t, __dadd_rn(T0, __dmul_rn(n, P))));
+    if (!(dist < hw)) return;
+    for (int d = 0; d < n_D; ++d) {
+        const int64_t o = (int64_t)d * n_t0 + i;
+        depth[o] = T(NAN);
+        var[o] = T(NAN);
+        dlnl[o] = T(NAN);
+    }
+}
+
+extern "C" nu_status nu_mask_transits(const double* t0s_dev, int64_t n_t0, int n_D,
+                                      void* depth_dev, void* var_dev, void* dlnl_dev,
+                                      nu_precision prec, double P, double T0,
+                                      double half_width, void* stream) {
+    if (!t0s_dev || !depth_dev || !var_dev || !dlnl_dev)
+        return fail(NU_EINVAL, "nu_mask_transits: null array");
+    if (n_t0 < 1 || n_D < 1) return fail(NU_EINVAL, "nu_mask_transits: need n_t0, n_D >= 1");
+    if (prec != NU_FP64 && prec != NU_MIXED)
+        return fail(NU_EINVAL, "nu_mask_transits: unknown precision");
+    if (!(P > 0.0) || !std::isfinite(P) || !std::isfinite(T0) || !std::isfinite(half_width))
+        return fail(NU_EINVAL, "nu_mask_transits: P must be finite and > 0, T0 and "
+                               "half_width finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == NU_FP64)
+        k_mask_transits<double><<<div_up(n_t0, 256), 256, 0, st>>>(
+            t0s_dev, n_t0, n_D, (double*)depth_dev, (double*)var_dev, (double*)dlnl_dev, P, T0,
+            half_width);
+    else
+        k_mask_transits<float><<<div_up(n_t0, 256), 256, 0, st>>>(
+            t0s_dev, n_t0, n_D, (float*)depth_dev, (float*)var_dev, (float*)dlnl_dev, P, T0,
+            half_width);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "nu_mask_transits: launch");
+    return NU_OK;
+}
+
 // ------------------------------------------------ allocation-free variant
 // nu_periodic_search_noalloc runs the same kernels as nu_periodic_search but
 // takes its scratch (epoch records, bucket table, slot table, flag) from the

@@ -225,3 +225,46 @@ def test_no_valid_cell():
     out = periodic.periodic_search(t0s, nan, nan, nan, np.array([0.05]), 0.01)
     assert out["Q"][0] == 0.0 and out["lnP"][0] == -np.inf
     assert out["D_idx"][0] == -1
+
+
+def test_mask_transits_matches_nearest_transit_distance():
+    """The oracle's mask (Sect. 4.3: windows of width 2 D centred on the
+    detected transits) equals the brute-force minimum distance to any
+    transit T0 + n P, away from ties at the window edge."""
+    rng = np.random.default_rng(91)
+    t0s = np.sort(rng.uniform(1000.0, 1010.0, 3000))
+    g = dict(depth=rng.normal(0, 1e-3, (2, 3000)), var=rng.uniform(1e-8, 2e-8, (2, 3000)),
+             dlnl=rng.uniform(0, 3, (2, 3000)))
+    for P, T0, hw in ((0.37, 1000.11, 0.02), (1.9, 1003.3, 0.05), (7.0, 995.5, 0.1)):
+        d, v, l, m = periodic.mask_transits(t0s, g["depth"], g["var"], g["dlnl"], P, T0, hw)
+        ns = np.arange(-40, 60)
+        brute = np.min(np.abs(t0s[:, None] - (T0 + ns[None, :] * P)), axis=1)
+        clear = np.abs(brute - hw) > 1e-9
+        assert np.array_equal(m[clear], (brute < hw)[clear])
+        assert np.isnan(d[:, m]).all() and np.isnan(v[:, m]).all() and np.isnan(l[:, m]).all()
+        assert np.array_equal(d[:, ~m], g["depth"][:, ~m])
+        assert 0 < m.sum() < len(t0s)
+
+
+def test_mask_then_search_finds_the_second_planet():
+    """Multi-planet search on the oracle (Sect. 3.5): on a white-noise grid
+    with two injected periodic signals the first search finds the stronger,
+    and after masking its transits the second search finds the other."""
+    rng = np.random.default_rng(5)
+    dt = 2.0 / 1440.0
+    t0s = np.arange(2400) * dt
+    n = len(t0s)
+    depth = rng.normal(0, 2e-4, (1, n))
+    var = np.full((1, n), 4e-8)
+    for P, T0, amp in ((0.41, 0.13, 2.4e-3), (0.67, 0.29, 1.6e-3)):
+        ph = np.abs(((t0s - T0 + 0.5 * P) % P) - 0.5 * P)
+        depth[0, ph < 0.01] += amp
+    dlnl = depth ** 2 / (2 * var)
+    periods = np.linspace(0.3, 0.9, 400)
+    r1 = periodic.periodic_search(t0s, depth, var, dlnl, periods, dt)
+    b1 = periodic.best(r1, periods)
+    assert abs(b1["period"] - 0.41) < 0.005
+    d2, v2, l2, _ = periodic.mask_transits(t0s, depth, var, dlnl, b1["period"], b1["T0"], 0.03)
+    r2 = periodic.periodic_search(t0s, d2, v2, l2, periods, dt)
+    b2 = periodic.best(r2, periods)
+    assert abs(b2["period"] - 0.67) < 0.005
