@@ -26,4 +26,4 @@ and scipy's LAPACK routines as the only library steps:
 Nothing here shares code with the CUDA sources; the two meet only through the
 seeded inputs of ``paper_2402_06835_gb300.synth``.
 """
-from . import gp, linear, periodic, semisep  # noqa: F401
+from . import gp, linear, periodic, refine, semisep  # noqa: F401
