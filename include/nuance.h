@@ -201,6 +201,42 @@ nu_status nu_mask_transits(const double* t0s_dev, int64_t n_t0, int n_D, void* d
                            void* var_dev, void* dlnl_dev, nu_precision prec, double P,
                            double T0, double half_width, void* stream);
 
+/* Exact periodic-template fit of candidates (Sect. 2.4 read as one fit).
+ *
+ * Sect. 2.4 defines Q(P) as the SNR of a periodic transit of period P, epoch
+ * T0 and duration D.  nu_periodic_search computes it from the single events
+ * with Eq. result, which treats the transits as independent (Sect. 2.3).
+ * This call solves Eq. ls once per candidate with the design matrix
+ * X' = [X, m_P] at the factor's full covariance, where m_P(t) is the sum over
+ * all integers n of the single template (tmpl) centred at T0 + n*P (the
+ * product rounded, then the sum, in FP64; windows half-open as in
+ * nu_linear_search).  depth = last weight, var = last diagonal entry of
+ * (X'^T Sigma^-1 X')^-1, dlnl = depth^2 / (2 var) (Eq. linear_search_ll),
+ * snr = depth / sqrt(var).  The difference between snr and the periodic
+ * search's Q at the same (P, T0, D) is the cost of the independence
+ * approximation.
+ *
+ *   f             factor from nu_gp_factor
+ *   P_dev, T0_dev (n_cand) periods and epochs, e.g. the trial periods and the
+ *                 T0 output of nu_periodic_search
+ *   D_idx_dev     (n_cand) int32 index into Ds_host, e.g. its D_idx output
+ *   Ds_host       (n_D) durations, finite and > 0
+ *   tmpl, ingress_frac  as in nu_linear_search
+ *   depth_dev, var_dev, dlnl_dev, snr_dev  (n_cand) FP64 outputs
+ * A candidate with P or T0 not finite, D_idx outside [0, n_D), 2 D > P
+ * (windows would overlap), no sample in any window, or a template in the
+ * span of X gets NaN in all four outputs.  Always FP64.  One thread walks a
+ * candidate's windows; the gaps between them advance in blocks of 32
+ * samples, so a candidate costs O(samples in its windows + n/32 + 64 per
+ * window).  Enqueued on `stream`; no synchronisation.
+ * Errors: NU_EINVAL (null pointer, n_cand < 1, n_D < 1, a duration not finite
+ * and > 0, bad template), NU_ENOMEM, NU_ECUDA. */
+nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev, const double* T0_dev,
+                             const int* D_idx_dev, int64_t n_cand, const double* Ds_host,
+                             int n_D, nu_template tmpl, double ingress_frac, void* stream,
+                             double* depth_dev, double* var_dev, double* dlnl_dev,
+                             double* snr_dev);
+
 /* Periodic search without device allocation (no counterpart in the paper).
  *
  * Same inputs, outputs and results as nu_periodic_search, for callers that

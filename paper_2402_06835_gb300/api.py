@@ -58,6 +58,8 @@ def _load():
                                        P, P, P, P, P, P]
     lib.nu_mask_transits.argtypes = [P, I64, I, P, P, P, I, D, D, D, P]
     lib.nu_mask_transits.restype = I
+    lib.nu_periodic_refine.argtypes = [P, P, P, P, I64, P, I, I, D, P, P, P, P, P]
+    lib.nu_periodic_refine.restype = I
     lib.nu_periodic_search_noalloc.argtypes = lib.nu_periodic_search.argtypes
     lib.nu_periodic_search_noalloc.restype = I
     lib.nu_periodic_search_noalloc_limit.restype = ctypes.c_uint64
@@ -246,6 +248,30 @@ def nu_mask_transits(t0s, depth, var, dlnl, period, T0, half_width, precision="f
                               _stream_ptr(stream))
     _check(st, "nu_mask_transits")
     return depth, var, dlnl
+
+
+def nu_periodic_refine(factor, periods, T0, D_idx, Ds, template="box", ingress_frac=0.1,
+                       stream=None):
+    """Exact periodic-template fit of candidates (see nu_periodic_refine in the
+    header).  periods, T0 (float64) and D_idx (int32) are (n_cand,) device
+    arrays, e.g. a selection of nu_periodic_search's outputs.  Returns a dict
+    of (n_cand,) float64 tensors depth, var, dlnl, snr."""
+    periods = _dev(periods, "periods")
+    T0 = _dev(T0, "T0")
+    D_idx = _dev(D_idx, "D_idx", torch.int32)
+    n = periods.numel()
+    if T0.numel() != n or D_idx.numel() != n:
+        raise ValueError("periods, T0 and D_idx must have the same length")
+    Ds_l = [float(d) for d in (Ds.tolist() if hasattr(Ds, "tolist") else Ds)]
+    Ds_arr = (ctypes.c_double * max(1, len(Ds_l)))(*Ds_l)
+    res = {name: torch.empty(n, dtype=torch.float64, device=periods.device)
+           for name in ("depth", "var", "dlnl", "snr")}
+    st = LIB.nu_periodic_refine(factor.handle, _p(periods), _p(T0), _p(D_idx), n, Ds_arr,
+                                len(Ds_l), _TMPL[template], float(ingress_frac),
+                                _stream_ptr(stream), _p(res["depth"]), _p(res["var"]),
+                                _p(res["dlnl"]), _p(res["snr"]))
+    _check(st, "nu_periodic_refine")
+    return res
 
 
 def nu_periodic_search_noalloc(t0s, Ds, depth, var, dlnl, periods, precision="fp64",

@@ -1,0 +1,324 @@
+// nu_periodic_refine: the exact fit of a periodic transit column.
+//
+// Sect. 2.4 takes Q(P) as the SNR of a periodic transit of period P, epoch T0
+// and duration D.  nu_periodic_search obtains it from the single events with
+// Eq. result, which treats the transits as independent (Sect. 2.3).  Here the
+// design matrix is X' = [X, m_P] with m_P the template repeated at every
+// T0 + n P, and Eq. ls is solved once at the full covariance.  The Schur
+// complement of the linear search carries over unchanged (linear.cu):
+//   c = m_P^T Sigma^-1 m_P,  num = m_P^T z0,  bt = Zt^T m_P,
+//   s = c - |bt|^2,  depth = num / s,  var = 1 / s,  dlnl = num^2 / (2 s).
+// num and bt only see the samples inside the windows.  c is the D^-1
+// weighted norm of the forward solve e = L^-1 m_P, which starts from a zero
+// state at the first window and runs through every later sample: inside a
+// window with the template as input, between windows with zero input, and
+// after the last window through the future information G.
+//
+// Between windows the recursion is homogeneous, s_{i+1} = A_{i+1} s_i with
+// A_{i+1} = F_{i+1} (I - kg_i h^T), and its D^-1 weighted innovations are a
+// quadratic form in the state entering the stretch.  For aligned blocks of
+// RB samples the map (Phi_b) and the form (M_b) are tabulated once per call
+// (k_refine_blocks), so a gap costs one J x J step per block plus at most
+// 2 (RB - 1) single samples at its ends.  One thread walks one candidate's
+// windows in time order (k_refine): FP64 throughout.
+#include <cmath>
+
+#include "nu_internal.cuh"
+#include "ss.cuh"
+
+namespace nu {
+
+constexpr int RB = 32;   // samples per tabulated block
+
+__device__ __forceinline__ int64_t rf_lower_bound(const double* __restrict__ t, int64_t n,
+                                                  double x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (t[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Phi_b (row-major J x J) and M_b (packed upper) of block b = samples
+// [b RB, (b+1) RB): with s the state entering sample b RB and zero input,
+// the state leaving the block is Phi_b s and the block's sum of e_i^2 / D_i
+// is s^T M_b s.  Only blocks whose transitions all exist ((b+1) RB <= n-1).
+template <int NB>
+__global__ void __launch_bounds__(128)
+k_refine_blocks(const double* __restrict__ F, const double* __restrict__ kg,
+                const double* __restrict__ invD, int64_t n_blk, double* __restrict__ Phi,
+                double* __restrict__ Mq) {
+    constexpr int J = Dims<NB>::J;
+    constexpr int JJ = Dims<NB>::JJ;
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n_blk) return;
+    double Ph[J][J], M[JJ];
+#pragma unroll
+    for (int r = 0; r < J; ++r)
+#pragma unroll
+        for (int c = 0; c < J; ++c) Ph[r][c] = r == c ? 1.0 : 0.0;
+#pragma unroll
+    for (int a = 0; a < JJ; ++a) M[a] = 0.0;
+    const int64_t i0 = b * RB;
+    for (int64_t i = i0; i < i0 + RB; ++i) {
+        // g^T = h^T Phi: the innovation of sample i is -g^T s
+        double g[J];
+#pragma unroll
+        for (int c = 0; c < J; ++c) {
+            double v = Ph[0][c];
+#pragma unroll
+            for (int q = 1; q < NB; ++q) v += Ph[2 * q][c];
+            g[c] = v;
+        }
+        const double iD = invD[i];
+#pragma unroll
+        for (int r = 0; r < J; ++r) {
+            const double gr = g[r] * iD;
+#pragma unroll
+            for (int c = r; c < J; ++c) M[pk(r, c, J)] = fma(gr, g[c], M[pk(r, c, J)]);
+        }
+        // Phi <- F_{i+1} (Phi - kg_i g^T)
+        const double* kgi = kg + i * J;
+        const double* f = F + (i + 1) * NB * 4;
+#pragma unroll
+        for (int c = 0; c < J; ++c) {
+            double col[J], out[J];
+#pragma unroll
+            for (int r = 0; r < J; ++r) col[r] = fma(-kgi[r], g[c], Ph[r][c]);
+            apply_F<NB>(f, col, out);
+#pragma unroll
+            for (int r = 0; r < J; ++r) Ph[r][c] = out[r];
+        }
+    }
+    double* po = Phi + b * J * J;
+#pragma unroll
+    for (int r = 0; r < J; ++r)
+#pragma unroll
+        for (int c = 0; c < J; ++c) po[r * J + c] = Ph[r][c];
+    double* mo = Mq + b * JJ;
+#pragma unroll
+    for (int a = 0; a < JJ; ++a) mo[a] = M[a];
+}
+
+// One sample of the forward solve with input x: e = x - h^T s, adds e^2/D_i,
+// s <- F_{i+1} (s + kg_i e) when sample i+1 exists.  Returns e.
+template <int NB>
+__device__ __forceinline__ double rf_step(const FactorView<double>& fv, int64_t i, int64_t n,
+                                          double x, double* s, double& c2) {
+    constexpr int J = Dims<NB>::J;
+    const double e = x - hdot<NB>(s);
+    c2 = fma(e * e, fv.invD[i], c2);
+    if (i + 1 < n) {
+        double tmp[J];
+#pragma unroll
+        for (int q = 0; q < J; ++q) tmp[q] = fma(fv.kg[i * J + q], e, s[q]);
+        apply_F<NB>(fv.F + (i + 1) * NB * 4, tmp, s);
+    }
+    return e;
+}
+
+// s^T Q s for Q packed upper
+template <int J>
+__device__ __forceinline__ double rf_quad(const double* __restrict__ Q, const double* s) {
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < J; ++r) {
+        double row = Q[pk(r, r, J)] * s[r];
+#pragma unroll
+        for (int c = r + 1; c < J; ++c) row = fma(2.0 * Q[pk(r, c, J)], s[c], row);
+        acc = fma(s[r], row, acc);
+    }
+    return acc;
+}
+
+// One thread per candidate.
+template <int NB, int TMPL>
+__global__ void __launch_bounds__(128)
+k_refine(const double* __restrict__ t, int64_t n, int k, FactorView<double> fv,
+         const double* __restrict__ Phi, const double* __restrict__ Mq, int64_t n_blk,
+         const double* __restrict__ Ps, const double* __restrict__ T0s,
+         const int* __restrict__ Didx, int64_t n_cand, const double* __restrict__ Ds, int n_D,
+         double ingress_frac, double* __restrict__ out_depth, double* __restrict__ out_var,
+         double* __restrict__ out_dlnl, double* __restrict__ out_snr) {
+    constexpr int J = Dims<NB>::J;
+    constexpr int JJ = Dims<NB>::JJ;
+    const int64_t cid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cid >= n_cand) return;
+    out_depth[cid] = NAN;
+    out_var[cid] = NAN;
+    out_dlnl[cid] = NAN;
+    out_snr[cid] = NAN;
+    const int jd = Didx[cid];
+    if (jd < 0 || jd >= n_D) return;
+    const double P = Ps[cid], T0 = T0s[cid], D = Ds[jd];
+    if (!isfinite(P) || !isfinite(T0) || !(D > 0.0) || !(2.0 * D <= P)) return;
+    const double half = D * 0.5;
+    const double ramp = ingress_frac * D;
+
+    double s[J];
+#pragma unroll
+    for (int q = 0; q < J; ++q) s[q] = 0.0;
+    double c2 = 0.0, num = 0.0, bt[NU_MAX_K];
+#pragma unroll
+    for (int a = 0; a < NU_MAX_K; ++a) bt[a] = 0.0;
+
+    bool started = false;
+    int64_t cur = 0;      // the state s enters sample cur
+    int64_t p = 0;        // no window that ends before t[p] is left to visit
+    double nf = -INFINITY;
+    // Every pass either moves p forward or steps nf by one; from any p the
+    // estimate is at most two windows early, so 4 n + 16 passes suffice.
+    int64_t budget = 4 * n + 16;
+    while (p < n) {
+        if (--budget < 0) return;
+        const double ne = rint(__ddiv_rn(__dsub_rn(t[p], T0), P)) - 1.0;
+        if (!(fabs(ne) < 0x1p50)) return;          // transit index beyond exact integers
+        nf = fmax(nf, ne);
+        const double tc = __dadd_rn(T0, __dmul_rn(nf, P));
+        const int64_t hi = rf_lower_bound(t, n, __dadd_rn(tc, half));
+        if (hi <= p) {                              // window nf ends before t[p]
+            nf += 1.0;
+            continue;
+        }
+        int64_t lo = rf_lower_bound(t, n, __dsub_rn(tc, half));
+        if (lo >= hi) {                             // no sample in window nf
+            p = hi;
+            nf += 1.0;
+            continue;
+        }
+        if (lo < cur) lo = cur;                     // windows are disjoint (2 D <= P)
+        if (!started) {
+            started = true;
+            cur = lo;
+        }
+        // zero input from cur up to the window
+        while (cur < lo) {
+            if ((cur % RB) == 0 && cur + RB <= lo && cur / RB < n_blk) {
+                const int64_t b = cur / RB;
+                c2 += rf_quad<J>(Mq + b * JJ, s);
+                const double* ph = Phi + b * J * J;
+                double o[J];
+#pragma unroll
+                for (int r = 0; r < J; ++r) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int q = 0; q < J; ++q) v = fma(ph[r * J + q], s[q], v);
+                    o[r] = v;
+                }
+#pragma unroll
+                for (int q = 0; q < J; ++q) s[q] = o[q];
+                cur += RB;
+            } else {
+                rf_step<NB>(fv, cur, n, 0.0, s, c2);
+                ++cur;
+            }
+        }
+        // the window, template as input
+        for (int64_t m = lo; m < hi; ++m) {
+            double mv;
+            if (TMPL == NU_BOX) {
+                mv = -1.0;
+            } else {
+                const double dd = __ddiv_rn(__dsub_rn(half, fabs(__dsub_rn(t[m], tc))), ramp);
+                mv = -fmin(fmax(dd, 0.0), 1.0);
+            }
+            rf_step<NB>(fv, m, n, mv, s, c2);
+            num = fma(mv, fv.z0[m], num);
+            for (int a = 0; a < k; ++a) bt[a] = fma(mv, fv.Zt[m * k + a], bt[a]);
+        }
+        cur = hi;
+        p = hi;
+        nf += 1.0;
+    }
+    if (!started) return;
+    if (cur < n) c2 += rf_quad<J>(fv.G + cur * JJ, s);   // zero input after the last window
+    double bb = 0.0;
+    for (int a = 0; a < k; ++a) bb = fma(bt[a], bt[a], bb);
+    const double sch = c2 - bb;
+    if (!(sch > 0.0)) return;
+    const double dep = num / sch;
+    const double var = 1.0 / sch;
+    out_depth[cid] = dep;
+    out_var[cid] = var;
+    out_dlnl[cid] = 0.5 * num * dep;
+    out_snr[cid] = dep / sqrt(var);
+}
+
+template <int NB>
+static void launch_refine(const nu_factor* f, const double* Phi, const double* Mq,
+                          int64_t n_blk, const double* P, const double* T0, const int* Didx,
+                          int64_t n_cand, const double* Ds, int n_D, int tmpl, double ingress,
+                          double* d, double* v, double* l, double* snr, cudaStream_t st) {
+    const FactorView<double> fv{f->F, f->kg, f->invD, f->G, f->z0, f->Zt};
+    const int th = 128;
+    if (n_blk > 0)
+        k_refine_blocks<NB><<<div_up(n_blk, th), th, 0, st>>>(f->F, f->kg, f->invD, n_blk,
+                                                             (double*)Phi, (double*)Mq);
+    if (tmpl == NU_BOX)
+        k_refine<NB, NU_BOX><<<div_up(n_cand, th), th, 0, st>>>(
+            f->t, f->n, f->k, fv, Phi, Mq, n_blk, P, T0, Didx, n_cand, Ds, n_D, ingress, d, v,
+            l, snr);
+    else
+        k_refine<NB, NU_TRAPEZOID><<<div_up(n_cand, th), th, 0, st>>>(
+            f->t, f->n, f->k, fv, Phi, Mq, n_blk, P, T0, Didx, n_cand, Ds, n_D, ingress, d, v,
+            l, snr);
+}
+
+}  // namespace nu
+
+using namespace nu;
+
+extern "C" nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev,
+                                        const double* T0_dev, const int* D_idx_dev,
+                                        int64_t n_cand, const double* Ds_host, int n_D,
+                                        nu_template tmpl, double ingress_frac, void* stream,
+                                        double* depth_dev, double* var_dev, double* dlnl_dev,
+                                        double* snr_dev) {
+    if (!f) return fail(NU_EINVAL, "nu_periodic_refine: null factor");
+    if (!P_dev || !T0_dev || !D_idx_dev || !Ds_host || !depth_dev || !var_dev || !dlnl_dev ||
+        !snr_dev)
+        return fail(NU_EINVAL, "nu_periodic_refine: null array");
+    if (n_cand < 1 || n_D < 1) return fail(NU_EINVAL, "nu_periodic_refine: empty input");
+    if (n_cand > (int64_t)1 << 31)
+        return fail(NU_EINVAL, "nu_periodic_refine: more than 2^31 candidates");
+    if (tmpl != NU_BOX && tmpl != NU_TRAPEZOID)
+        return fail(NU_EINVAL, "nu_periodic_refine: unknown template %d", (int)tmpl);
+    if (tmpl == NU_TRAPEZOID && !(ingress_frac > 0.0 && ingress_frac <= 0.5))
+        return fail(NU_EINVAL, "nu_periodic_refine: ingress_frac must be in (0, 0.5]");
+    for (int j = 0; j < n_D; ++j)
+        if (!(Ds_host[j] > 0.0) || !std::isfinite(Ds_host[j]))
+            return fail(NU_EINVAL, "nu_periodic_refine: durations must be finite and > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int J = 2 * f->nb, JJ = J * (J + 1) / 2;
+    const int64_t n_blk = (f->n - 1) / RB;
+    const size_t bytes = (n_D + n_blk * (int64_t)(J * J + JJ)) * sizeof(double);
+    pool_keep_memory();
+    double* mem = nullptr;
+    cudaError_t e = cudaMallocAsync(&mem, bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_refine: cudaMallocAsync");
+    double* Ds_dev = mem;
+    double* Phi = mem + n_D;
+    double* Mq = Phi + n_blk * J * J;
+    e = cudaMemcpyAsync(Ds_dev, Ds_host, n_D * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_refine: copy");
+    if (f->stream != st) {
+        cudaEvent_t ev;
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        cudaEventRecord(ev, f->stream);
+        cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    switch (f->nb) {
+        case 1: launch_refine<1>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+        case 2: launch_refine<2>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+        case 3: launch_refine<3>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+        default: launch_refine<4>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+    }
+    count_launches(n_blk > 0 ? 2 : 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_refine: launch");
+    e = cudaFreeAsync(mem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_refine: cudaFreeAsync");
+    return NU_OK;
+}
