@@ -48,9 +48,9 @@ typedef enum {
 
 typedef enum {
     NU_FP64 = 0,      /* every step in IEEE binary64                           */
-    NU_MIXED = 1      /* FP64 factor and prefix bases; FP32 window recursion,
-                         window sums and GLS with compensated accumulation;
-                         FP32 fold with FP64 epoch arithmetic                   */
+    NU_MIXED = 1      /* FP64 factor; FP32 window recursion, window sums and
+                         GLS with compensated accumulation; FP32 fold with
+                         FP64 epoch arithmetic                                  */
 } nu_precision;
 
 typedef enum {
