@@ -228,11 +228,15 @@ FactorPlan plan_factor(const int64_t* n_per_seg, const Blocks* blocks, int n_seg
     p.k = k;
     p.n_seg = n_seg;
     std::vector<int64_t> nc(n_seg);
+    int64_t n_all = 0;
+    for (int g = 0; g < n_seg; ++g) n_all += n_per_seg[g];
+    p.B = scan_chunk_len(n_all);
+    p.G = scan_group(p.B);
     p.s_off.assign(n_seg + 1, 0);
     p.segs.resize(n_seg);
     p.blocks.assign(blocks, blocks + n_seg);
     for (int g = 0; g < n_seg; ++g) {
-        nc[g] = (n_per_seg[g] + SCAN_B - 1) / SCAN_B;
+        nc[g] = (n_per_seg[g] + p.B - 1) / p.B;
         SegInfo& sg = p.segs[g];
         sg.s_off = p.n_total;
         sg.n = n_per_seg[g];
@@ -247,9 +251,9 @@ FactorPlan plan_factor(const int64_t* n_per_seg, const Blocks* blocks, int n_seg
         p.n_chunks += nc[g];
         p.s_off[g + 1] = p.n_total;
     }
-    p.shape = build_scan_shape(nc.data(), n_seg, SCAN_G, SCAN_TOP, nullptr);
+    p.shape = build_scan_shape(nc.data(), n_seg, p.G, SCAN_TOP, nullptr);
     p.index.assign(p.shape.n_index, 0);
-    build_scan_shape(nc.data(), n_seg, SCAN_G, SCAN_TOP, p.index.data());
+    build_scan_shape(nc.data(), n_seg, p.G, SCAN_TOP, p.index.data());
     p.chunk_seg.resize(p.n_chunks);
     int64_t c = 0;
     for (int g = 0; g < n_seg; ++g)
@@ -328,10 +332,10 @@ static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* w
     k_transitions<NB><<<nblk, 256, 0, st>>>(b.t, n, s_off, p.n_seg, blocks, b.F, b.dstat);
     ++launched;
     // 1. pivots and gains
-    RiccatiOp<NB> ric{segs, chunk_seg, b.F, dv, SCAN_B, b.kg, b.invD, Dpiv, b.dstat};
+    RiccatiOp<NB> ric{segs, chunk_seg, b.F, dv, p.B, b.kg, b.invD, Dpiv, b.dstat};
     launched += run_scan(ric, p.shape, idx, scan_ws, st);
     // 2. forward solves of X and y, cross products
-    ForwardOp<NB> fw{segs, chunk_seg, b.F, b.kg, b.invD, X, ldx, b.t, y, k, SCAN_B, b.work,
+    ForwardOp<NB> fw{segs, chunk_seg, b.F, b.kg, b.invD, X, ldx, b.t, y, k, p.B, b.work,
                      partial};
     launched += run_scan(fw, p.shape, idx, scan_ws, st);
     k_reduce_cross<<<p.n_seg * nr * nr, 128, 0, st>>>(partial, segs, nr, cross);
@@ -343,10 +347,10 @@ static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* w
     }
     k_rhs<<<nblk, 256, 0, st>>>(n, k, s_off, p.n_seg, b.work, b.invD, wR, Dpiv, U, chi, logD);
     ++launched;
-    BackwardOp<NB> bw{segs, chunk_seg, b.F, b.kg, U, nr, k, SCAN_B, b.z0, b.Zt};
+    BackwardOp<NB> bw{segs, chunk_seg, b.F, b.kg, U, nr, k, p.B, b.z0, b.Zt};
     launched += run_scan(bw, p.shape, idx, scan_ws, st);
     // 4. future information
-    FutureOp<NB> fu{segs, chunk_seg, b.F, b.kg, b.invD, SCAN_B, b.G};
+    FutureOp<NB> fu{segs, chunk_seg, b.F, b.kg, b.invD, p.B, b.G};
     launched += run_scan(fu, p.shape, idx, scan_ws, st);
     k_seg_scalars<<<p.n_seg, 256, 0, st>>>(chi, logD, segs, b.scal);
     ++launched;

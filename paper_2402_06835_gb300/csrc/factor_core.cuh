@@ -9,10 +9,21 @@
 
 namespace nu {
 
-// chunk length, group size and top-level count of the scans
-constexpr int SCAN_B = 32;
-constexpr int SCAN_G = 8;
+// Chunk length and group size of the scans, chosen per factor by the number
+// of samples.  The scan's sequential depth is about 2 B per-sample steps plus
+// 2 G element operations per tree level; the GPU runs 608 sub-partitions x
+// 32 lanes of such chains at once.  While the level-0 chunks fit in about two
+// such waves, short chunks and small groups shorten the chain (on a 19 440-
+// sample curve B = 8, G = 4 takes the factor from 2.63 to 1.65 ms); a large
+// batch has chunks to spare, and long chunks keep the tree's extra work and
+// its element memory small.
 constexpr int SCAN_TOP = 16;
+inline int scan_chunk_len(int64_t n_total) {
+    int B = 8;
+    while (B < 32 && n_total > (int64_t)B * 2 * 608 * 32) B *= 2;
+    return B;
+}
+inline int scan_group(int B) { return B <= 8 ? 4 : 8; }
 
 // Device arrays of a factor, all indexed by packed sample.
 struct FactorBuffers {
@@ -41,6 +52,8 @@ struct FactorPlan {
     int n_seg;
     int64_t n_total;
     int64_t n_chunks;
+    int B;                           // chunk length of the scans
+    int G;                           // group size of the scan tree
     ScanShape shape;
     std::vector<int64_t> index;      // scan index arrays
     std::vector<int> chunk_seg;      // segment of each chunk
