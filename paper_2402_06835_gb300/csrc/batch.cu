@@ -226,13 +226,14 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     // the enqueue of everything after setup (graph body)
+    cudaStream_t side = thread_side_stream();
     auto enqueue = [&](int grid, int threads, int64_t nP_run, int n_run,
                        cudaStream_t st) -> int {
         int l = 0;
         k_init_dstat<<<div_up(n_lc, 128), 128, 0, st>>>(fb.dstat, s_off_dev, n_lc);
         ++l;
         int lf = 0;
-        launch_factor(plan, fb, ws, diag_var_dev, nullptr, 0, y_dev, st, &lf);
+        launch_factor(plan, fb, ws, diag_var_dev, nullptr, 0, y_dev, st, side, &lf);
         l += lf;
         if (fp64) {
             FactorView<double> fv{fb.F, fb.kg, fb.invD, fb.G, fb.z0, fb.Zt};

@@ -213,12 +213,12 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 }
 
 // ------------------------------------------------------------------ plan
+// workspace of the scans that run one after another on the main stream
 template <int NB>
 static size_t scan_workspace(const ScanShape& sh) {
     size_t m = scan_bytes<RiccatiOp<NB>>(sh);
     m = std::max(m, scan_bytes<ForwardOp<NB>>(sh));
     m = std::max(m, scan_bytes<BackwardOp<NB>>(sh));
-    m = std::max(m, scan_bytes<FutureOp<NB>>(sh));
     return m;
 }
 
@@ -258,17 +258,18 @@ FactorPlan plan_factor(const int64_t* n_per_seg, const Blocks* blocks, int n_seg
     int64_t c = 0;
     for (int g = 0; g < n_seg; ++g)
         for (int64_t q = 0; q < nc[g]; ++q) p.chunk_seg[c++] = g;
-    size_t scan = 0;
+    size_t scan = 0, scan_fu = 0;
     switch (p.nb) {
-        case 1: scan = scan_workspace<1>(p.shape); break;
-        case 2: scan = scan_workspace<2>(p.shape); break;
-        case 3: scan = scan_workspace<3>(p.shape); break;
-        default: scan = scan_workspace<4>(p.shape); break;
+        case 1: scan = scan_workspace<1>(p.shape); scan_fu = scan_bytes<FutureOp<1>>(p.shape); break;
+        case 2: scan = scan_workspace<2>(p.shape); scan_fu = scan_bytes<FutureOp<2>>(p.shape); break;
+        case 3: scan = scan_workspace<3>(p.shape); scan_fu = scan_bytes<FutureOp<3>>(p.shape); break;
+        default: scan = scan_workspace<4>(p.shape); scan_fu = scan_bytes<FutureOp<4>>(p.shape); break;
     }
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const int nr = k + 1;
     size_t off = 0;
     p.off_scan = off;       off += al(scan);
+    p.off_scan_fu = off;    off += al(scan_fu);
     p.off_partial = off;    off += al((size_t)p.n_chunks * NRMAX * NRMAX * 8);
     p.off_idx = off;        off += al(p.index.size() * 8);
     p.off_chunk_seg = off;  off += al(p.chunk_seg.size() * 4);
@@ -308,7 +309,7 @@ nu_status upload_factor_plan(const FactorPlan& p, char* ws, cudaStream_t st) {
 template <int NB>
 static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* ws,
                             const double* dv, const double* X, int64_t ldx, const double* y,
-                            cudaStream_t st) {
+                            cudaStream_t st, cudaStream_t side) {
     constexpr int J = Dims<NB>::J;
     constexpr int JJ = Dims<NB>::JJ;
     const int64_t n = p.n_total;
@@ -334,6 +335,21 @@ static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* w
     // 1. pivots and gains
     RiccatiOp<NB> ric{segs, chunk_seg, b.F, dv, p.B, b.kg, b.invD, Dpiv, b.dstat};
     launched += run_scan(ric, p.shape, idx, scan_ws, st);
+    // 4. future information: needs only the pivots and gains, so it runs on the
+    //    side stream (when there is one) beside steps 2 and 3
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool forked = false;
+    if (side && side != st &&
+        cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(ev_fork, st) == cudaSuccess &&
+        cudaStreamWaitEvent(side, ev_fork, 0) == cudaSuccess)
+        forked = true;
+    FutureOp<NB> fu{segs, chunk_seg, b.F, b.kg, b.invD, p.B, b.G};
+    if (forked) {
+        launched += run_scan(fu, p.shape, idx, ws + p.off_scan_fu, side);
+        if (cudaEventRecord(ev_join, side) != cudaSuccess) forked = false;
+    }
     // 2. forward solves of X and y, cross products
     ForwardOp<NB> fw{segs, chunk_seg, b.F, b.kg, b.invD, X, ldx, b.t, y, k, p.B, b.work,
                      partial};
@@ -349,9 +365,13 @@ static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* w
     ++launched;
     BackwardOp<NB> bw{segs, chunk_seg, b.F, b.kg, U, nr, k, p.B, b.z0, b.Zt};
     launched += run_scan(bw, p.shape, idx, scan_ws, st);
-    // 4. future information
-    FutureOp<NB> fu{segs, chunk_seg, b.F, b.kg, b.invD, p.B, b.G};
-    launched += run_scan(fu, p.shape, idx, scan_ws, st);
+    if (forked) {
+        cudaStreamWaitEvent(st, ev_join, 0);
+    } else {
+        launched += run_scan(fu, p.shape, idx, ws + p.off_scan_fu, st);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     k_seg_scalars<<<p.n_seg, 256, 0, st>>>(chi, logD, segs, b.scal);
     ++launched;
     if (b.F32) {
@@ -370,19 +390,29 @@ static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* w
 
 nu_status launch_factor(const FactorPlan& p, const FactorBuffers& b, char* ws,
                         const double* dv, const double* X, int64_t ldx, const double* y,
-                        cudaStream_t st, int* launched) {
+                        cudaStream_t st, cudaStream_t side, int* launched) {
     int l = 0;
     switch (p.nb) {
-        case 1: l = launch_factor_nb<1>(p, b, ws, dv, X, ldx, y, st); break;
-        case 2: l = launch_factor_nb<2>(p, b, ws, dv, X, ldx, y, st); break;
-        case 3: l = launch_factor_nb<3>(p, b, ws, dv, X, ldx, y, st); break;
-        default: l = launch_factor_nb<4>(p, b, ws, dv, X, ldx, y, st); break;
+        case 1: l = launch_factor_nb<1>(p, b, ws, dv, X, ldx, y, st, side); break;
+        case 2: l = launch_factor_nb<2>(p, b, ws, dv, X, ldx, y, st, side); break;
+        case 3: l = launch_factor_nb<3>(p, b, ws, dv, X, ldx, y, st, side); break;
+        default: l = launch_factor_nb<4>(p, b, ws, dv, X, ldx, y, st, side); break;
     }
     if (launched) *launched += l;
     count_launches(l);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "factor launch");
     return NU_OK;
+}
+
+cudaStream_t thread_side_stream() {
+    constexpr int MAXDEV = 64;
+    thread_local cudaStream_t side[MAXDEV] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return nullptr;
+    if (!side[dev] && cudaStreamCreateWithFlags(&side[dev], cudaStreamNonBlocking) != cudaSuccess)
+        side[dev] = nullptr;
+    return side[dev];
 }
 
 }  // namespace nu
@@ -466,7 +496,8 @@ extern "C" nu_status nu_gp_factor(const double* t_dev, const double* diag_var_de
     if (s == NU_OK) {
         FactorBuffers b{f->t, f->F, f->kg, f->invD, f->G, f->z0, f->Zt, f->work, f->scal,
                         f->dstat, f->F32, f->kg32, f->invD32, f->G32, f->z032, f->Zt32};
-        s = launch_factor(plan, b, ws, diag_var_dev, X_dev, n, y_dev, st, nullptr);
+        s = launch_factor(plan, b, ws, diag_var_dev, X_dev, n, y_dev, st,
+                          thread_side_stream(), nullptr);
     }
     cudaFreeAsync(ws, st);
     if (s != NU_OK) {

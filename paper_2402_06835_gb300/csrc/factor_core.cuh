@@ -61,7 +61,7 @@ struct FactorPlan {
     std::vector<SegInfo> segs;
     std::vector<Blocks> blocks;
     // workspace layout (bytes)
-    size_t off_scan, off_partial, off_idx, off_chunk_seg, off_segs, off_blocks, off_s_off,
+    size_t off_scan, off_scan_fu, off_partial, off_idx, off_chunk_seg, off_segs, off_blocks, off_s_off,
         off_cross, off_wR, off_Dpiv, off_U, off_chi, off_logD, bytes;
 };
 
@@ -75,8 +75,16 @@ nu_status upload_factor_plan(const FactorPlan& p, char* ws, cudaStream_t st);
 // Enqueue every kernel of the factor (no host synchronisation, no
 // allocation): safe to capture in a CUDA graph.  X may be null (then the
 // columns are [1, t] up to k), with leading dimension ldx otherwise.
+// When `side` is a stream other than st, the future-information scan (which
+// needs only the pivots and gains) runs on it concurrently with the forward
+// and backward solves, forked from and joined back into st by events; the
+// caller must not use `side` concurrently for anything else.
 nu_status launch_factor(const FactorPlan& p, const FactorBuffers& b, char* ws,
                         const double* diag_var, const double* X, int64_t ldx,
-                        const double* y, cudaStream_t st, int* launched);
+                        const double* y, cudaStream_t st, cudaStream_t side, int* launched);
+
+// A non-blocking stream private to the calling thread and current device,
+// created on first use and kept for the thread's lifetime (null on failure).
+cudaStream_t thread_side_stream();
 
 }  // namespace nu
