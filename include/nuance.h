@@ -201,6 +201,25 @@ nu_status nu_mask_transits(const double* t0s_dev, int64_t n_t0, int n_D, void* d
                            void* var_dev, void* dlnl_dev, nu_precision prec, double P,
                            double T0, double half_width, void* stream);
 
+/* Rotation-alias period exclusion (Sect. 3, the comparison set-up).
+ *
+ * Removes from a period grid the periods near whole multiples of the stellar
+ * rotation period P_star: with dP = P / P_star, a period is dropped when
+ * |dP - ceil(dP)| < tol (the printed criterion, tol = 0.02 in the paper), or,
+ * with symmetric != 0, when |dP - rint(dP)| < tol (the wording "less than 2 %
+ * from an integer", which also drops periods just above a multiple).  Each
+ * operation is rounded once in FP64.  Periods that are not finite are kept.
+ *   periods_dev  (n_P) input grid
+ *   kept_dev     (n_P capacity) receives the kept periods in input order;
+ *                must not overlap periods_dev
+ *   n_kept_dev   one int64 in device memory: the number of kept periods
+ * Enqueued on `stream`; no synchronisation.
+ * Errors: NU_EINVAL (null pointer, n_P < 1, P_star not finite and > 0, tol
+ * not finite and >= 0, kept_dev == periods_dev), NU_ECUDA. */
+nu_status nu_rotation_alias_filter(const double* periods_dev, int64_t n_P, double P_star,
+                                   double tol, int symmetric, double* kept_dev,
+                                   int64_t* n_kept_dev, void* stream);
+
 /* Exact periodic-template fit of candidates (Sect. 2.4 read as one fit).
  *
  * Sect. 2.4 defines Q(P) as the SNR of a periodic transit of period P, epoch

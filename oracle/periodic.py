@@ -179,3 +179,18 @@ def mask_transits(t0s, depth, var, dlnl, P, T0, half_width):
         b[:, m] = np.nan
         out.append(b)
     return out[0], out[1], out[2], m
+
+
+def rotation_alias_keep(periods, P_star, tol=0.02, symmetric=False):
+    """Sect. 3's exclusion of the rotation period's aliases from the grid.
+
+    With dP = P / P_star a period is removed when |dP - ceil(dP)| < tol (the
+    printed criterion), or, symmetric, when |dP - rint(dP)| < tol (the
+    wording "less than 2 % from an integer").  Returns the boolean keep mask.
+    """
+    P = np.asarray(periods, dtype=np.float64)
+    dP = P / P_star
+    ref = np.rint(dP) if symmetric else np.ceil(dP)
+    with np.errstate(invalid="ignore"):
+        drop = np.abs(dP - ref) < tol
+    return ~drop

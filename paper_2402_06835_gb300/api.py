@@ -60,6 +60,8 @@ def _load():
     lib.nu_mask_transits.restype = I
     lib.nu_periodic_refine.argtypes = [P, P, P, P, I64, P, I, I, D, P, P, P, P, P]
     lib.nu_periodic_refine.restype = I
+    lib.nu_rotation_alias_filter.argtypes = [P, I64, D, D, I, P, P, P]
+    lib.nu_rotation_alias_filter.restype = I
     lib.nu_periodic_search_noalloc.argtypes = lib.nu_periodic_search.argtypes
     lib.nu_periodic_search_noalloc.restype = I
     lib.nu_periodic_search_noalloc_limit.restype = ctypes.c_uint64
@@ -248,6 +250,20 @@ def nu_mask_transits(t0s, depth, var, dlnl, period, T0, half_width, precision="f
                               _stream_ptr(stream))
     _check(st, "nu_mask_transits")
     return depth, var, dlnl
+
+
+def nu_rotation_alias_filter(periods, P_star, tol=0.02, symmetric=False, stream=None):
+    """Period grid without the rotation period's aliases (see
+    nu_rotation_alias_filter in the header).  Returns the kept periods (a new
+    device tensor; reading its length synchronises the stream)."""
+    periods = _dev(periods, "periods")
+    kept = torch.empty_like(periods)
+    n = torch.empty(1, dtype=torch.int64, device=periods.device)
+    st = LIB.nu_rotation_alias_filter(_p(periods), periods.numel(), float(P_star), float(tol),
+                                      1 if symmetric else 0, _p(kept), _p(n),
+                                      _stream_ptr(stream))
+    _check(st, "nu_rotation_alias_filter")
+    return kept[: int(n.item())]
 
 
 def nu_periodic_refine(factor, periods, T0, D_idx, Ds, template="box", ingress_frac=0.1,

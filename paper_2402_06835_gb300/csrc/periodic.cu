@@ -2131,6 +2131,68 @@ extern "C" nu_status nu_mask_transits(const double* t0s_dev, int64_t n_t0, int n
     return NU_OK;
 }
 
+// ------------------------------------------------ rotation-alias periods
+// One block walks the grid in tiles of its threads; a period is dropped when
+// dP = P / P_star is within tol below its ceiling (or, symmetric, of its
+// nearest integer), each operation rounded once; the kept periods are written
+// in input order (warp ballots, then the warps' counts in shared memory).
+__global__ void __launch_bounds__(1024)
+k_alias_filter(const double* __restrict__ P, int64_t n_P, double P_star, double tol,
+               int symmetric, double* __restrict__ kept, int64_t* __restrict__ n_kept) {
+    __shared__ int warp_cnt[32];
+    __shared__ int64_t base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n_warps = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < n_P; t0 += blockDim.x) {
+        const int64_t i = t0 + threadIdx.x;
+        bool keep = false;
+        double p = 0.0;
+        if (i < n_P) {
+            p = P[i];
+            const double dP = __ddiv_rn(p, P_star);
+            const double ref = symmetric ? rint(dP) : ceil(dP);
+            keep = !(fabs(__dsub_rn(dP, ref)) < tol);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) warp_cnt[wid] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < n_warps; ++w) {
+            const int c = warp_cnt[w];
+            if (w < wid) before += c;
+            total += c;
+        }
+        if (keep) kept[base + before + __popc(m & ((1u << lane) - 1u))] = p;
+        __syncthreads();
+        if (threadIdx.x == 0) base += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_kept = base;
+}
+
+extern "C" nu_status nu_rotation_alias_filter(const double* periods_dev, int64_t n_P,
+                                              double P_star, double tol, int symmetric,
+                                              double* kept_dev, int64_t* n_kept_dev,
+                                              void* stream) {
+    if (!periods_dev || !kept_dev || !n_kept_dev)
+        return fail(NU_EINVAL, "nu_rotation_alias_filter: null array");
+    if (n_P < 1) return fail(NU_EINVAL, "nu_rotation_alias_filter: n_P must be >= 1");
+    if (!(P_star > 0.0) || !std::isfinite(P_star) || !(tol >= 0.0) || !std::isfinite(tol))
+        return fail(NU_EINVAL, "nu_rotation_alias_filter: P_star must be finite and > 0, "
+                               "tol finite and >= 0");
+    if (periods_dev == kept_dev)
+        return fail(NU_EINVAL, "nu_rotation_alias_filter: kept must not alias periods");
+    cudaStream_t st = (cudaStream_t)stream;
+    k_alias_filter<<<1, 1024, 0, st>>>(periods_dev, n_P, P_star, tol, symmetric ? 1 : 0,
+                                       kept_dev, n_kept_dev);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "nu_rotation_alias_filter: launch");
+    return NU_OK;
+}
+
 // ------------------------------------------------ allocation-free variant
 // nu_periodic_search_noalloc runs the same kernels as nu_periodic_search but
 // takes its scratch (epoch records, bucket table, slot table, flag) from the

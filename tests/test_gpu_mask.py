@@ -120,3 +120,30 @@ def test_per_sector_factors_with_one_fold():
     print(f"per-sector factors, one fold: lnP err {wl:.2e}, Q err {wq:.2e}, ties {differ}, "
           f"best {best['period']:.4f}")
     assert abs(best["period"] - P) < 0.01
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_rotation_alias_filter_is_bit_exact(symmetric):
+    rng = np.random.default_rng(17)
+    P_star = 1.37
+    P = np.concatenate([rng.uniform(0.2, 13.5, 20000),
+                        P_star * np.arange(1, 10),                 # exact multiples
+                        P_star * np.arange(1, 10) * (1 - 0.02),    # at the edge
+                        P_star * np.arange(1, 10) * (1 + 0.0199),
+                        [np.nan, np.inf, -1.0]])
+    got = api.nu_rotation_alias_filter(cu(P), P_star, 0.02, symmetric=symmetric).cpu().numpy()
+    want = P[periodic.rotation_alias_keep(P, P_star, 0.02, symmetric)]
+    assert got.shape == want.shape
+    assert np.array_equal(got, want, equal_nan=True)
+    assert 0 < len(want) < len(P)
+
+
+def test_rotation_alias_filter_edge_cases():
+    # everything dropped, a single period, bad arguments
+    P = cu(2.0 * np.arange(1, 50))
+    assert api.nu_rotation_alias_filter(P, 2.0).numel() == 0
+    assert api.nu_rotation_alias_filter(cu([0.7]), 2.0).cpu().numpy().tolist() == [0.7]
+    with pytest.raises(api.NuanceError):
+        api.nu_rotation_alias_filter(P, 0.0)
+    with pytest.raises(api.NuanceError):
+        api.nu_rotation_alias_filter(P, 2.0, tol=float("nan"))

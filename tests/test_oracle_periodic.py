@@ -268,3 +268,18 @@ def test_mask_then_search_finds_the_second_planet():
     r2 = periodic.periodic_search(t0s, d2, v2, l2, periods, dt)
     b2 = periodic.best(r2, periods)
     assert abs(b2["period"] - 0.67) < 0.005
+
+
+def test_rotation_alias_keep_worked_cases():
+    """Sect. 3's criterion |dP - ceil(dP)| < 0.02 with dP = P / P_star, on cases
+    worked by hand for P_star = 2 d (dP and the distance to the ceiling)."""
+    P = np.array([1.99, 2.01, 3.97, 1.0, 4.0, 4.03, 0.5, 6.1, np.nan])
+    # dP:        0.995 1.005 1.985  0.5  2.0  2.015 0.25 3.05
+    # to ceil:   0.005 0.995 0.015  0.5  0    0.985 0.75 0.95
+    want = np.array([False, True, False, True, False, True, True, True, True])
+    assert np.array_equal(periodic.rotation_alias_keep(P, 2.0), want)
+    # the wording's two-sided reading also drops 2.01 and 4.03 (nearest integer)
+    want_sym = np.array([False, False, False, True, False, False, True, True, True])
+    assert np.array_equal(periodic.rotation_alias_keep(P, 2.0, symmetric=True), want_sym)
+    # the inequality is strict: tol = 0 keeps every period, exact multiples too
+    assert periodic.rotation_alias_keep(P, 2.0, tol=0.0).all()
