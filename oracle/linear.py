@@ -18,7 +18,9 @@ the box template is -1 inside the window and 0 outside, so that a dip has a
 positive depth; a sample belongs to the window when t0 - D/2 <= t < t0 + D/2
 (half-open, evaluated in FP64 exactly as written); the trapezoid (not in the
 paper) has total width D, linear ingress and egress of width ingress_frac*D
-and a flat bottom of -1.
+and a flat bottom of -1; the limb-darkened template (Sect. 4.4 names
+limb-darkened transits as a base model to come) is the small-planet,
+central-transit profile under the quadratic law on the same window.
 
 How it is evaluated: Sigma is formed densely (``oracle.gp.covariance``) and
 factored once, Sigma = C C^T (LAPACK Cholesky).  Every column is whitened by
@@ -57,11 +59,31 @@ def trapezoid_template(t, t0, D, ingress_frac):
     return np.where(inside, -np.clip(depth, 0.0, 1.0), 0.0)
 
 
-def template(t, t0, D, kind="box", ingress_frac=0.1):
+def limb_quad_template(t, t0, D, u1, u2):
+    """Limb-darkened transit as base model (the prospect of Sect. 4.4).
+
+    Small-planet limit of a central transit (Mandel & Agol 2002, ApJ 580,
+    L171, Sect. 5): the planet at projected distance r = 2 (t - t0) / D stellar
+    radii blocks flux in proportion to the local intensity, here the quadratic
+    law I(mu) = 1 - u1 (1 - mu) - u2 (1 - mu)^2 with mu = sqrt(1 - r^2).  The
+    template is -I on the box's window (-1 at the centre), 0 outside.
+    """
+    t = np.asarray(t, dtype=np.float64)
+    inside = (t >= t0 - D * 0.5) & (t < t0 + D * 0.5)
+    r = np.where(inside, 2.0 * (t - t0) / D, 0.0)
+    mu = np.sqrt(1.0 - r * r)
+    x = 1.0 - mu
+    intensity = 1.0 - u1 * x - u2 * x * x
+    return np.where(inside, -intensity, 0.0)
+
+
+def template(t, t0, D, kind="box", ingress_frac=0.1, ld=(0.4, 0.25)):
     if kind == "box":
         return box_template(t, t0, D)
     if kind == "trapezoid":
         return trapezoid_template(t, t0, D, ingress_frac)
+    if kind == "limb_quad":
+        return limb_quad_template(t, t0, D, ld[0], ld[1])
     raise ValueError(kind)
 
 
@@ -144,7 +166,7 @@ def _ols_qr(A, y):
 
 
 def linear_search(t, y, diag_var, terms, X, t0s, Ds, kind="box",
-                  ingress_frac=0.1, chunk=256, model=None):
+                  ingress_frac=0.1, chunk=256, model=None, ld=(0.4, 0.25)):
     """Sect. 2.2 linear search on the (t0s x Ds) grid.
 
     Returns dict with depth, var, dlnl of shape (n_D, n_t0) (duration-major),
@@ -159,7 +181,7 @@ def linear_search(t, y, diag_var, terms, X, t0s, Ds, kind="box",
     for j, D in enumerate(Ds):
         for s in range(0, len(t0s), chunk):
             sl = slice(s, min(s + chunk, len(t0s)))
-            M = np.stack([template(model.t, t0, D, kind, ingress_frac)
+            M = np.stack([template(model.t, t0, D, kind, ingress_frac, ld)
                           for t0 in t0s[sl]], axis=1)
             d, v, l = model.fit_templates(M)
             out["depth"][j, sl] = d
@@ -170,8 +192,9 @@ def linear_search(t, y, diag_var, terms, X, t0s, Ds, kind="box",
     return out
 
 
-def sampled_linear_search(model, t0s, Ds, pairs, kind="box", ingress_frac=0.1):
+def sampled_linear_search(model, t0s, Ds, pairs, kind="box", ingress_frac=0.1,
+                          ld=(0.4, 0.25)):
     """Templates for a list of (duration index, t0 index) pairs only."""
-    M = np.stack([template(model.t, t0s[i], Ds[j], kind, ingress_frac)
+    M = np.stack([template(model.t, t0s[i], Ds[j], kind, ingress_frac, ld)
                   for (j, i) in pairs], axis=1)
     return model.fit_templates(M)

@@ -13,9 +13,9 @@ fold's measures the independence approximation.
 Definitions (readings listed with the design):
 
 * m_P(t) = sum over all integers n of m(t; T0 + n P, D), where m is the
-  single-transit template of ``oracle.linear.template`` (box or trapezoid,
-  the same half-open window) and each centre T0 + n P is evaluated in FP64
-  as written (the product n P rounded, then the sum);
+  single-transit template of ``oracle.linear.template`` (box, trapezoid or
+  limb-darkened, the same half-open window) and each centre T0 + n P is
+  evaluated in FP64 as written (the product n P rounded, then the sum);
 * the windows must not overlap: a candidate needs 0 < 2 D <= P; a candidate
   that is not finite, breaks that, or whose template has no non-zero sample,
   gets NaN for depth, var, dlnl and snr;
@@ -40,7 +40,7 @@ def valid_candidate(P, T0, D):
             and D > 0.0 and 2.0 * D <= P)
 
 
-def periodic_template(t, P, T0, D, kind="box", ingress_frac=0.1):
+def periodic_template(t, P, T0, D, kind="box", ingress_frac=0.1, ld=(0.4, 0.25)):
     """m_P(t): the single template repeated at every T0 + n P.
 
     Every n whose window can reach [t_min, t_max] is summed; the range is
@@ -54,11 +54,12 @@ def periodic_template(t, P, T0, D, kind="box", ingress_frac=0.1):
     n_hi = math.ceil((t[-1] - T0 + D) / P) + 1
     m = np.zeros_like(t)
     for n in range(n_lo, n_hi + 1):
-        m += template(t, T0 + float(n) * P, D, kind, ingress_frac)
+        m += template(t, T0 + float(n) * P, D, kind, ingress_frac, ld)
     return m
 
 
-def refine(model, candidates, kind="box", ingress_frac=0.1, X=None, y=None):
+def refine(model, candidates, kind="box", ingress_frac=0.1, X=None, y=None,
+           ld=(0.4, 0.25)):
     """Eq. ls with the periodic template for each (P, T0, D) of candidates.
 
     model is an ``oracle.linear.DenseModel`` or an ``oracle.semisep.Semisep``
@@ -71,8 +72,8 @@ def refine(model, candidates, kind="box", ingress_frac=0.1, X=None, y=None):
     ok = [i for i, (P, T0, D) in enumerate(cands) if valid_candidate(P, T0, D)]
     if not ok:
         return out
-    M = np.stack([periodic_template(model.t, *cands[i], kind, ingress_frac) for i in ok],
-                 axis=1)
+    M = np.stack([periodic_template(model.t, *cands[i], kind, ingress_frac, ld)
+                  for i in ok], axis=1)
     if X is None:
         d, v, l = model.fit_templates(M)
     else:

@@ -144,11 +144,11 @@ class Semisep:
 
 
 def sampled_linear_search(t, y, diag_var, terms, X, Ds, pairs, kind="box",
-                          ingress_frac=0.1, model=None):
+                          ingress_frac=0.1, model=None, ld=(0.4, 0.25)):
     """Templates for (duration index, t0 index) pairs with t0s = t."""
     if model is None:
         model = Semisep(t, diag_var, terms)
-    M = np.stack([template(model.t, t[i], Ds[j], kind, ingress_frac) for (j, i) in pairs],
+    M = np.stack([template(model.t, t[i], Ds[j], kind, ingress_frac, ld) for (j, i) in pairs],
                  axis=1)
     d, v, l = model.fit_templates(X, np.asarray(y, dtype=np.float64), M)
     return d, v, l, model

@@ -59,7 +59,7 @@ def _brute_force(Sigma, X, y, m):
     return float(w[-1]), float(Gi[-1, -1]), float(0.5 * (chi2_0 - chi2))
 
 
-@pytest.mark.parametrize("kind", ["box", "trapezoid"])
+@pytest.mark.parametrize("kind", ["box", "trapezoid", "limb_quad"])
 def test_p1_brute_force_tiny(kind):
     lc = synth.small_curve(n=48, seed=3, p_rot=0.2)
     t, y, dv = lc.t, lc.y, lc.diag_var
@@ -143,7 +143,7 @@ def test_white_noise_logdet_and_null():
 
 
 # ---------------------------------------------------------- noiseless recovery
-@pytest.mark.parametrize("kind", ["box", "trapezoid"])
+@pytest.mark.parametrize("kind", ["box", "trapezoid", "limb_quad"])
 def test_p3_noiseless_recovery(kind):
     lc = synth.small_curve(n=240, seed=5, gap=30)
     t = lc.t
@@ -200,6 +200,27 @@ def test_trapezoid_shape():
     # ramp: halfway through ingress the template is -1/2
     assert m[np.argmin(np.abs(t + 0.4))] == pytest.approx(-0.5, abs=1e-9)
     assert np.all(m[np.abs(t) <= 0.3] == -1.0)
+
+
+def test_limb_quad_shape_and_integral():
+    """Centre -1, limb -(1 - u1 - u2), zero outside; no darkening is the box;
+    and the area of the dip is the closed form of the quadratic law's chord
+    integral, int_{-1}^{1} I(sqrt(1 - x^2)) dx = 2 - u1 (2 - pi/2) - u2 (10/3 - pi)."""
+    u1, u2 = 0.45, 0.2
+    D = 1.0
+    t = (np.arange(2_000_001) - 1_000_000) * 1e-6          # step 1e-6, t0 = 0
+    m = linear.limb_quad_template(t, 0.0, D, u1, u2)
+    assert m[1_000_000] == -1.0
+    assert m[np.argmin(np.abs(t + 0.5))] == pytest.approx(-(1.0 - u1 - u2), rel=1e-15)
+    assert np.all(m[np.abs(t) > 0.5] == 0.0) and m[np.argmin(np.abs(t - 0.5))] == 0.0
+    assert np.array_equal(linear.limb_quad_template(t, 0.0, D, 0.0, 0.0),
+                          linear.box_template(t, 0.0, D))
+    area = -m.sum() * 1e-6
+    exact = 0.5 * D * (2.0 - u1 * (2.0 - np.pi / 2) - u2 * (10.0 / 3.0 - np.pi))
+    assert area == pytest.approx(exact, rel=1e-6)
+    # monotone from the limb to the centre for a physical law
+    left = m[(t >= -0.5) & (t <= 0.0)]
+    assert np.all(np.diff(left) <= 0.0)
 
 
 def test_empty_window_gives_nan():
