@@ -56,10 +56,21 @@ typedef enum {
 typedef enum {
     NU_BOX = 0,       /* -1 for t0 - D/2 <= t < t0 + D/2, else 0 (Sect. 2.1:
                          "normalized box-shaped transit")                        */
-    NU_TRAPEZOID = 1  /* total width D, linear ingress and egress of width
+    NU_TRAPEZOID = 1, /* total width D, linear ingress and egress of width
                          ingress_frac*D, flat bottom -1; not in the paper (its
-                         Sect. 4.4 names other base templates as a prospect)     */
+                         Sect. 4.4 names other base templates as a prospect).
+                         params[0] = ingress_frac, 0 < ingress_frac <= 0.5      */
+    NU_LIMB_QUAD = 2  /* limb-darkened transit as base model (Sect. 4.4's
+                         prospect): small-planet limit of a central transit
+                         under the quadratic law, -I(mu) on the window with
+                         r = 2 (t - t0) / D, mu = sqrt(1 - r^2), x = 1 - mu,
+                         I = 1 - u1 x - u2 x^2 (depth = the central dip).
+                         params[0] = u1, params[1] = u2, any finite values
+                         (physical laws have u1 + u2 <= 1)                       */
 } nu_template;
+/* Every template is zero outside its window t0 - D/2 <= t < t0 + D/2; the
+ * `tmpl_params` argument of the calls below is a host array read during the
+ * call (NULL allowed for NU_BOX). */
 
 /* Covariance terms.  kind and parameters:
  *   NU_TERM_SHO      p = {sigma, omega, Q}: Appendix A, k(0) = sigma^2;
@@ -137,13 +148,13 @@ void nu_factor_free(nu_factor* f);
  *   f             factor from nu_gp_factor (its samples define the windows)
  *   t0s_dev       (n_t0) trial epochs, any order
  *   Ds_host       (n_D) trial durations, > 0
- *   tmpl, ingress_frac  template and, for NU_TRAPEZOID, 0 < ingress_frac <= 0.5
+ *   tmpl, tmpl_params  template and its parameters (see nu_template)
  *   depth_dev, var_dev, dlnl_dev  outputs as above (double* or float*)
- * Errors: NU_EINVAL (null pointer, n_t0 < 1, n_D < 1, D <= 0, bad template),
- * NU_ENOMEM, NU_ECUDA. */
+ * Errors: NU_EINVAL (null pointer, n_t0 < 1, n_D < 1, D <= 0, bad template or
+ * template parameters), NU_ENOMEM, NU_ECUDA. */
 nu_status nu_linear_search(const nu_factor* f, const double* t0s_dev, int64_t n_t0,
                            const double* Ds_host, int n_D, nu_template tmpl,
-                           double ingress_frac, nu_precision prec, void* stream,
+                           const double* tmpl_params, nu_precision prec, void* stream,
                            void* depth_dev, void* var_dev, void* dlnl_dev);
 
 /* Periodic search (Sect. 2.3-2.4) over trial periods.
@@ -240,7 +251,7 @@ nu_status nu_rotation_alias_filter(const double* periods_dev, int64_t n_P, doubl
  *                 T0 output of nu_periodic_search
  *   D_idx_dev     (n_cand) int32 index into Ds_host, e.g. its D_idx output
  *   Ds_host       (n_D) durations, finite and > 0
- *   tmpl, ingress_frac  as in nu_linear_search
+ *   tmpl, tmpl_params  as in nu_linear_search
  *   depth_dev, var_dev, dlnl_dev, snr_dev  (n_cand) FP64 outputs
  * A candidate with P or T0 not finite, D_idx outside [0, n_D), 2 D > P
  * (windows would overlap), no sample in any window, or a template in the
@@ -249,10 +260,10 @@ nu_status nu_rotation_alias_filter(const double* periods_dev, int64_t n_P, doubl
  * samples, so a candidate costs O(samples in its windows + n/32 + 64 per
  * window).  Enqueued on `stream`; no synchronisation.
  * Errors: NU_EINVAL (null pointer, n_cand < 1, n_D < 1, a duration not finite
- * and > 0, bad template), NU_ENOMEM, NU_ECUDA. */
+ * and > 0, bad template or template parameters), NU_ENOMEM, NU_ECUDA. */
 nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev, const double* T0_dev,
                              const int* D_idx_dev, int64_t n_cand, const double* Ds_host,
-                             int n_D, nu_template tmpl, double ingress_frac, void* stream,
+                             int n_D, nu_template tmpl, const double* tmpl_params, void* stream,
                              double* depth_dev, double* var_dev, double* dlnl_dev,
                              double* snr_dev);
 

@@ -18,13 +18,22 @@ from . import build as _build
 
 NU_OK, NU_EINVAL, NU_ENOTPD, NU_ECUDA, NU_ENOMEM, NU_ETIMEOUT = range(6)
 NU_FP64, NU_MIXED = 0, 1
-NU_BOX, NU_TRAPEZOID = 0, 1
+NU_BOX, NU_TRAPEZOID, NU_LIMB_QUAD = 0, 1, 2
 NU_TERM_SHO, NU_TERM_EXP, NU_TERM_ROTATION = 0, 1, 2
 
 _STATUS_NAMES = {0: "NU_OK", 1: "NU_EINVAL", 2: "NU_ENOTPD", 3: "NU_ECUDA",
                  4: "NU_ENOMEM", 5: "NU_ETIMEOUT"}
 _PREC = {"fp64": NU_FP64, "mixed": NU_MIXED}
-_TMPL = {"box": NU_BOX, "trapezoid": NU_TRAPEZOID}
+_TMPL = {"box": NU_BOX, "trapezoid": NU_TRAPEZOID, "limb_quad": NU_LIMB_QUAD}
+
+
+def _tmpl_params(template, ingress_frac, ld):
+    """Host array of the template's parameters (see nu_template)."""
+    if template not in _TMPL:
+        raise ValueError(f"unknown template {template!r}")
+    vals = {"box": (0.0, 0.0), "trapezoid": (float(ingress_frac), 0.0),
+            "limb_quad": (float(ld[0]), float(ld[1]))}[template]
+    return (ctypes.c_double * 2)(*vals)
 
 
 class NuanceError(RuntimeError):
@@ -53,12 +62,12 @@ def _load():
     lib.nu_factor_size.restype = I64
     lib.nu_factor_free.argtypes = [P]
     lib.nu_factor_free.restype = None
-    lib.nu_linear_search.argtypes = [P, P, I64, P, I, I, D, I, P, P, P, P]
+    lib.nu_linear_search.argtypes = [P, P, I64, P, I, I, P, I, P, P, P, P]
     lib.nu_periodic_search.argtypes = [P, I64, P, I, P, P, P, I, P, I64, D, D, P,
                                        P, P, P, P, P, P]
     lib.nu_mask_transits.argtypes = [P, I64, I, P, P, P, I, D, D, D, P]
     lib.nu_mask_transits.restype = I
-    lib.nu_periodic_refine.argtypes = [P, P, P, P, I64, P, I, I, D, P, P, P, P, P]
+    lib.nu_periodic_refine.argtypes = [P, P, P, P, I64, P, I, I, P, P, P, P, P, P]
     lib.nu_periodic_refine.restype = I
     lib.nu_rotation_alias_filter.argtypes = [P, I64, D, D, I, P, P, P]
     lib.nu_rotation_alias_filter.restype = I
@@ -184,7 +193,7 @@ def nu_factor_info(factor):
 
 
 def nu_linear_search(factor, t0s, Ds, template="box", ingress_frac=0.1,
-                     precision="fp64", stream=None, out=None):
+                     precision="fp64", stream=None, out=None, ld=(0.4, 0.25)):
     """Linear search (Sect. 2.2).  Returns (depth, var, dlnl), each (n_D, n_t0)."""
     t0s = _dev(t0s, "t0s")
     Ds = [float(d) for d in (Ds.tolist() if hasattr(Ds, "tolist") else Ds)]
@@ -200,7 +209,7 @@ def nu_linear_search(factor, t0s, Ds, template="box", ingress_frac=0.1,
                              "precision's dtype")
     Ds_arr = (ctypes.c_double * n_D)(*Ds)
     st = LIB.nu_linear_search(factor.handle, _p(t0s), n_t0, Ds_arr, n_D,
-                              _TMPL[template], float(ingress_frac), prec,
+                              _TMPL[template], _tmpl_params(template, ingress_frac, ld), prec,
                               _stream_ptr(stream), _p(out[0]), _p(out[1]), _p(out[2]))
     _check(st, "nu_linear_search")
     return out
@@ -267,7 +276,7 @@ def nu_rotation_alias_filter(periods, P_star, tol=0.02, symmetric=False, stream=
 
 
 def nu_periodic_refine(factor, periods, T0, D_idx, Ds, template="box", ingress_frac=0.1,
-                       stream=None):
+                       stream=None, ld=(0.4, 0.25)):
     """Exact periodic-template fit of candidates (see nu_periodic_refine in the
     header).  periods, T0 (float64) and D_idx (int32) are (n_cand,) device
     arrays, e.g. a selection of nu_periodic_search's outputs.  Returns a dict
@@ -283,7 +292,8 @@ def nu_periodic_refine(factor, periods, T0, D_idx, Ds, template="box", ingress_f
     res = {name: torch.empty(n, dtype=torch.float64, device=periods.device)
            for name in ("depth", "var", "dlnl", "snr")}
     st = LIB.nu_periodic_refine(factor.handle, _p(periods), _p(T0), _p(D_idx), n, Ds_arr,
-                                len(Ds_l), _TMPL[template], float(ingress_frac),
+                                len(Ds_l), _TMPL[template],
+                                _tmpl_params(template, ingress_frac, ld),
                                 _stream_ptr(stream), _p(res["depth"]), _p(res["var"]),
                                 _p(res["dlnl"]), _p(res["snr"]))
     _check(st, "nu_periodic_refine")

@@ -20,6 +20,7 @@
 
 #include "nu_internal.cuh"
 #include "ss.cuh"
+#include "templates.cuh"
 
 namespace nu {
 
@@ -59,7 +60,7 @@ template <> struct Acc<double> {
 template <int NB, typename T, int TMPL>
 __device__ __forceinline__ void window_fit(const double* __restrict__ t, int64_t n, int k,
                                            const FactorView<T>& fv, double t0, double D,
-                                           double ingress_frac, T& out_d, T& out_v, T& out_l) {
+                                           const TmplArgs& ta, T& out_d, T& out_v, T& out_l) {
     constexpr int J = Dims<NB>::J;
     constexpr int JJ = Dims<NB>::JJ;
     const double half = D * 0.5;
@@ -71,7 +72,6 @@ __device__ __forceinline__ void window_fit(const double* __restrict__ t, int64_t
     out_v = nanv;
     out_l = nanv;
     if (hi <= lo) return;
-    const double ramp = ingress_frac * D;
     T s[J];
 #pragma unroll
     for (int c = 0; c < J; ++c) s[c] = T(0);
@@ -81,13 +81,7 @@ __device__ __forceinline__ void window_fit(const double* __restrict__ t, int64_t
 #pragma unroll
     for (int a = 0; a < NU_MAX_K; ++a) bt[a].init();
     for (int64_t m = lo; m < hi; ++m) {
-        T mv;
-        if (TMPL == NU_BOX) {
-            mv = T(-1);
-        } else {
-            const double dd = __ddiv_rn(__dsub_rn(half, fabs(__dsub_rn(t[m], t0))), ramp);
-            mv = (T)(-fmin(fmax(dd, 0.0), 1.0));
-        }
+        const T mv = TMPL == NU_BOX ? T(-1) : (T)template_value<TMPL>(t[m], t0, half, D, ta);
         const T e = mv - hdot<NB>(s);
         const T iD = fv.invD[m];
         c2.add(e * e * iD);
@@ -138,14 +132,14 @@ template <int NB, typename T, int TMPL>
 __global__ void __launch_bounds__(128)
 k_window(const double* __restrict__ t, int64_t n, int k, FactorView<T> fv,
          const double* __restrict__ t0s, int64_t n_t0, const double* __restrict__ Ds,
-         int n_D, double ingress_frac, T* __restrict__ out_depth, T* __restrict__ out_var,
+         int n_D, TmplArgs ta, T* __restrict__ out_depth, T* __restrict__ out_var,
          T* __restrict__ out_dlnl) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= n_t0 * (int64_t)n_D) return;
     const int j = (int)(gid / n_t0);
     const int64_t i = gid - (int64_t)j * n_t0;
     T d, v, l;
-    window_fit<NB, T, TMPL>(t, n, k, fv, t0s[i], Ds[j], ingress_frac, d, v, l);
+    window_fit<NB, T, TMPL>(t, n, k, fv, t0s[i], Ds[j], ta, d, v, l);
     out_depth[gid] = d;
     out_var[gid] = v;
     out_dlnl[gid] = l;
@@ -171,8 +165,8 @@ k_window_batch(const double* __restrict__ t, int k, FactorView<T> fv,
     const int j = (int)(w / ng);
     const int64_t i = w - (int64_t)j * ng;
     T d, v, l;
-    window_fit<NB, T, NU_BOX>(t + s0, ng, k, view_at<NB, T>(fv, s0, k), t[s0 + i], Ds[j], 0.1,
-                              d, v, l);
+    window_fit<NB, T, NU_BOX>(t + s0, ng, k, view_at<NB, T>(fv, s0, k), t[s0 + i], Ds[j],
+                              TmplArgs{0.0, 0.0}, d, v, l);
     out_depth[gid] = d;
     out_var[gid] = v;
     out_dlnl[gid] = l;
@@ -181,17 +175,19 @@ k_window_batch(const double* __restrict__ t, int k, FactorView<T> fv,
 template <int NB, typename T>
 static void launch_window(const nu_factor* f, FactorView<T> fv, const double* t0s,
                           int64_t n_t0, const double* Ds_dev, int n_D, int tmpl,
-                          double ingress, void* d, void* v, void* l, cudaStream_t st) {
+                          const TmplArgs& ta, void* d, void* v, void* l, cudaStream_t st) {
     const int64_t total = n_t0 * (int64_t)n_D;
     const int th = 128;
     const int blocks = div_up(total, th);
     if (tmpl == NU_BOX)
         k_window<NB, T, NU_BOX><<<blocks, th, 0, st>>>(f->t, f->n, f->k, fv, t0s, n_t0,
-                                                      Ds_dev, n_D, ingress, (T*)d, (T*)v,
-                                                      (T*)l);
-    else
+                                                      Ds_dev, n_D, ta, (T*)d, (T*)v, (T*)l);
+    else if (tmpl == NU_TRAPEZOID)
         k_window<NB, T, NU_TRAPEZOID><<<blocks, th, 0, st>>>(
-            f->t, f->n, f->k, fv, t0s, n_t0, Ds_dev, n_D, ingress, (T*)d, (T*)v, (T*)l);
+            f->t, f->n, f->k, fv, t0s, n_t0, Ds_dev, n_D, ta, (T*)d, (T*)v, (T*)l);
+    else
+        k_window<NB, T, NU_LIMB_QUAD><<<blocks, th, 0, st>>>(
+            f->t, f->n, f->k, fv, t0s, n_t0, Ds_dev, n_D, ta, (T*)d, (T*)v, (T*)l);
 }
 
 // Linear search of packed light curves (batch path); no allocation, no sync.
@@ -229,17 +225,17 @@ using namespace nu;
 
 extern "C" nu_status nu_linear_search(const nu_factor* f, const double* t0s_dev,
                                       int64_t n_t0, const double* Ds_host, int n_D,
-                                      nu_template tmpl, double ingress_frac,
+                                      nu_template tmpl, const double* tmpl_params,
                                       nu_precision prec, void* stream, void* depth_dev,
                                       void* var_dev, void* dlnl_dev) {
     if (!f) return fail(NU_EINVAL, "nu_linear_search: null factor");
     if (!t0s_dev || !Ds_host || !depth_dev || !var_dev || !dlnl_dev)
         return fail(NU_EINVAL, "nu_linear_search: null array");
     if (n_t0 < 1 || n_D < 1) return fail(NU_EINVAL, "nu_linear_search: empty grid");
-    if (tmpl != NU_BOX && tmpl != NU_TRAPEZOID)
-        return fail(NU_EINVAL, "nu_linear_search: unknown template %d", (int)tmpl);
-    if (tmpl == NU_TRAPEZOID && !(ingress_frac > 0.0 && ingress_frac <= 0.5))
-        return fail(NU_EINVAL, "nu_linear_search: ingress_frac must be in (0, 0.5]");
+    TmplArgs ta;
+    const char* why = "";
+    if (!template_args((int)tmpl, tmpl_params, &ta, &why))
+        return fail(NU_EINVAL, "nu_linear_search: %s (template %d)", why, (int)tmpl);
     if (prec != NU_FP64 && prec != NU_MIXED)
         return fail(NU_EINVAL, "nu_linear_search: unknown precision %d", (int)prec);
     for (int j = 0; j < n_D; ++j)
@@ -263,18 +259,18 @@ extern "C" nu_status nu_linear_search(const nu_factor* f, const double* t0s_dev,
     if (prec == NU_FP64) {
         FactorView<double> fv{f->F, f->kg, f->invD, f->G, f->z0, f->Zt};
         switch (f->nb) {
-            case 1: launch_window<1, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
-            case 2: launch_window<2, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
-            case 3: launch_window<3, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
-            default: launch_window<4, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
+            case 1: launch_window<1, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
+            case 2: launch_window<2, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
+            case 3: launch_window<3, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
+            default: launch_window<4, double>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
         }
     } else {
         FactorView<float> fv{f->F32, f->kg32, f->invD32, f->G32, f->z032, f->Zt32};
         switch (f->nb) {
-            case 1: launch_window<1, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
-            case 2: launch_window<2, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
-            case 3: launch_window<3, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
-            default: launch_window<4, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, st); break;
+            case 1: launch_window<1, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
+            case 2: launch_window<2, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
+            case 3: launch_window<3, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
+            default: launch_window<4, float>(f, fv, t0s_dev, n_t0, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, st); break;
         }
     }
     count_launches(1);

@@ -25,6 +25,7 @@
 
 #include "nu_internal.cuh"
 #include "ss.cuh"
+#include "templates.cuh"
 
 namespace nu {
 
@@ -139,7 +140,7 @@ k_refine(const double* __restrict__ t, int64_t n, int k, FactorView<double> fv,
          const double* __restrict__ Phi, const double* __restrict__ Mq, int64_t n_blk,
          const double* __restrict__ Ps, const double* __restrict__ T0s,
          const int* __restrict__ Didx, int64_t n_cand, const double* __restrict__ Ds, int n_D,
-         double ingress_frac, double* __restrict__ out_depth, double* __restrict__ out_var,
+         TmplArgs ta, double* __restrict__ out_depth, double* __restrict__ out_var,
          double* __restrict__ out_dlnl, double* __restrict__ out_snr) {
     constexpr int J = Dims<NB>::J;
     constexpr int JJ = Dims<NB>::JJ;
@@ -154,7 +155,6 @@ k_refine(const double* __restrict__ t, int64_t n, int k, FactorView<double> fv,
     const double P = Ps[cid], T0 = T0s[cid], D = Ds[jd];
     if (!isfinite(P) || !isfinite(T0) || !(D > 0.0) || !(2.0 * D <= P)) return;
     const double half = D * 0.5;
-    const double ramp = ingress_frac * D;
 
     double s[J];
 #pragma unroll
@@ -216,13 +216,7 @@ k_refine(const double* __restrict__ t, int64_t n, int k, FactorView<double> fv,
         }
         // the window, template as input
         for (int64_t m = lo; m < hi; ++m) {
-            double mv;
-            if (TMPL == NU_BOX) {
-                mv = -1.0;
-            } else {
-                const double dd = __ddiv_rn(__dsub_rn(half, fabs(__dsub_rn(t[m], tc))), ramp);
-                mv = -fmin(fmax(dd, 0.0), 1.0);
-            }
+            const double mv = template_value<TMPL>(t[m], tc, half, D, ta);
             rf_step<NB>(fv, m, n, mv, s, c2);
             num = fma(mv, fv.z0[m], num);
             for (int a = 0; a < k; ++a) bt[a] = fma(mv, fv.Zt[m * k + a], bt[a]);
@@ -248,8 +242,9 @@ k_refine(const double* __restrict__ t, int64_t n, int k, FactorView<double> fv,
 template <int NB>
 static void launch_refine(const nu_factor* f, const double* Phi, const double* Mq,
                           int64_t n_blk, const double* P, const double* T0, const int* Didx,
-                          int64_t n_cand, const double* Ds, int n_D, int tmpl, double ingress,
-                          double* d, double* v, double* l, double* snr, cudaStream_t st) {
+                          int64_t n_cand, const double* Ds, int n_D, int tmpl,
+                          const TmplArgs& ta, double* d, double* v, double* l, double* snr,
+                          cudaStream_t st) {
     const FactorView<double> fv{f->F, f->kg, f->invD, f->G, f->z0, f->Zt};
     const int th = 128;
     if (n_blk > 0)
@@ -257,12 +252,16 @@ static void launch_refine(const nu_factor* f, const double* Phi, const double* M
                                                              (double*)Phi, (double*)Mq);
     if (tmpl == NU_BOX)
         k_refine<NB, NU_BOX><<<div_up(n_cand, th), th, 0, st>>>(
-            f->t, f->n, f->k, fv, Phi, Mq, n_blk, P, T0, Didx, n_cand, Ds, n_D, ingress, d, v,
-            l, snr);
-    else
+            f->t, f->n, f->k, fv, Phi, Mq, n_blk, P, T0, Didx, n_cand, Ds, n_D, ta, d, v, l,
+            snr);
+    else if (tmpl == NU_TRAPEZOID)
         k_refine<NB, NU_TRAPEZOID><<<div_up(n_cand, th), th, 0, st>>>(
-            f->t, f->n, f->k, fv, Phi, Mq, n_blk, P, T0, Didx, n_cand, Ds, n_D, ingress, d, v,
-            l, snr);
+            f->t, f->n, f->k, fv, Phi, Mq, n_blk, P, T0, Didx, n_cand, Ds, n_D, ta, d, v, l,
+            snr);
+    else
+        k_refine<NB, NU_LIMB_QUAD><<<div_up(n_cand, th), th, 0, st>>>(
+            f->t, f->n, f->k, fv, Phi, Mq, n_blk, P, T0, Didx, n_cand, Ds, n_D, ta, d, v, l,
+            snr);
 }
 
 }  // namespace nu
@@ -272,7 +271,8 @@ using namespace nu;
 extern "C" nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev,
                                         const double* T0_dev, const int* D_idx_dev,
                                         int64_t n_cand, const double* Ds_host, int n_D,
-                                        nu_template tmpl, double ingress_frac, void* stream,
+                                        nu_template tmpl, const double* tmpl_params,
+                                        void* stream,
                                         double* depth_dev, double* var_dev, double* dlnl_dev,
                                         double* snr_dev) {
     if (!f) return fail(NU_EINVAL, "nu_periodic_refine: null factor");
@@ -282,10 +282,10 @@ extern "C" nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev,
     if (n_cand < 1 || n_D < 1) return fail(NU_EINVAL, "nu_periodic_refine: empty input");
     if (n_cand > (int64_t)1 << 31)
         return fail(NU_EINVAL, "nu_periodic_refine: more than 2^31 candidates");
-    if (tmpl != NU_BOX && tmpl != NU_TRAPEZOID)
-        return fail(NU_EINVAL, "nu_periodic_refine: unknown template %d", (int)tmpl);
-    if (tmpl == NU_TRAPEZOID && !(ingress_frac > 0.0 && ingress_frac <= 0.5))
-        return fail(NU_EINVAL, "nu_periodic_refine: ingress_frac must be in (0, 0.5]");
+    TmplArgs ta;
+    const char* why = "";
+    if (!template_args((int)tmpl, tmpl_params, &ta, &why))
+        return fail(NU_EINVAL, "nu_periodic_refine: %s (template %d)", why, (int)tmpl);
     for (int j = 0; j < n_D; ++j)
         if (!(Ds_host[j] > 0.0) || !std::isfinite(Ds_host[j]))
             return fail(NU_EINVAL, "nu_periodic_refine: durations must be finite and > 0");
@@ -310,10 +310,10 @@ extern "C" nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev,
         cudaEventDestroy(ev);
     }
     switch (f->nb) {
-        case 1: launch_refine<1>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
-        case 2: launch_refine<2>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
-        case 3: launch_refine<3>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
-        default: launch_refine<4>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ingress_frac, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+        case 1: launch_refine<1>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+        case 2: launch_refine<2>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+        case 3: launch_refine<3>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
+        default: launch_refine<4>(f, Phi, Mq, n_blk, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;
     }
     count_launches(n_blk > 0 ? 2 : 1);
     e = cudaGetLastError();

@@ -45,7 +45,7 @@ def test_host_side_argument_errors(lib):
     assert st == 1
     assert b"n >= 2" in lib.nu_last_error()
     st = lib.nu_linear_search(None, None, ctypes.c_int64(0), None, 0, 0,
-                              ctypes.c_double(0.1), 0, None, None, None, None)
+                              None, 0, None, None, None, None)
     assert st == 1
     lib.nu_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.nu_version()

@@ -50,7 +50,7 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("kind", ["box", "trapezoid"])
+@pytest.mark.parametrize("kind", ["box", "trapezoid", "limb_quad"])
 def test_linear_fp64_small(case, kind):
     lc = synth.small_curve(n=300, seed=21, gap=40)
     terms = CASES[case]["terms"]
@@ -109,6 +109,36 @@ def test_single_2048_mixed_full_grid(c1):
     print("single_2048 mixed errors", err)
     assert err["depth"] <= MIXED_DEPTH_TOL, err
     assert err["var"] <= 1e-4 and err["dlnl"] <= 1e-3, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_limb_quad_coefficients(precision):
+    """The limb-darkening coefficients reach the kernel: non-default (u1, u2)
+    against the oracle, and u1 = u2 = 0 reproduces the box."""
+    lc = synth.small_curve(n=500, seed=8, gap=25)
+    Ds = np.array([0.02, 0.06])
+    f = api.nu_gp_factor(cu(lc.t), cu(lc.diag_var), lc.terms, cu(lc.X), cu(lc.y))
+    g = [o.double().cpu().numpy() for o in
+         api.nu_linear_search(f, cu(lc.t), Ds, template="limb_quad", ld=(0.62, -0.1),
+                              precision=precision)]
+    ora = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t, Ds,
+                               kind="limb_quad", ld=(0.62, -0.1))
+    err = linear_errors(g, (ora["depth"], ora["var"], ora["dlnl"]))
+    if precision == "fp64":
+        assert max(err["depth"], err["var"], err["dlnl"]) <= FP64_TOL, err
+    else:
+        assert err["depth"] <= MIXED_DEPTH_TOL and err["var"] <= 1e-4, err
+    flat = [o.double().cpu().numpy() for o in
+            api.nu_linear_search(f, cu(lc.t), Ds, template="limb_quad", ld=(0.0, 0.0),
+                                 precision=precision)]
+    box = [o.double().cpu().numpy() for o in
+           api.nu_linear_search(f, cu(lc.t), Ds, template="box", precision=precision)]
+    for a, b in zip(flat, box):
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        ok = ~np.isnan(b)
+        assert np.allclose(a[ok], b[ok], rtol=1e-12 if precision == "fp64" else 1e-6, atol=0)
+    with pytest.raises(api.NuanceError):
+        api.nu_linear_search(f, cu(lc.t), Ds, template="limb_quad", ld=(float("nan"), 0.1))
 
 
 def test_factor_rejects_unsorted_times():

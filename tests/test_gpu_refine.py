@@ -73,7 +73,7 @@ def candidate_set(t, n_D, rng, n_random=120):
     return c
 
 
-@pytest.mark.parametrize("kind", ["box", "trapezoid"])
+@pytest.mark.parametrize("kind", ["box", "trapezoid", "limb_quad"])
 @pytest.mark.parametrize("gap", [None, 400])
 def test_refine_matches_dense_oracle(kind, gap):
     lc = synth.small_curve(n=2200, seed=3, p_rot=1.3, sigma=4e-3, sigma_w=1e-3, gap=gap,
