@@ -242,6 +242,26 @@ def run_refine(pipe, api, torch, n_top=64, reps=5):
 
 
 # ------------------------------------------------------------ batch (C4)
+def recovery(w, r):
+    """Sect. 3's detection rule on the batch result, for workloads whose
+    curves all carry the same injected period p: a curve counts as recovered
+    when its best period is within 0.01 d of p, 2p or p/2 and its Q >= 6."""
+    ps = {lc.injected.get("period") for lc in w.curves}
+    if len(ps) != 1 or None in ps:
+        return {}
+    p = ps.pop()
+    Q = r["Q"].double().cpu().numpy()
+    Q = np.where(np.isfinite(Q), Q, -np.inf)
+    best = np.argmax(Q, axis=1)
+    pb = w.periods[best]
+    qb = Q[np.arange(len(best)), best]
+    near = np.min(np.abs(pb[:, None] - np.array([p, 2 * p, p / 2])[None, :]), axis=1) < 0.01
+    hit = near & (qb >= 6.0)
+    return {"recovered_fraction": float(hit.mean()), "recovered": int(hit.sum()),
+            "curves": int(len(hit))}
+
+
+
 def run_batch(api, torch, w, precision, steps, warmup, flush):
     """nu_batch_search over all curves of a survey workload; one step = one
     batched call (factor, linear search and fold of every curve)."""
@@ -265,7 +285,8 @@ def run_batch(api, torch, w, precision, steps, warmup, flush):
         times.append(e0.elapsed_time(e1))
     n_templates = sum(len(lc.t) for lc in w.curves) * len(w.durations)
     ms = float(np.mean(times))
-    return {"workload": f"{w.name}: {len(w.curves)} curves, "
+    out_rec = recovery(w, r)
+    return {**out_rec, "workload": f"{w.name}: {len(w.curves)} curves, "
                         f"{sum(len(lc.t) for lc in w.curves)} samples, "
                         f"{len(w.durations)} durations, {len(w.periods)} periods",
             "precision": precision, "ms_per_step": ms,

@@ -23,6 +23,13 @@ periods from a fraction of a day to days):
 * ``survey_438``    438 light curves, N ~ U[8000, 20000], 1-3 random gaps.
 * ``multisector_136080`` seven sectors with 1-day gaps, 20 durations 15 min-4 h,
                     100 000 periods 0.2-50 d.
+* ``injection_4000`` the simulated injection-recovery set-up of Sect. 3 (its
+                    first comparison): 4000 curves of 4 days at 2 min (N = 2880),
+                    white noise 0.1 %, a common transit P = 1.1 d, T0 = 0.2 d,
+                    D = 0.04 d, depth 1 %, and SHO variability whose frequency and
+                    amplitude follow Eq. relative_params from tau ~ U(0.1, 10),
+                    delta ~ U(0.1, 25), with Q ~ U(10, 100); searched with the
+                    same SHO kernel, the one duration and 4000 periods 0.3-3 d.
 """
 from __future__ import annotations
 
@@ -198,10 +205,44 @@ def small_curve(n=300, seed=7, p_rot=0.5, sigma=1e-2, sigma_w=1e-3, gap=None,
                       design=design)
 
 
+def injection_4000(n_curves=4000, seed_index=5):
+    """Sect. 3's simulated injection-recovery curves (see the module notes).
+
+    Eq. relative_params ties the SHO kernel to the transit: tau = pi/(omega D)
+    and delta = 2 sigma / depth, so omega = pi/(tau D) and sigma = delta
+    depth / 2.  The variability is the driven AR(2) sequence with its peak at
+    the SHO's period 2 pi / omega and quality Q (a stand-in, as elsewhere in
+    this module); the search kernel is the SHO (sigma, omega, Q) itself.
+    """
+    rng = np.random.default_rng(BASE_SEED + seed_index)
+    n, depth, duration, period, epoch = 2880, 1e-2, 0.04, 1.1, 0.2
+    sigma_w = 1e-3
+    t = np.arange(n) * CADENCE_DAYS
+    curves = []
+    for _ in range(n_curves):
+        tau = float(rng.uniform(0.1, 10.0))
+        delta = float(rng.uniform(0.1, 25.0))
+        q = float(rng.uniform(10.0, 100.0))
+        omega = np.pi / (tau * duration)
+        sigma = delta * depth / 2.0
+        var = _ar2_variability(rng, n, 2.0 * np.pi / omega, q, sigma)
+        y = 1.0 + var + sigma_w * rng.standard_normal(n)
+        y = _inject_box(t, y, depth, duration, period, epoch)
+        curves.append(LightCurve(
+            t=t.copy(), y=y, diag_var=np.full(n, sigma_w ** 2),
+            terms=[(TERM_SHO, (sigma, omega, q, 0.0, 0.0))],
+            X=np.stack([np.ones(n), t], axis=1),
+            injected=dict(depth=depth, duration=duration, period=period, epoch=epoch,
+                          tau=tau, delta=delta, Q=q)))
+    return Workload("injection_4000", curves, np.array([duration]),
+                    np.linspace(0.3, 3.0, 4000), BASE_SEED + seed_index)
+
+
 WORKLOADS = {
     "single_2048": single_2048,
     "sector_19440": sector_19440,
     "sector_19440_16d": sector_19440_16d,
     "survey_438": survey_438,
     "multisector_136080": multisector_136080,
+    "injection_4000": injection_4000,
 }

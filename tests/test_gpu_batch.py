@@ -93,3 +93,35 @@ def test_batch_reports_a_failing_curve_alone(curves):
     res = api.nu_batch_search(items, DS, PERIODS, k=2, precision="fp64", phase_step=dt)
     st = res["status"]
     assert st[2] != 0 and all(s == 0 for i, s in enumerate(st) if i != 2)
+
+
+def test_injection_workload_shape_against_oracle():
+    """The injection-recovery set-up (4-day curves, SHO kernels with Q up to
+    100 and amplitudes up to 12 % of the flux, one duration) through the batch:
+    every curve equals its single-curve calls, two equal the oracle."""
+    w = synth.injection_4000(n_curves=6)
+    Ds = w.durations
+    periods = np.linspace(0.3, 3.0, 300)
+    dt = synth.CADENCE_DAYS
+    res = api.nu_batch_search([(lc.t, lc.y, lc.diag_var, lc.terms) for lc in w.curves], Ds,
+                              periods, k=2, precision="fp64", phase_step=dt)
+    assert res["status"] == [0] * len(w.curves)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    for c, lc in enumerate(w.curves):
+        f = api.nu_gp_factor(cu(lc.t), cu(lc.diag_var), lc.terms, cu(lc.X), cu(lc.y))
+        d, v, l = api.nu_linear_search(f, cu(lc.t), Ds)
+        one = api.nu_periodic_search(cu(lc.t), Ds, d, v, l, cu(periods), phase_step=dt)
+        for key in ("Q", "T0", "lnP"):
+            np.testing.assert_allclose(res[key][c].cpu().numpy(), one[key].cpu().numpy(),
+                                       rtol=1e-12, atol=0, err_msg=key)
+    for c in (0, 3):
+        lc = w.curves[c]
+        g = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t, Ds)
+        ora = periodic.periodic_search(lc.t, g["depth"], g["var"], g["dlnl"], periods, dt)
+        gpu = {k: res[k][c].cpu().numpy() for k in ("Q", "T0", "D_idx", "depth", "sigma", "lnP")}
+        wl, wq, _ = periodic_compare(gpu, ora, lc.t, g["depth"], g["var"], g["dlnl"], periods,
+                                     dt, FP64_TOL, FP64_TOL, periodic.fold_period)
+        print(f"injection curve {c} (tau {lc.injected['tau']:.2f}, delta "
+              f"{lc.injected['delta']:.2f}, Q {lc.injected['Q']:.1f}): lnP err {wl:.2e}, "
+              f"Q err {wq:.2e}")
+        assert wl <= FP64_TOL and wq <= FP64_TOL
