@@ -25,6 +25,14 @@
 
 namespace nu {
 
+// n_out periods spread evenly over the grid (the autotuner's slice)
+__global__ void k_sample_periods(const double* __restrict__ periods, int64_t n_P, int n_out,
+                                 double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_out) return;
+    out[i] = periods[(int64_t)((double)i * (double)n_P / (double)n_out)];
+}
+
 __global__ void k_init_dstat(long long* dstat, const int64_t* __restrict__ s_off, int n_seg) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_seg) return;
@@ -125,6 +133,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t o_irr = off;   off += al((size_t)n_lc * 4);
     const size_t o_Ds = off;    off += al((size_t)n_D * 8);
     const size_t o_ctr = off;   off += 256;
+    const size_t o_tune = off;  off += al(512 * 8);
     const size_t base_bytes = off;
     char* mem = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&mem, base_bytes, st);
@@ -263,20 +272,29 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         if (it != g_tune.end()) tv = it->second;
     }
     if (tv.threads == 0) {
-        // time the fold on a slice (first curves, first periods) for each shape
-        const int n_run = n_lc < 8 ? n_lc : 8;
-        const int64_t nP_run = n_P < 256 ? n_P : 256;
-        const int cand[4][2] = {{2, 256}, {4, 256}, {4, 128}, {8, 128}};
+        // time the fold on a slice (the first curves, periods spread over the
+        // whole grid) for each shape; the slice holds several times more
+        // (curve, period) items than the largest grid has blocks, so that it
+        // measures throughput rather than the latency of single items
+        const int n_run = n_lc < 64 ? n_lc : 64;
+        const int64_t nP_run = n_P < 512 ? n_P : 512;
+        double* tune_periods = (double*)(mem + o_tune);
+        k_sample_periods<<<2, 256, 0, st>>>(periods_dev, n_P, (int)nP_run, tune_periods);
+        count_launches(1);
+        ++launched;
+        // blocks per SM x threads; small blocks suit short curves, whose
+        // (curve, period) items hold few cells (each warp seeds its item)
+        const int cand[6][2] = {{2, 256}, {4, 256}, {4, 128}, {8, 128}, {8, 64}, {16, 64}};
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         launched += enqueue(n_sm * 2, 256, nP_run, n_run, st);    // warm the caches
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 6; ++c) {
             cudaMemsetAsync(ctr, 0, 16, st);
             cudaEventRecord(e0, st);
             const int lt = launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, fsc,
-                                             n_D, phase_step, gap_factor, periods_dev,
+                                             n_D, phase_step, gap_factor, tune_periods,
                                              nP_run, ctr, n_sm * cand[c][0], cand[c][1], Q_dev,
                                              T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
                                              lnP_dev, st);
