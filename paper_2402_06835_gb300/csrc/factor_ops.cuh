@@ -271,6 +271,288 @@ struct RiccatiOp {
     }
 };
 
+// ------------------------------------------- Riccati tree, one warp per group
+// The tree levels of the Riccati scan have few groups (C2: 608 at the widest),
+// and each combine or apply is a chain of about 600 FP64 operations on J x J
+// matrices in one thread.  Here one warp takes a group and its lanes own the
+// matrix entries (row-major in shared memory), so a product is J FMAs per
+// lane and the Gauss-Jordan solve J short steps.  Every entry goes through the
+// same sequence of FP64 operations as in the thread version (mat_mul,
+// mat_solve, mat_symmetrize).
+template <int J>
+struct WEnt {
+    static constexpr int N = J * J;
+    static constexpr int PER = (N + 31) / 32;
+};
+
+// C = A B, C = A^T B, C = A B^T (C must not alias A or B)
+template <int J, int MODE>
+__device__ __forceinline__ void wmat_prod(const double* A, const double* B, double* C,
+                                          int lane) {
+#pragma unroll
+    for (int t = 0; t < WEnt<J>::PER; ++t) {
+        const int e = lane + 32 * t;
+        if (e < J * J) {
+            const int r = e / J, c = e - r * J;
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < J; ++k) {
+                const double a = MODE == 1 ? A[k * J + r] : A[r * J + k];
+                const double b = MODE == 2 ? B[c * J + k] : B[k * J + c];
+                s = fma(a, b, s);
+            }
+            C[e] = s;
+        }
+    }
+    __syncwarp();
+}
+
+// m <- (m + add) symmetrised as mat_symmetrize does (add may be null)
+template <int J>
+__device__ __forceinline__ void wmat_add_sym(double* m, const double* add, int lane) {
+    if (add) {
+#pragma unroll
+        for (int t = 0; t < WEnt<J>::PER; ++t) {
+            const int e = lane + 32 * t;
+            if (e < J * J) m[e] += add[e];
+        }
+        __syncwarp();
+    }
+    double v[WEnt<J>::PER];
+#pragma unroll
+    for (int t = 0; t < WEnt<J>::PER; ++t) {
+        const int e = lane + 32 * t;
+        if (e < J * J) {
+            const int r = e / J, c = e - r * J;
+            const int lo = r < c ? r : c, hi = r < c ? c : r;
+            v[t] = r == c ? m[e] : 0.5 * (m[lo * J + hi] + m[hi * J + lo]);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < WEnt<J>::PER; ++t) {
+        const int e = lane + 32 * t;
+        if (e < J * J) m[e] = v[t];
+    }
+    __syncwarp();
+}
+
+// [B1 B2] <- M^-1 [B1 B2] by Gauss-Jordan with partial pivoting (the first
+// row of largest magnitude), as mat_solve; M is overwritten.  B2 may be null.
+template <int J, int NRHS>
+__device__ __forceinline__ void wmat_solve(double* M, double* B1, double* B2, int lane) {
+    constexpr int W = (NRHS + 1) * J;                  // augmented row width
+    constexpr int PER = (J * W + 31) / 32;
+    auto at = [&](int r, int k) -> double* {
+        return k < J ? &M[r * J + k] : (k < 2 * J ? &B1[r * J + k - J] : &B2[r * J + k - 2 * J]);
+    };
+    for (int c = 0; c < J; ++c) {
+        double v = (lane >= c && lane < J) ? fabs(M[lane * J + c]) : -1.0;
+        int piv = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int p2 = __shfl_xor_sync(0xffffffffu, piv, o);
+            if (v2 > v || (v2 == v && p2 < piv)) {
+                v = v2;
+                piv = p2;
+            }
+        }
+        // lane 0's choice for all (lanes could disagree only on NaN entries)
+        piv = __shfl_sync(0xffffffffu, piv, 0);
+        if (piv != c && piv < J) {
+            for (int k = lane; k < W; k += 32) {
+                double* a = at(c, k);
+                double* b = at(piv, k);
+                const double tmp = *a;
+                *a = *b;
+                *b = tmp;
+            }
+            __syncwarp();
+        }
+        const double inv = 1.0 / M[c * J + c];
+        __syncwarp();
+        for (int k = lane; k < W; k += 32) *at(c, k) *= inv;
+        __syncwarp();
+        double f[PER];
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int e = lane + 32 * t;
+            f[t] = e < J * W ? M[(e / W) * J + c] : 0.0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int e = lane + 32 * t;
+            if (e < J * W) {
+                const int r = e / W, k = e - r * W;
+                if (r != c) {
+                    double* x = at(r, k);
+                    *x = fma(-f[t], *at(c, k), *x);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void wcopy(double* dst, const double* src, int n, int lane) {
+    for (int e = lane; e < n; e += 32) dst[e] = src[e];
+    __syncwarp();
+}
+
+// shared-memory workspace of one warp
+template <int J>
+struct RicWarpSmem {
+    double A[J * J], C[J * J], Jm[J * J];       // accumulated element / state P in A
+    double eA[J * J], eC[J * J], eJ[J * J];     // the element being applied
+    double M[J * J], Y1[J * J], Y2[J * J], T[J * J], R1[J * J], R2[J * J], R3[J * J];
+};
+
+// acc <- combine(acc, e) (RiccatiOp::combine)
+template <int J>
+__device__ __forceinline__ void ric_combine_w(RicWarpSmem<J>& s, int lane) {
+    wmat_prod<J, 0>(s.C, s.eJ, s.M, lane);            // C_i Jm_j
+    if (lane < J) s.M[lane * J + lane] += 1.0;
+    wcopy<J>(s.Y1, s.A, J * J, lane);
+    wcopy<J>(s.Y2, s.C, J * J, lane);
+    wmat_solve<J, 2>(s.M, s.Y1, s.Y2, lane);          // X A_i, X C_i
+    wmat_prod<J, 0>(s.eA, s.Y1, s.R1, lane);          // A_j X A_i
+    wmat_prod<J, 0>(s.eA, s.Y2, s.T, lane);           // A_j X C_i
+    wmat_prod<J, 2>(s.T, s.eA, s.R2, lane);           // ... A_j^T
+    wmat_add_sym<J>(s.R2, s.eC, lane);
+    wmat_prod<J, 1>(s.Y1, s.eJ, s.T, lane);           // (X A_i)^T Jm_j
+    wmat_prod<J, 0>(s.T, s.A, s.R3, lane);            // ... A_i
+    wmat_add_sym<J>(s.R3, s.Jm, lane);
+    wcopy<J>(s.A, s.R1, J * J, lane);
+    wcopy<J>(s.C, s.R2, J * J, lane);
+    wcopy<J>(s.Jm, s.R3, J * J, lane);
+}
+
+// P (in s.A) <- apply(e, P) (RiccatiOp::apply)
+template <int J>
+__device__ __forceinline__ void ric_apply_w(RicWarpSmem<J>& s, int lane) {
+    wmat_prod<J, 0>(s.A, s.eJ, s.M, lane);            // P Jm
+    if (lane < J) s.M[lane * J + lane] += 1.0;
+    wcopy<J>(s.Y1, s.A, J * J, lane);
+    wmat_solve<J, 1>(s.M, s.Y1, nullptr, lane);        // (I + P Jm)^-1 P
+    wmat_prod<J, 0>(s.eA, s.Y1, s.T, lane);
+    wmat_prod<J, 2>(s.T, s.eA, s.R1, lane);
+    wmat_add_sym<J>(s.R1, s.eC, lane);
+    wcopy<J>(s.A, s.R1, J * J, lane);
+}
+
+template <int J, class E>
+__device__ __forceinline__ void ric_load_elem(RicWarpSmem<J>& s, const E& src, bool to_acc,
+                                              int lane) {
+    double* dA = to_acc ? s.A : s.eA;
+    double* dC = to_acc ? s.C : s.eC;
+    double* dJ = to_acc ? s.Jm : s.eJ;
+    for (int e = lane; e < J * J; e += 32) {
+        dA[e] = src.A.a[e];
+        dC[e] = src.C.a[e];
+        dJ[e] = src.Jm.a[e];
+    }
+    __syncwarp();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_ric_combine_warp(const typename RiccatiOp<NB>::Elem* __restrict__ Ein,
+                   const int64_t* __restrict__ cb, const int64_t* __restrict__ ce,
+                   int64_t n_out, typename RiccatiOp<NB>::Elem* __restrict__ Eout) {
+    constexpr int J = 2 * NB;
+    __shared__ RicWarpSmem<J> s;
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (q >= n_out) return;
+    ric_load_elem<J>(s, Ein[cb[q]], true, lane);
+    for (int64_t r = cb[q] + 1; r < ce[q]; ++r) {
+        ric_load_elem<J>(s, Ein[r], false, lane);
+        ric_combine_w<J>(s, lane);
+    }
+    for (int e = lane; e < J * J; e += 32) {
+        Eout[q].A.a[e] = s.A[e];
+        Eout[q].C.a[e] = s.C[e];
+        Eout[q].Jm.a[e] = s.Jm[e];
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_ric_down_warp(const typename RiccatiOp<NB>::Elem* __restrict__ E,
+                const int64_t* __restrict__ cb, const int64_t* __restrict__ ce,
+                int64_t n_parent, const typename RiccatiOp<NB>::State* __restrict__ Sparent,
+                typename RiccatiOp<NB>::State* __restrict__ S) {
+    constexpr int J = 2 * NB;
+    __shared__ RicWarpSmem<J> s;
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (q >= n_parent) return;
+    wcopy<J>(s.A, Sparent[q].P.a, J * J, lane);
+    for (int64_t r = cb[q]; r < ce[q]; ++r) {
+        for (int e = lane; e < J * J; e += 32) S[r].P.a[e] = s.A[e];
+        ric_load_elem<J>(s, E[r], false, lane);
+        ric_apply_w<J>(s, lane);
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_ric_top_warp(const typename RiccatiOp<NB>::Elem* __restrict__ E,
+               const int64_t* __restrict__ tb, const int64_t* __restrict__ te, int n_seg,
+               typename RiccatiOp<NB>::State* __restrict__ S) {
+    constexpr int J = 2 * NB;
+    __shared__ RicWarpSmem<J> s;
+    const int g = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (g >= n_seg) return;
+    for (int e = lane; e < J * J; e += 32) s.A[e] = 0.0;
+    __syncwarp();
+    for (int64_t i = tb[g]; i < te[g]; ++i) {
+        for (int e = lane; e < J * J; e += 32) S[i].P.a[e] = s.A[e];
+        ric_load_elem<J>(s, E[i], false, lane);
+        ric_apply_w<J>(s, lane);
+    }
+}
+
+// Levels with up to this many groups run one warp per group; wider levels
+// (large batches) keep one thread per group, which packs 32 groups into each
+// FP64 warp instruction.
+constexpr int64_t RIC_WARP_TREE_MAX = 4096;
+
+template <int NB>
+inline void scan_combine(const RiccatiOp<NB>& op, const typename RiccatiOp<NB>::Elem* Ein,
+                         const int64_t* cb, const int64_t* ce, int64_t n,
+                         typename RiccatiOp<NB>::Elem* Eout, cudaStream_t st) {
+    if (n <= RIC_WARP_TREE_MAX)
+        k_ric_combine_warp<NB><<<(unsigned)n, 32, 0, st>>>(Ein, cb, ce, n, Eout);
+    else
+        scan_combine_threads(op, Ein, cb, ce, n, Eout, st);
+}
+
+template <int NB>
+inline void scan_down(const RiccatiOp<NB>& op, const typename RiccatiOp<NB>::Elem* E,
+                      const int64_t* cb, const int64_t* ce, int64_t n,
+                      const typename RiccatiOp<NB>::State* Sp,
+                      typename RiccatiOp<NB>::State* S, cudaStream_t st) {
+    if (n <= RIC_WARP_TREE_MAX)
+        k_ric_down_warp<NB><<<(unsigned)n, 32, 0, st>>>(E, cb, ce, n, Sp, S);
+    else
+        scan_down_threads(op, E, cb, ce, n, Sp, S, st);
+}
+
+template <int NB>
+inline void scan_top(const RiccatiOp<NB>& op, const typename RiccatiOp<NB>::Elem* E,
+                     const int64_t* tb, const int64_t* te, int n_seg,
+                     typename RiccatiOp<NB>::State* S, cudaStream_t st) {
+    if (n_seg <= RIC_WARP_TREE_MAX)
+        k_ric_top_warp<NB><<<(unsigned)n_seg, 32, 0, st>>>(E, tb, te, n_seg, S);
+    else
+        scan_top_threads(op, E, tb, te, n_seg, S, st);
+}
+
 // ---------------------------------------------------------- forward solve
 // Right-hand sides: the k columns of X (column-major with leading dimension
 // ldx, or the polynomial columns [1, t] when X is null) and y.

@@ -172,6 +172,57 @@ inline size_t scan_bytes(const ScanShape& sh) {
     return off;
 }
 
+// Lanes per warp for n thread-level work items: at most one warp per
+// sub-partition (608 on 152 SMs) -- more warps would share a sub-partition's
+// FP64 pipe -- with as few lanes per warp as that allows.
+inline int scan_lanes(int64_t n) {
+    int L = 1;
+    while (L < 32 && n > (int64_t)L * 608) L *= 2;
+    return L;
+}
+inline int scan_grid(int64_t n, int L, int th) { return div_up(div_up(n, L) * 32, th); }
+
+// Tree steps, one thread per group.  An Op may overload scan_combine /
+// scan_down / scan_top for its own type (found by argument-dependent lookup
+// when run_scan is instantiated) to run some levels another way.
+template <class Op>
+inline void scan_combine_threads(const Op& op, const typename Op::Elem* Ein,
+                                 const int64_t* cb, const int64_t* ce, int64_t n,
+                                 typename Op::Elem* Eout, cudaStream_t st) {
+    const int L = scan_lanes(n);
+    k_scan_combine<Op><<<scan_grid(n, L, 128), 128, 0, st>>>(op, Ein, cb, ce, n, Eout, L);
+}
+template <class Op>
+inline void scan_down_threads(const Op& op, const typename Op::Elem* E, const int64_t* cb,
+                              const int64_t* ce, int64_t n, const typename Op::State* Sp,
+                              typename Op::State* S, cudaStream_t st) {
+    const int L = scan_lanes(n);
+    k_scan_down<Op><<<scan_grid(n, L, 128), 128, 0, st>>>(op, E, cb, ce, n, Sp, S, L);
+}
+template <class Op>
+inline void scan_top_threads(const Op& op, const typename Op::Elem* E, const int64_t* tb,
+                             const int64_t* te, int n_seg, typename Op::State* S,
+                             cudaStream_t st) {
+    k_scan_top<Op><<<div_up(n_seg, 32), 32, 0, st>>>(op, E, tb, te, n_seg, S);
+}
+template <class Op>
+inline void scan_combine(const Op& op, const typename Op::Elem* Ein, const int64_t* cb,
+                         const int64_t* ce, int64_t n, typename Op::Elem* Eout,
+                         cudaStream_t st) {
+    scan_combine_threads(op, Ein, cb, ce, n, Eout, st);
+}
+template <class Op>
+inline void scan_down(const Op& op, const typename Op::Elem* E, const int64_t* cb,
+                      const int64_t* ce, int64_t n, const typename Op::State* Sp,
+                      typename Op::State* S, cudaStream_t st) {
+    scan_down_threads(op, E, cb, ce, n, Sp, S, st);
+}
+template <class Op>
+inline void scan_top(const Op& op, const typename Op::Elem* E, const int64_t* tb,
+                     const int64_t* te, int n_seg, typename Op::State* S, cudaStream_t st) {
+    scan_top_threads(op, E, tb, te, n_seg, S, st);
+}
+
 // Enqueue the whole scan on `st`; idx_dev holds the uploaded index arrays.
 // Returns the number of kernel launches.
 template <class Op>
@@ -190,44 +241,32 @@ inline int run_scan(const Op& op, const ScanShape& sh, const int64_t* idx_dev, c
         off += al((size_t)sh.count[l] * sizeof(S));
     }
     const int TH = 128;
-    // lanes per warp for n items: at most one warp per sub-partition (608 on
-    // 152 SMs) — more warps would share a sub-partition's FP64 pipe — with
-    // as few lanes per warp as that allows
-    auto lanes = [](int64_t n) {
-        int L = 1;
-        while (L < 32 && n > (int64_t)L * 608) L *= 2;
-        return L;
-    };
-    auto grid = [&](int64_t n, int L) { return div_up(div_up(n, L) * 32, TH); };
     int launches = 0;
     {
-        const int L = lanes(sh.count[0]);
-        k_scan_elem<Op><<<grid(sh.count[0], L), TH, 0, st>>>(op, sh.count[0], Ep[0], L);
+        const int L = scan_lanes(sh.count[0]);
+        k_scan_elem<Op><<<scan_grid(sh.count[0], L, TH), TH, 0, st>>>(op, sh.count[0], Ep[0],
+                                                                    L);
         ++launches;
     }
     for (int l = 1; l <= sh.levels; ++l) {
         const int64_t* cb = idx_dev + sh.child_off[l];
         const int64_t* ce = cb + sh.count[l];
-        const int L = lanes(sh.count[l]);
-        k_scan_combine<Op><<<grid(sh.count[l], L), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
-                                                               sh.count[l], Ep[l], L);
+        scan_combine(op, Ep[l - 1], cb, ce, sh.count[l], Ep[l], st);
         ++launches;
     }
     const int64_t* tb = idx_dev + sh.top_off;
-    k_scan_top<Op><<<div_up(sh.n_seg, 32), 32, 0, st>>>(op, Ep[sh.levels], tb, tb + sh.n_seg,
-                                                       sh.n_seg, Sp[sh.levels]);
+    scan_top(op, Ep[sh.levels], tb, tb + sh.n_seg, sh.n_seg, Sp[sh.levels], st);
     ++launches;
     for (int l = sh.levels; l >= 1; --l) {
         const int64_t* cb = idx_dev + sh.child_off[l];
         const int64_t* ce = cb + sh.count[l];
-        const int L = lanes(sh.count[l]);
-        k_scan_down<Op><<<grid(sh.count[l], L), TH, 0, st>>>(op, Ep[l - 1], cb, ce,
-                                                           sh.count[l], Sp[l], Sp[l - 1], L);
+        scan_down(op, Ep[l - 1], cb, ce, sh.count[l], Sp[l], Sp[l - 1], st);
         ++launches;
     }
     {
-        const int L = lanes(sh.count[0]);
-        k_scan_final<Op><<<grid(sh.count[0], L), TH, 0, st>>>(op, sh.count[0], Sp[0], L);
+        const int L = scan_lanes(sh.count[0]);
+        k_scan_final<Op><<<scan_grid(sh.count[0], L, TH), TH, 0, st>>>(op, sh.count[0], Sp[0],
+                                                                     L);
         ++launches;
     }
     return launches;
