@@ -218,8 +218,10 @@ __device__ __forceinline__ void write_best(const Best& b, int64_t p, int64_t n_p
     }
 }
 
+// MAXT: the largest block size the caller is launched with
+template <int MAXT = 256>
 __device__ __forceinline__ Best block_argmax(Best best) {
-    __shared__ Best sh[256];
+    __shared__ Best sh[MAXT];
     sh[threadIdx.x] = best;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -523,7 +525,7 @@ __device__ __forceinline__ void cell_pass2(const FoldGeom& g, const Node8<T>* __
 // first pass of one cell, the cells whose bound can still beat the block's
 // best are compacted into a shared queue, and the queue's second passes run
 // densely (a warp instruction costs the same however many lanes are active).
-template <typename T, int KC>
+template <typename T, int KC, int MAXT = 256>
 __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node8<T>* __restrict__ nodes,
                                                int n_D, double P, int64_t p,
                                                double* __restrict__ Q_out,
@@ -532,7 +534,7 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node8<T>
                                                double* __restrict__ dep_out,
                                                double* __restrict__ sig_out,
                                                double* __restrict__ lnp_out) {
-    __shared__ QCell<T> sh_q[256];
+    __shared__ QCell<T> sh_q[MAXT];
     __shared__ int sh_nq;
     __shared__ unsigned long long sh_best;
     if (bad_period(P, g)) {
@@ -599,7 +601,7 @@ __device__ __forceinline__ void fold_exact_one(const FoldGeom& g, const Node8<T>
     }
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (bc != LLONG_MAX) best = Best{bl, bc, (double)bD, sqrt((double)bs2)};
-    const Best b = block_argmax(best);
+    const Best b = block_argmax<MAXT>(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, g.t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
@@ -1165,6 +1167,7 @@ __device__ __forceinline__ void evaluate_queued_warp(const FoldGeom& g,
 // In its first round each warp evaluates its best-bounded cell with all its
 // lanes to seed the threshold.  The thresholds (best ln P, and its FP32
 // lower bound) are shared by the block through atomic maxima.
+template <int MAXT = 256>
 __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const ScreenGeom& sg,
                                                   const Node8<double>* __restrict__ nodes,
                                                   int n_D, double P, int64_t p,
@@ -1174,11 +1177,11 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                                                   double* __restrict__ dep_out,
                                                   double* __restrict__ sig_out,
                                                   double* __restrict__ lnp_out) {
-    __shared__ long long sh_qc[8][64];      // per-warp survivor queues
-    __shared__ int sh_qd[8][64];
+    __shared__ long long sh_qc[MAXT / 32][64];      // per-warp survivor queues
+    __shared__ int sh_qd[MAXT / 32][64];
     __shared__ unsigned long long sh_sbest; // best ln P evaluated (max key)
     __shared__ unsigned sh_bfk;             // its FP32 lower bound (float key)
-    __shared__ Best sh_tb[256];             // each thread's best evaluated cell (kept
+    __shared__ Best sh_tb[MAXT];            // each thread's best evaluated cell (kept
                                             // out of registers during the screen)
     if (bad_period(P, g)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
@@ -1192,7 +1195,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     if (threadIdx.x == 0) sh_sp = screen_period(g, sg, P, n_phi);
     __syncthreads();
     if (!sh_sp.on) {
-        fold_exact_one<double, 8>(g, nodes, n_D, P, p, Q_out, T0_out, Didx_out, dep_out,
+        fold_exact_one<double, 8, MAXT>(g, nodes, n_D, P, p, Q_out, T0_out, Didx_out, dep_out,
                                   sig_out, lnp_out);
         return;
     }
@@ -1333,7 +1336,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     __syncthreads();
     Best best = sh_tb[threadIdx.x];
     if (best.cell != LLONG_MAX) best.sigma = sqrt(best.sigma);   // held sigma^2
-    const Best b = block_argmax(best);
+    const Best b = block_argmax<MAXT>(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, g.t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
@@ -1343,7 +1346,10 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
 #define NU_SCREEN_MIN_BLOCKS 3
 #endif
 
-__global__ void __launch_bounds__(256, NU_SCREEN_MIN_BLOCKS)
+// 256-thread blocks: 3 per SM (about 80 registers); 128-thread blocks: 7 per
+// SM (72 registers, no spills; the shared arrays are sized for 4 warps).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 7 : NU_SCREEN_MIN_BLOCKS)
 k_fold_screened(FoldGeom g, ScreenGeom sg, const Node8<double>* __restrict__ nodes, int n_D,
                 const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
                 double* __restrict__ T0_out, int* __restrict__ Didx_out,
@@ -1351,8 +1357,8 @@ k_fold_screened(FoldGeom g, ScreenGeom sg, const Node8<double>* __restrict__ nod
                 double* __restrict__ lnp_out) {
     const int64_t p = blockIdx.x;
     if (p >= n_P) return;
-    fold_screened_one(g, sg, nodes, n_D, periods[p], p, Q_out, T0_out, Didx_out, dep_out,
-                      sig_out, lnp_out);
+    fold_screened_one<MAXT>(g, sg, nodes, n_D, periods[p], p, Q_out, T0_out, Didx_out,
+                            dep_out, sig_out, lnp_out);
 }
 
 // ---------------------------------------- slot path (mixed, regular grids)
@@ -1981,10 +1987,14 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             // on an SM (registers and the 37 KB of queues) and each period has
             // half the warps to seed; with few, 8-warp blocks keep the GPU full
             // (C2, 20 000 periods: 15.4 ms at 128 threads, 16.5 ms at 256).
-            const int fold_threads = n_P >= 8192 ? 128 : 256;
-            k_fold_screened<<<(unsigned)n_P, fold_threads, 0, st>>>(
-                g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
-                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+            if (n_P >= 8192)
+                k_fold_screened<128><<<(unsigned)n_P, 128, 0, st>>>(
+                    g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                    D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+            else
+                k_fold_screened<256><<<(unsigned)n_P, 256, 0, st>>>(
+                    g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
+                    D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
             launched += 7;
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
