@@ -1346,10 +1346,10 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
 #define NU_SCREEN_MIN_BLOCKS 3
 #endif
 
-// 256-thread blocks: 3 per SM (about 80 registers); 128-thread blocks: 7 per
-// SM (72 registers, no spills; the shared arrays are sized for 4 warps).
+// 256-thread blocks: 3 per SM (about 80 registers); 64-thread blocks: 14 per
+// SM (72 registers, no spills; the shared arrays are sized for 2 warps).
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT, MAXT <= 128 ? 7 : NU_SCREEN_MIN_BLOCKS)
+__global__ void __launch_bounds__(MAXT, MAXT <= 64 ? 14 : NU_SCREEN_MIN_BLOCKS)
 k_fold_screened(FoldGeom g, ScreenGeom sg, const Node8<double>* __restrict__ nodes, int n_D,
                 const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
                 double* __restrict__ T0_out, int* __restrict__ Didx_out,
@@ -1983,12 +1983,12 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
                 t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, lslot, n_slots, slot_of,
                 vpair);
             k_lwin<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(lslot, n_slots * n_D, lwin);
-            // One block per period.  With many periods, 4-warp blocks: six fit
-            // on an SM (registers and the 37 KB of queues) and each period has
-            // half the warps to seed; with few, 8-warp blocks keep the GPU full
-            // (C2, 20 000 periods: 15.4 ms at 128 threads, 16.5 ms at 256).
+            // One block per period.  With many periods, 2-warp blocks: 14 fit
+            // on an SM (28 warps) and each period has 2 warps to seed; with
+            // few, 8-warp blocks keep the GPU full (C2, 20 000 periods: 16.5 ms
+            // at 256 threads, 14.0 at 128 (7 per SM), 13.6 at 64).
             if (n_P >= 8192)
-                k_fold_screened<128><<<(unsigned)n_P, 128, 0, st>>>(
+                k_fold_screened<64><<<(unsigned)n_P, 64, 0, st>>>(
                     g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                     D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
             else
