@@ -1443,7 +1443,7 @@ struct SCell {
 // pass of its cells and queues those the bound keeps in its own shared
 // queue; 32 queued cells get their second passes, one per lane, from that
 // warp alone (no block barriers until the final argmax).
-template <int KC>
+template <int KC, int MAXT = 256>
 __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ rec,
                                                int64_t n_slots, int n_D, double dt,
                                                double t_ref, double t_last, double P, int64_t p,
@@ -1453,7 +1453,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                                                double* __restrict__ dep_out,
                                                double* __restrict__ sig_out,
                                                double* __restrict__ lnp_out) {
-    __shared__ SCell sh_q[8][64];
+    __shared__ SCell sh_q[MAXT / 32][64];
     __shared__ unsigned int sh_best;
     FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
     if (bad_period(P, gg)) {
@@ -1549,7 +1549,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     if (lane < nq) pass2(q[lane]);
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (bc != LLONG_MAX) best = Best{(double)bl, bc, (double)bD, sqrt((double)bs2)};
-    const Best b = block_argmax(best);
+    const Best b = block_argmax<MAXT>(best);
     if (threadIdx.x == 0)
         write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
@@ -1578,8 +1578,19 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
 // exact FP64-epoch path with FP64 values; 1: exact path, FP32 values;
 // 2: slot path (mixed precision, regular grids).  Items of curves that do not
 // use this kernel's path are skipped.
-template <int KIND>
-__global__ void __launch_bounds__(256)
+// Resident blocks per SM the registers are sized for, by path and block size.
+// The FP64 batch kernel carries the work-item loop besides the screen: at 80
+// registers it spills, at 96 (10 x 64 threads) it does not; slots as the
+// single-curve kernel (64 registers at any size).
+template <int KIND, int MAXT>
+struct BatchBlocks {
+    static constexpr int value =
+        KIND == 0 ? (MAXT <= 64 ? 10 : (MAXT <= 128 ? 5 : NU_SCREEN_MIN_BLOCKS))
+                  : (KIND == 2 ? NU_SLOTS_MIN_BLOCKS * 256 / MAXT : 1);
+};
+
+template <int KIND, int MAXT>
+__global__ void __launch_bounds__(MAXT, BatchBlocks<KIND, MAXT>::value)
 k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restrict__ t,
              const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
              const ulonglong2* __restrict__ vpair, const ScreenRec* __restrict__ srec,
@@ -1604,7 +1615,7 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
         if ((KIND == 2) != (fs.use_slots != 0)) continue;
         const int64_t o = (int64_t)g * n_P + p;
         if (KIND == 2) {
-            fold_slots_one<8>(rec + fs.rec_off, fs.n_slots, n_D, dt, fs.t_ref, fs.t_last,
+            fold_slots_one<8, MAXT>(rec + fs.rec_off, fs.n_slots, n_D, dt, fs.t_ref, fs.t_last,
                               periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                               lnp_out);
         } else {
@@ -1614,12 +1625,12 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
                 const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off,
                                     srec + fs.srec_off, lwin + fs.srec_off, fs.n_slots,
                                     reg + 2 * g, fs.screen};
-                fold_screened_one(gg, sg, (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
+                fold_screened_one<MAXT>(gg, sg, (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
                                   periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                                   lnp_out);
             }
             else
-                fold_exact_one<float, 8>(gg, (const Node8<float>*)nodes + fs.s_off * n_D, n_D,
+                fold_exact_one<float, 8, MAXT>(gg, (const Node8<float>*)nodes + fs.s_off * n_D, n_D,
                                          periods[p], o, Q_out, T0_out, Didx_out, dep_out,
                                          sig_out, lnp_out);
         }
@@ -1844,23 +1855,31 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
         fp64 ? (const ScreenRec*)((const char*)fs.nodes + L.off_screen) : nullptr;
     const ulonglong2* vpair =
         fp64 ? (const ulonglong2*)((const char*)fs.nodes + L.off_vpos) : nullptr;
+    // the kernel instance whose shared arrays and register budget match the
+    // block size (64, 128 or 256 threads)
+#define NU_FB(KIND_, MAXT_, CTR_)                                                          \
+    k_fold_batch<KIND_, MAXT_><<<grid, MAXT_, 0, st>>>(                                  \
+        segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket,  \
+        fs.rec, n_D, dt, gap_factor, periods, n_P, CTR_, Q, T0, Didx, dep, sig, lnp)
+#define NU_FB_SIZE(KIND_, CTR_)                                                            \
+    do {                                                                                   \
+        if (threads <= 64) NU_FB(KIND_, 64, CTR_);                                         \
+        else if (threads <= 128) NU_FB(KIND_, 128, CTR_);                                  \
+        else NU_FB(KIND_, 256, CTR_);                                                      \
+    } while (0)
     if (fb.any_exact) {
         if (fp64)
-            k_fold_batch<0><<<grid, threads, 0, st>>>(
-                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket, fs.rec,
-                n_D, dt, gap_factor, periods, n_P, counter, Q, T0, Didx, dep, sig, lnp);
+            NU_FB_SIZE(0, counter);
         else
-            k_fold_batch<1><<<grid, threads, 0, st>>>(
-                segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket, fs.rec,
-                n_D, dt, gap_factor, periods, n_P, counter, Q, T0, Didx, dep, sig, lnp);
+            NU_FB_SIZE(1, counter);
         ++launched;
     }
     if (fb.any_slots) {
-        k_fold_batch<2><<<grid, threads, 0, st>>>(
-            segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket, fs.rec, n_D,
-            dt, gap_factor, periods, n_P, counter + 1, Q, T0, Didx, dep, sig, lnp);
+        NU_FB_SIZE(2, counter + 1);
         ++launched;
     }
+#undef NU_FB_SIZE
+#undef NU_FB
     return launched;
 }
 
