@@ -1554,12 +1554,18 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
+#ifndef NU_SLOTS_SMALL
+#define NU_SLOTS_SMALL 128         // block size of the mixed fold on large grids
+#endif
+#ifndef NU_SLOTS_SMALL_FROM
+#define NU_SLOTS_SMALL_FROM 8192   // periods from which it is used
+#endif
 #ifndef NU_SLOTS_MIN_BLOCKS
 #define NU_SLOTS_MIN_BLOCKS 4
 #endif
 
-template <int KC>
-__global__ void __launch_bounds__(256, NU_SLOTS_MIN_BLOCKS)
+template <int KC, int MAXT>
+__global__ void __launch_bounds__(MAXT, NU_SLOTS_MIN_BLOCKS * 256 / MAXT)
 k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, double dt,
              double t_ref, double t_last, const double* __restrict__ periods, int64_t n_P,
              double* __restrict__ Q_out, double* __restrict__ T0_out,
@@ -1567,7 +1573,7 @@ k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, dou
              double* __restrict__ sig_out, double* __restrict__ lnp_out) {
     const int64_t p = blockIdx.x;
     if (p >= n_P) return;
-    fold_slots_one<KC>(rec, n_slots, n_D, dt, t_ref, t_last, periods[p], p, Q_out, T0_out,
+    fold_slots_one<KC, MAXT>(rec, n_slots, n_D, dt, t_ref, t_last, periods[p], p, Q_out, T0_out,
                        Didx_out, dep_out, sig_out, lnp_out);
 }
 
@@ -1962,10 +1968,14 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
         k_slot_fill<<<div_up(ngrid, 256), 256, 0, st>>>(
             (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
             n_t0, n_D, n_slots, rec);
-        k_fold_slots<8><<<(unsigned)n_P, 256, 0, st>>>(rec, n_slots, n_D, phase_step, t_ref,
-                                                      t_last, periods_dev, n_P, Q_dev, T0_dev,
-                                                      D_idx_dev, depth_out_dev, sigma_out_dev,
-                                                      lnP_dev);
+        if (n_P >= NU_SLOTS_SMALL_FROM)
+            k_fold_slots<8, NU_SLOTS_SMALL><<<(unsigned)n_P, NU_SLOTS_SMALL, 0, st>>>(
+                rec, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+        else
+            k_fold_slots<8, 256><<<(unsigned)n_P, 256, 0, st>>>(
+                rec, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev, T0_dev,
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         launched += 3;
     } else {
         k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
