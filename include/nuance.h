@@ -255,10 +255,9 @@ nu_status nu_rotation_alias_filter(const double* periods_dev, int64_t n_P, doubl
  *   depth_dev, var_dev, dlnl_dev, snr_dev  (n_cand) FP64 outputs
  * A candidate with P or T0 not finite, D_idx outside [0, n_D), 2 D > P
  * (windows would overlap), no sample in any window, or a template in the
- * span of X gets NaN in all four outputs.  Always FP64.  One thread walks a
- * candidate's windows; the gaps between them advance in blocks of 32
- * samples, so a candidate costs O(samples in its windows + n/32 + 64 per
- * window).  Enqueued on `stream`; no synchronisation.
+ * span of X gets NaN in all four outputs.  Always FP64.  One warp per
+ * candidate, its lanes over 32 segments of the samples; gaps between windows
+ * advance in blocks of 32 samples.  Enqueued on `stream`; no synchronisation.
  * Errors: NU_EINVAL (null pointer, n_cand < 1, n_D < 1, a duration not finite
  * and > 0, bad template or template parameters), NU_ENOMEM, NU_ECUDA. */
 nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev, const double* T0_dev,
