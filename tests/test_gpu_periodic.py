@@ -196,3 +196,38 @@ def test_fold_fp64_screen_hard_cases(offset, regular):
                                       FP64_TOL, FP64_TOL, periodic.fold_period)
     print(f"fp64 screen hard cases offset={offset} regular={regular}: lnP err {wl:.2e}, "
           f"Q err {wq:.2e}, ties {differ}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_period_grid_kernels(precision):
+    """Grids of 8192 periods or more run the small-block fold instances (FP64:
+    64 threads, 14 blocks per SM; mixed: 128 threads).  On 9000 periods they
+    must give what the 256-thread instances give on the two halves of the grid,
+    and the oracle's results at sampled periods."""
+    lc = synth.small_curve(n=2200, seed=3, p_rot=1.3, sigma=4e-3, sigma_w=1e-3,
+                           inject=(3e-3, 1.0 / 24.0, 0.41))
+    Ds = np.array([0.03, 1.0 / 24.0, 0.055])
+    periods = np.linspace(0.12, 3.0, 9000)
+    dt = periodic.median_spacing(lc.t)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    f = api.nu_gp_factor(cu(lc.t), cu(lc.diag_var), lc.terms, cu(lc.X), cu(lc.y))
+    d, v, l = api.nu_linear_search(f, cu(lc.t), Ds, precision=precision)
+    whole = api.nu_periodic_search(cu(lc.t), Ds, d, v, l, cu(periods), precision=precision,
+                                   phase_step=dt)
+    halves = [api.nu_periodic_search(cu(lc.t), Ds, d, v, l, cu(periods[s]),
+                                     precision=precision, phase_step=dt)
+              for s in (slice(0, 4500), slice(4500, 9000))]
+    for key in ("Q", "T0", "D_idx", "lnP", "depth", "sigma"):
+        a = whole[key].cpu().numpy()
+        b = np.concatenate([h[key].cpu().numpy() for h in halves])
+        assert np.array_equal(a, b, equal_nan=True), key
+    if precision == "fp64":
+        sel = np.arange(0, 9000, 225)
+        ora_lin = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t, Ds)
+        ora = periodic.periodic_search(lc.t, ora_lin["depth"], ora_lin["var"], ora_lin["dlnl"],
+                                       periods[sel], dt)
+        gpu = {k: whole[k].cpu().numpy()[sel] for k in ("Q", "T0", "D_idx", "lnP")}
+        wl, wq, _ = periodic_compare(gpu, ora, lc.t, ora_lin["depth"], ora_lin["var"],
+                                     ora_lin["dlnl"], periods[sel], dt, FP64_TOL, FP64_TOL,
+                                     periodic.fold_period)
+        assert wl <= FP64_TOL and wq <= FP64_TOL
