@@ -1517,6 +1517,8 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                 SlotPass1 p1;
                 p1.init();
                 int kmax = 0;
+                // two epochs' record loads in flight (C3: 16.6 -> 16.1 ms)
+#pragma unroll 2
                 for (unsigned long long u = u0; u <= ulast; u += ustep, ++kmax)
                     p1.add(slot_event(rd, u));
                 const unsigned int kb = sh_best;
