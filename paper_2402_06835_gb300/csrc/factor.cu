@@ -207,9 +207,19 @@ __global__ void k_seg_scalars(const double* __restrict__ chi_terms,
 }
 
 // ------------------------------------------------------------- FP32 copies
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+// Up to six arrays in one launch: element i of the concatenation.
+struct F32Copies {
+    const double* src[6];
+    float* dst[6];
+    int64_t end[6];          // running element counts
+};
+__global__ void k_to_f32(F32Copies c, int64_t total) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
+    if (i >= total) return;
+    int a = 0;
+    while (i >= c.end[a]) ++a;
+    const int64_t j = i - (a > 0 ? c.end[a - 1] : 0);
+    c.dst[a][j] = (float)c.src[a][j];
 }
 
 // ------------------------------------------------------------------ plan
@@ -379,11 +389,16 @@ static int launch_factor_nb(const FactorPlan& p, const FactorBuffers& b, char* w
                                   n * (int64_t)k};
         const double* src[6] = {b.F, b.kg, b.invD, b.G, b.z0, b.Zt};
         float* dst[6] = {b.F32, b.kg32, b.invD32, b.G32, b.z032, b.Zt32};
-        for (int a = 0; a < 6; ++a)
-            if (sizes[a] > 0) {
-                k_to_f32<<<div_up(sizes[a], 256), 256, 0, st>>>(src[a], dst[a], sizes[a]);
-                ++launched;
-            }
+        F32Copies c;
+        int64_t total = 0;
+        for (int a = 0; a < 6; ++a) {
+            c.src[a] = src[a];
+            c.dst[a] = dst[a];
+            total += sizes[a];
+            c.end[a] = total;
+        }
+        k_to_f32<<<div_up(total, 256), 256, 0, st>>>(c, total);
+        ++launched;
     }
     return launched;
 }

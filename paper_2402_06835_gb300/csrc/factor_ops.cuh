@@ -909,4 +909,241 @@ struct FutureOp {
     }
 };
 
+// ------------------------------- affine and future-information trees, warps
+// The same one-warp-per-group scheme for the other three scans.  Forward and
+// backward solves share one element layout (Phi J x J, beta NRMAX x J; the
+// state NRMAX x J), combined as P = Phi_j Phi_i, beta_i <- Phi_j beta_i +
+// beta_j and applied as s <- Phi s + beta; the future information's element
+// (Psi, Gam) combines as Psi_i Psi_j, Psi_j^T Gam_i Psi_j + Gam_j and applies
+// to G as Psi^T G Psi + Gam.  Each entry follows the thread code's order.
+template <int J>
+struct AffWarpSmem {
+    double P[J * J], b[NRMAX * J];        // accumulated element, or the state in b
+    double eP[J * J], eb[NRMAX * J];      // the element being applied
+    double R[J * J], rb[NRMAX * J];
+};
+
+template <int J>
+__device__ __forceinline__ void aff_load(double* P, double* b, const double* src, int lane) {
+    for (int e = lane; e < J * J; e += 32) P[e] = src[e];
+    for (int e = lane; e < NRMAX * J; e += 32) b[e] = src[J * J + e];
+    __syncwarp();
+}
+
+// acc (P, b) <- combine(acc, e): b rows r < nr
+template <int J>
+__device__ __forceinline__ void aff_combine_w(AffWarpSmem<J>& s, int nr, int lane) {
+    wmat_prod<J, 0>(s.eP, s.P, s.R, lane);
+    for (int e = lane; e < nr * J; e += 32) {
+        const int r = e / J, a = e - r * J;
+        double v = s.eb[r * J + a];
+#pragma unroll
+        for (int q = 0; q < J; ++q) v = fma(s.eP[a * J + q], s.b[r * J + q], v);
+        s.rb[e] = v;
+    }
+    __syncwarp();
+    for (int e = lane; e < J * J; e += 32) s.P[e] = s.R[e];
+    for (int e = lane; e < nr * J; e += 32) s.b[e] = s.rb[e];
+    __syncwarp();
+}
+
+// state (in b) <- apply(e, state)
+template <int J>
+__device__ __forceinline__ void aff_apply_w(AffWarpSmem<J>& s, int nr, int lane) {
+    for (int e = lane; e < nr * J; e += 32) {
+        const int r = e / J, a = e - r * J;
+        double v = s.eb[r * J + a];
+#pragma unroll
+        for (int q = 0; q < J; ++q) v = fma(s.eP[a * J + q], s.b[r * J + q], v);
+        s.rb[e] = v;
+    }
+    __syncwarp();
+    for (int e = lane; e < nr * J; e += 32) s.b[e] = s.rb[e];
+    __syncwarp();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_aff_combine_warp(const double* __restrict__ Ein, const int64_t* __restrict__ cb,
+                   const int64_t* __restrict__ ce, int64_t n_out, double* __restrict__ Eout,
+                   int nr) {
+    constexpr int J = 2 * NB, ES = J * J + NRMAX * J;
+    __shared__ AffWarpSmem<J> s;
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (q >= n_out) return;
+    aff_load<J>(s.P, s.b, Ein + cb[q] * ES, lane);
+    for (int64_t r = cb[q] + 1; r < ce[q]; ++r) {
+        aff_load<J>(s.eP, s.eb, Ein + r * ES, lane);
+        aff_combine_w<J>(s, nr, lane);
+    }
+    double* out = Eout + q * ES;
+    for (int e = lane; e < J * J; e += 32) out[e] = s.P[e];
+    for (int e = lane; e < NRMAX * J; e += 32) out[J * J + e] = e < nr * J ? s.b[e] : 0.0;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_aff_down_warp(const double* __restrict__ E, const int64_t* __restrict__ cb,
+                const int64_t* __restrict__ ce, int64_t n_parent,
+                const double* __restrict__ Sparent, double* __restrict__ S, int nr) {
+    constexpr int J = 2 * NB, ES = J * J + NRMAX * J, SS = NRMAX * J;
+    __shared__ AffWarpSmem<J> s;
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (q >= n_parent) return;
+    for (int e = lane; e < SS; e += 32) s.b[e] = Sparent[q * SS + e];
+    __syncwarp();
+    for (int64_t r = cb[q]; r < ce[q]; ++r) {
+        for (int e = lane; e < SS; e += 32) S[r * SS + e] = s.b[e];
+        aff_load<J>(s.eP, s.eb, E + r * ES, lane);
+        aff_apply_w<J>(s, nr, lane);
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_aff_top_warp(const double* __restrict__ E, const int64_t* __restrict__ tb,
+               const int64_t* __restrict__ te, int n_seg, double* __restrict__ S, int nr) {
+    constexpr int J = 2 * NB, ES = J * J + NRMAX * J, SS = NRMAX * J;
+    __shared__ AffWarpSmem<J> s;
+    const int g = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (g >= n_seg) return;
+    for (int e = lane; e < SS; e += 32) s.b[e] = 0.0;
+    __syncwarp();
+    for (int64_t i = tb[g]; i < te[g]; ++i) {
+        for (int e = lane; e < SS; e += 32) S[i * SS + e] = s.b[e];
+        aff_load<J>(s.eP, s.eb, E + i * ES, lane);
+        aff_apply_w<J>(s, nr, lane);
+    }
+}
+
+template <int J>
+struct FutWarpSmem {
+    double Psi[J * J], Gam[J * J];        // accumulated element; the state G in Gam
+    double ePsi[J * J], eGam[J * J];
+    double T[J * J], R1[J * J], R2[J * J];
+};
+
+template <int J>
+__device__ __forceinline__ void fut_load(double* Psi, double* Gam, const double* src, int lane) {
+    for (int e = lane; e < J * J; e += 32) {
+        Psi[e] = src[e];
+        Gam[e] = src[J * J + e];
+    }
+    __syncwarp();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_fut_combine_warp(const double* __restrict__ Ein, const int64_t* __restrict__ cb,
+                   const int64_t* __restrict__ ce, int64_t n_out, double* __restrict__ Eout) {
+    constexpr int J = 2 * NB, ES = 2 * J * J;
+    __shared__ FutWarpSmem<J> s;
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (q >= n_out) return;
+    fut_load<J>(s.Psi, s.Gam, Ein + cb[q] * ES, lane);
+    for (int64_t r = cb[q] + 1; r < ce[q]; ++r) {
+        fut_load<J>(s.ePsi, s.eGam, Ein + r * ES, lane);
+        wmat_prod<J, 0>(s.Psi, s.ePsi, s.R1, lane);          // Psi_i Psi_j
+        wmat_prod<J, 0>(s.Gam, s.ePsi, s.T, lane);           // Gam_i Psi_j
+        wmat_prod<J, 1>(s.ePsi, s.T, s.R2, lane);            // Psi_j^T ...
+        wmat_add_sym<J>(s.R2, s.eGam, lane);
+        wcopy<J>(s.Psi, s.R1, J * J, lane);
+        wcopy<J>(s.Gam, s.R2, J * J, lane);
+    }
+    double* out = Eout + q * ES;
+    for (int e = lane; e < J * J; e += 32) {
+        out[e] = s.Psi[e];
+        out[J * J + e] = s.Gam[e];
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void fut_apply_w(FutWarpSmem<J>& s, int lane) {
+    wmat_prod<J, 0>(s.Gam, s.ePsi, s.T, lane);               // G Psi
+    wmat_prod<J, 1>(s.ePsi, s.T, s.R1, lane);                // Psi^T ...
+    wmat_add_sym<J>(s.R1, s.eGam, lane);
+    wcopy<J>(s.Gam, s.R1, J * J, lane);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_fut_down_warp(const double* __restrict__ E, const int64_t* __restrict__ cb,
+                const int64_t* __restrict__ ce, int64_t n_parent,
+                const double* __restrict__ Sparent, double* __restrict__ S) {
+    constexpr int J = 2 * NB, ES = 2 * J * J;
+    __shared__ FutWarpSmem<J> s;
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (q >= n_parent) return;
+    wcopy<J>(s.Gam, Sparent + q * J * J, J * J, lane);
+    for (int64_t r = cb[q]; r < ce[q]; ++r) {
+        for (int e = lane; e < J * J; e += 32) S[r * J * J + e] = s.Gam[e];
+        fut_load<J>(s.ePsi, s.eGam, E + r * ES, lane);
+        fut_apply_w<J>(s, lane);
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_fut_top_warp(const double* __restrict__ E, const int64_t* __restrict__ tb,
+               const int64_t* __restrict__ te, int n_seg, double* __restrict__ S) {
+    constexpr int J = 2 * NB, ES = 2 * J * J;
+    __shared__ FutWarpSmem<J> s;
+    const int g = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (g >= n_seg) return;
+    for (int e = lane; e < J * J; e += 32) s.Gam[e] = 0.0;
+    __syncwarp();
+    for (int64_t i = tb[g]; i < te[g]; ++i) {
+        for (int e = lane; e < J * J; e += 32) S[i * J * J + e] = s.Gam[e];
+        fut_load<J>(s.ePsi, s.eGam, E + i * ES, lane);
+        fut_apply_w<J>(s, lane);
+    }
+}
+
+// Narrow levels of these scans run one warp per group (as the Riccati tree).
+#define NU_WARP_TREE_OVERLOADS(OP, COMBINE, DOWN, TOP, ...)                               \
+    template <int NB>                                                                      \
+    inline void scan_combine(const OP<NB>& op, const typename OP<NB>::Elem* Ein,           \
+                             const int64_t* cb, const int64_t* ce, int64_t n,              \
+                             typename OP<NB>::Elem* Eout, cudaStream_t st) {               \
+        if (n <= RIC_WARP_TREE_MAX)                                                        \
+            COMBINE<NB><<<(unsigned)n, 32, 0, st>>>((const double*)Ein, cb, ce, n,          \
+                                                     (double*)Eout __VA_ARGS__);                 \
+        else                                                                               \
+            scan_combine_threads(op, Ein, cb, ce, n, Eout, st);                            \
+    }                                                                                      \
+    template <int NB>                                                                      \
+    inline void scan_down(const OP<NB>& op, const typename OP<NB>::Elem* E,                \
+                          const int64_t* cb, const int64_t* ce, int64_t n,                 \
+                          const typename OP<NB>::State* Sp, typename OP<NB>::State* S,     \
+                          cudaStream_t st) {                                               \
+        if (n <= RIC_WARP_TREE_MAX)                                                        \
+            DOWN<NB><<<(unsigned)n, 32, 0, st>>>((const double*)E, cb, ce, n,               \
+                                                  (const double*)Sp, (double*)S __VA_ARGS__);    \
+        else                                                                               \
+            scan_down_threads(op, E, cb, ce, n, Sp, S, st);                                \
+    }                                                                                      \
+    template <int NB>                                                                      \
+    inline void scan_top(const OP<NB>& op, const typename OP<NB>::Elem* E,                 \
+                         const int64_t* tb, const int64_t* te, int n_seg,                  \
+                         typename OP<NB>::State* S, cudaStream_t st) {                     \
+        if (n_seg <= RIC_WARP_TREE_MAX)                                                    \
+            TOP<NB><<<(unsigned)n_seg, 32, 0, st>>>((const double*)E, tb, te, n_seg,        \
+                                                     (double*)S __VA_ARGS__);                    \
+        else                                                                               \
+            scan_top_threads(op, E, tb, te, n_seg, S, st);                                 \
+    }
+
+NU_WARP_TREE_OVERLOADS(ForwardOp, k_aff_combine_warp, k_aff_down_warp, k_aff_top_warp,
+                       , op.k + 1)
+NU_WARP_TREE_OVERLOADS(BackwardOp, k_aff_combine_warp, k_aff_down_warp, k_aff_top_warp,
+                       , op.nr)
+NU_WARP_TREE_OVERLOADS(FutureOp, k_fut_combine_warp, k_fut_down_warp, k_fut_top_warp, )
+#undef NU_WARP_TREE_OVERLOADS
+
 }  // namespace nu
