@@ -14,12 +14,12 @@ namespace nu {
 // 2 G element operations per tree level; the GPU runs 608 sub-partitions x
 // 32 lanes of such chains at once.  While the level-0 chunks fit in about two
 // such waves, short chunks and small groups shorten the chain (on a 19 440-
-// sample curve B = 8, G = 4 takes the factor from 2.63 to 1.65 ms); a large
-// batch has chunks to spare, and long chunks keep the tree's extra work and
-// its element memory small.
+// sample curve B = 4, G = 4 with warp-level trees); a large batch has chunks
+// to spare, and long chunks keep the tree's extra work and its element memory
+// small.
 constexpr int SCAN_TOP = 16;
 inline int scan_chunk_len(int64_t n_total) {
-    int B = 8;
+    int B = 4;
     while (B < 32 && n_total > (int64_t)B * 2 * 608 * 32) B *= 2;
     return B;
 }
