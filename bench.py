@@ -42,7 +42,7 @@ FOLD_FLOPS_PER_VISIT = 55.0    # 25 in pass 1 + 30 in pass 2 (one log per visit)
 # DRAM bytes (read + write) of one fold launch on the bench workload (sector_19440,
 # FP64), from an ncu capture of the kernel as it stands
 # (profiles/k_fold_screened_sector_19440.md); other workloads report None
-FOLD_TRAFFIC_BYTES = {"sector_19440": 26994176}
+FOLD_TRAFFIC_BYTES = {"sector_19440": 27046912}
 FLUSH_BYTES = 512 << 20        # > 129 MB L2
 
 
@@ -352,8 +352,9 @@ def blas_threads():
 def profile_case(args):
     """Small cases for ncu: the sector light curve (19 440 epochs with the
     mid-sector gap, 10 durations) through nu_gp_factor and nu_linear_search,
-    then one nu_periodic_search per precision over 600 of its 20 000 periods
-    (every 33rd, 0.2-13.5 d)."""
+    then one nu_periodic_search per precision over 10 000 of its 20 000
+    periods (every 2nd, 0.2-13.5 d: enough periods for the folds' launch shapes
+    of the full grid)."""
     import torch
     from paper_2402_06835_gb300 import api
     w = synth.sector_19440()
@@ -361,7 +362,7 @@ def profile_case(args):
     cu = lambda a: torch.as_tensor(a, device="cuda")
     t = cu(lc.t)
     f = api.nu_gp_factor(t, cu(lc.diag_var), lc.terms, cu(lc.X), cu(lc.y))
-    per = cu(np.ascontiguousarray(w.periods[::33]))
+    per = cu(np.ascontiguousarray(w.periods[::2]))
     for prec in ("mixed", "fp64"):
         d, v, l = api.nu_linear_search(f, t, w.durations, precision=prec)
         r = api.nu_periodic_search(t, w.durations, d, v, l, per, precision=prec)
