@@ -46,6 +46,9 @@ CASES = {
     "sho_critical": dict(terms=[(gp.SHO, (5e-3, 30.0, 0.5))]),
     "sho_q45": dict(terms=[(gp.SHO, (8e-3, 40.0, 45.0))]),
     "white_only": dict(terms=[]),
+    # four 2x2 blocks: the largest state (J = 8)
+    "two_rotations": dict(terms=[(gp.ROTATION, (1e-2, 0.5, 5.0, 0.0, 0.5)),
+                                 (gp.ROTATION, (5e-3, 2.3, 3.0, 0.5, 0.3))]),
 }
 
 

@@ -4,7 +4,7 @@ oracle's dense and semiseparable fits."""
 import numpy as np
 import pytest
 
-from oracle import linear, periodic, refine, semisep
+from oracle import gp, linear, periodic, refine, semisep
 from paper_2402_06835_gb300 import synth
 from parity import FP64_TOL
 
@@ -151,3 +151,23 @@ def test_refine_rejects_bad_arguments():
         api.nu_periodic_refine(f, P[:0], T0[:0], J[:0], [0.05])
     with pytest.raises(api.NuanceError):
         api.nu_periodic_refine(f, P, T0, J, [])
+
+
+@pytest.mark.parametrize("terms_case", ["sho", "rotation_exp", "two_rotations"])
+def test_refine_other_state_sizes(terms_case):
+    """State dimensions J = 2, 6 and 8 (the segment maps, the block tables and
+    the warp walk for every block count)."""
+    terms = {"sho": [(gp.SHO, (5e-3, 30.0, 2.0))],
+             "rotation_exp": [(gp.ROTATION, (1e-2, 0.5, 5.0, 0.0, 0.5)), (gp.EXP, (2e-3, 0.08))],
+             "two_rotations": [(gp.ROTATION, (1e-2, 0.5, 5.0, 0.0, 0.5)),
+                               (gp.ROTATION, (5e-3, 2.3, 3.0, 0.5, 0.3))]}[terms_case]
+    lc = synth.small_curve(n=1500, seed=31, gap=200)
+    Ds = np.array([0.03, 0.06])
+    model = linear.DenseModel(lc.t, lc.y, lc.diag_var, terms, lc.X)
+    cands = candidate_set(lc.t, len(Ds), np.random.default_rng(3), n_random=40)
+    f = api.nu_gp_factor(cu(lc.t), cu(lc.diag_var), terms, cu(lc.X), cu(lc.y))
+    g = gpu_refine(f, cands, Ds)
+    o = oracle_refine(model, cands, Ds)
+    err = errors(g, o)
+    print(f"refine {terms_case}: {err}")
+    assert max(err["depth"], err["var"], err["dlnl"], err["snr"]) <= FP64_TOL, err
