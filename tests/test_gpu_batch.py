@@ -125,3 +125,24 @@ def test_injection_workload_shape_against_oracle():
               f"{lc.injected['delta']:.2f}, Q {lc.injected['Q']:.1f}): lnP err {wl:.2e}, "
               f"Q err {wq:.2e}")
         assert wl <= FP64_TOL and wq <= FP64_TOL
+
+
+def test_batch_with_wide_tree_levels():
+    """75 000 samples in one batch: the factor scans' widest tree level has
+    more than 4096 groups (one thread per group) and the upper levels fewer
+    (one warp per group); every curve equals its single-curve calls, whose
+    trees are warp-level throughout."""
+    curves = [synth.small_curve(n=2500, seed=300 + c, p_rot=0.3 + 0.05 * c, sigma=8e-3,
+                                gap=(60 if c % 3 == 0 else None),
+                                inject=(2.5e-3, 1.0 / 24.0, 0.37))
+              for c in range(30)]
+    dt = synth.CADENCE_DAYS
+    res = api.nu_batch_search([(lc.t, lc.y, lc.diag_var, lc.terms) for lc in curves], DS,
+                              PERIODS, k=2, precision="fp64", phase_step=dt)
+    assert res["status"] == [0] * len(curves)
+    for c in (0, 7, 29):
+        one = _single(curves[c], "fp64", dt)
+        assert np.array_equal(res["D_idx"][c].cpu().numpy(), one["D_idx"])
+        for key in ("Q", "T0", "lnP", "depth", "sigma"):
+            np.testing.assert_allclose(res[key][c].cpu().numpy(), one[key], rtol=1e-12, atol=0,
+                                       err_msg=key)
