@@ -38,6 +38,37 @@ METRIC = "linear-search (t0,D) fits/s + period trials/s, %HBM roofline, mixed vs
 MEASURED_FP64_TFLOPS = 1.197   # DFMA microbenchmark on this machine's GB300 (2 DFMA/clk/SM)
 # FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_READ_GBS = 17700.0          # L2-resident read microbenchmark on this machine's GB300
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth from the machine's measured peaks, else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def linear_search_roofline(lc, Ds, ms, nb=2, k=2):
+    """Algorithmic bytes and FP64 flops of one nu_linear_search: per sample
+    the factor arrays it reads (t, F, kg, 1/D, G, z0, Zt), per template the
+    three FP64 outputs; per window sample about 8 + 6 J flops of the forward
+    solve and sums, per template the tail s^T G s and the epilogue."""
+    J = 2 * nb
+    JJ = J * (J + 1) // 2
+    n = len(lc.t)
+    dt = float(np.median(np.diff(lc.t)))
+    steps = sum(int(round(D / dt)) for D in Ds) * n
+    flops = steps * (8 + 6 * J) + n * len(Ds) * (2 * JJ + 2 * J + 30)
+    bytes_ = n * 8 * (1 + 4 * nb + J + 1 + JJ + 1 + k) + n * len(Ds) * 24
+    hbm, src = measured_hbm_gbs()
+    gbs = bytes_ / (ms / 1e3) / 1e9
+    tfl = flops / (ms / 1e3) / 1e12
+    return {"bytes": bytes_, "GB/s": gbs, "hbm_frac": gbs / hbm, "hbm_peak": hbm,
+            "hbm_peak_source": src, "fp64_tflops": tfl,
+            "fp64_pipe_frac": tfl / MEASURED_FP64_TFLOPS, "flops": flops}
 FOLD_FLOPS_PER_VISIT = 55.0    # 25 in pass 1 + 30 in pass 2 (one log per visit)
 # DRAM bytes (read + write) of one fold launch on the bench workload (sector_19440,
 # FP64), from an ncu capture of the kernel as it stands
@@ -485,6 +516,14 @@ def main():
            "stages_ms": {"factor": float(stage_ms[0]), "linear_search": float(stage_ms[1]),
                          "periodic_search": float(stage_ms[2])},
            "linear_search_fits_per_s": n_templates / ((stage_ms[0] + stage_ms[1]) / 1e3),
+           "linear_search_roofline": linear_search_roofline(lc, w.durations, float(stage_ms[1])),
+           "fold_gather": {"bytes_per_visit": 48,
+                           "GB/s": visits * 48 / (float(stage_ms[2]) / 1e3) / 1e9,
+                           "l2_read_GB/s": L2_READ_GBS,
+                           "frac": visits * 48 / (float(stage_ms[2]) / 1e3) / 1e9 / L2_READ_GBS,
+                           "note": "algorithmic bytes: two bracketing FP64 nodes of three "
+                                   "values per visit; the FP32 screen reads one 32-byte "
+                                   "record per visit from L1/L2"},
            "fold_visits_per_s": visits / (fold_ms / 1e3),
            "gpu_launches": int(launches), "wall_s_timed": t_wall, "clocks": clocks,
            "roofline": roofline}
