@@ -676,6 +676,8 @@ struct ScreenGeom {
     const unsigned* reg;               // [0]: an epoch is off the slot grid,
                                        // [1]: max |offset from its slot| (float bits)
     int on;                            // screening allowed for this curve
+    const double2* peak;               // epoch time and duration index of the
+                                       // largest finite gain (y < 0: none)
 };
 
 // Node sigma of one (duration, epoch) in FP64 (NaN when invalid).
@@ -813,6 +815,61 @@ __global__ void k_lwin(const float* __restrict__ lslot, int64_t n, float* __rest
     const int64_t e = x + NU_LWIN < n ? x + NU_LWIN : n;
     for (int64_t t = x; t < e; ++t) m = fmaxf(m, lslot[t]);
     lwin[x] = m;
+}
+
+// Largest finite single-event gain of each curve (first maximum in
+// duration-major order): peak[g] = (its epoch time, its duration index), or
+// (NaN, -1) when no gain is finite.  One block per curve; s_off == nullptr
+// means one curve of n_t0 epochs.  The gains of curve g are the rows of ng
+// values starting at s_off[g] * n_D.
+__global__ void k_gain_peak(const double* __restrict__ gain, const double* __restrict__ t,
+                            const int64_t* __restrict__ s_off, int64_t n_t0, int n_D,
+                            double2* __restrict__ peak) {
+    const int g = blockIdx.x;
+    const int64_t s0 = s_off ? s_off[g] : 0;
+    const int64_t ng = s_off ? s_off[g + 1] - s0 : n_t0;
+    const int64_t base = s0 * n_D, n = ng * n_D;
+    double best = -INFINITY;
+    long long at = -1;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const double v = gain[base + e];
+        if (v > best && v < INFINITY) {
+            best = v;
+            at = e;
+        }
+    }
+    auto better = [](double v2, long long a2, double v, long long a) {
+        return a2 >= 0 && (a < 0 || v2 > v || (v2 == v && a2 < a));
+    };
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long a2 = __shfl_xor_sync(0xffffffffu, at, o);
+        if (better(v2, a2, best, at)) {
+            best = v2;
+            at = a2;
+        }
+    }
+    __shared__ double sv[32];
+    __shared__ long long sa[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sv[wid] = best;
+        sa[wid] = at;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (better(sv[w], sa[w], best, at)) {
+                best = sv[w];
+                at = sa[w];
+            }
+        if (at >= 0) {
+            const int64_t d = at / ng, i = at - d * ng;
+            peak[g] = make_double2(t[s0 + i], (double)d);
+        } else {
+            peak[g] = make_double2(NAN, -1.0);
+        }
+    }
 }
 
 // Per-period constants of the screen.
@@ -1164,8 +1221,9 @@ __device__ __forceinline__ void evaluate_queued_warp(const FoldGeom& g,
 // cells (the block's cells in strides of blockDim) and queues the survivors
 // in its own shared queue; a full queue (32 cells) is evaluated exactly, one
 // cell per lane, by that warp alone, so the screen needs no block barriers.
-// In its first round each warp evaluates its best-bounded cell with all its
-// lanes to seed the threshold.  The thresholds (best ln P, and its FP32
+// Warp 0 first evaluates the cell through the curve's largest single-event
+// gain, and in its first round each warp evaluates its best-bounded cell with
+// all its lanes when that bound is above the threshold.  The thresholds (best ln P, and its FP32
 // lower bound) are shared by the block through atomic maxima.
 template <int MAXT = 256>
 __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const ScreenGeom& sg,
@@ -1210,6 +1268,29 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     const ScreenPeriod& sp = sh_sp;
     const CellCtx& c = sh_cc;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // Peak seed: the cell whose epochs pass through the epoch of the curve's
+    // largest single-event gain (phase index nearest to it), evaluated
+    // exactly by warp 0.  When one event dominates (a deep transit), every
+    // cell that catches it would otherwise pass the screen until the
+    // threshold has risen.
+    if (sg.peak) {
+        const double2 pk = *sg.peak;
+        if (pk.y >= 0.0) {
+            if (wid == 0) {
+                const double x = (pk.x - g.t_ref) / P;
+                int64_t pj = (int64_t)rint((x - floor(x)) * (double)n_phi);
+                if (pj >= n_phi || pj < 0) pj = 0;
+                const double lnp = exact_cell_warp(g, nodes + (int64_t)pk.y * g.n_t0, c, pj);
+                if (lane == 0 && lnp == lnp && lnp > -INFINITY) {
+                    // the same margin as the first-round seed below
+                    const double seed = lnp - 1e-9 * (1.0 + fabs(lnp));
+                    atomicMax(&sh_sbest, max_key(seed));
+                    atomicMax(&sh_bfk, fkey(__double2float_rd(seed)));
+                }
+            }
+            __syncthreads();
+        }
+    }
     long long* qc = sh_qc[wid];
     int* qd = sh_qd[wid];
     int nq = 0;                              // warp-uniform queue length
@@ -1262,7 +1343,9 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                              sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c, j,
                              (unsigned long long)j * sp.uph, from_fkey(sh_bfk));
         if (first) {
-            // seed: the warp evaluates its lane with the largest finite bound
+            // seed: the warp evaluates its lane with the largest finite bound,
+            // unless that bound is already below the threshold (the cell
+            // cannot raise it)
             first = false;
             float v = (ub < INFINITY) ? ub : -INFINITY;
             int src = lane;
@@ -1274,7 +1357,9 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                     src = s2;
                 }
             }
-            if (v > -INFINITY) {
+            // (the threshold is broadcast so that the branch is warp-uniform)
+            const float thr = __shfl_sync(0xffffffffu, from_fkey(sh_bfk), 0);
+            if (v > -INFINITY && !(v < thr)) {
                 const int pd = __shfl_sync(0xffffffffu, d, src);
                 const long long pj = __shfl_sync(0xffffffffu, (long long)j, src);
                 const double lnp = exact_cell_warp(g, nodes + (int64_t)pd * g.n_t0, c, pj);
@@ -1603,6 +1688,7 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
              const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
              const ulonglong2* __restrict__ vpair, const ScreenRec* __restrict__ srec,
              const float* __restrict__ lwin, const unsigned* __restrict__ reg,
+             const double2* __restrict__ peak,
              const int* __restrict__ bucket,
              const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
              const double* __restrict__ periods, int64_t n_P, unsigned long long* counter,
@@ -1632,7 +1718,7 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
             if (KIND == 0) {
                 const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off,
                                     srec + fs.srec_off, lwin + fs.srec_off, fs.n_slots,
-                                    reg + 2 * g, fs.screen};
+                                    reg + 2 * g, fs.screen, peak + g};
                 fold_screened_one<MAXT>(gg, sg, (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
                                   periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                                   lnp_out);
@@ -1830,7 +1916,9 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
                 (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.lslot, fs.slot_of);
             k_lwin<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(fs.lslot, fb.n_srec_total,
                                                                     fs.lwin);
-            launched += 4;
+            k_gain_peak<<<n_seg, 256, 0, st>>>((const double*)gain, t, s_off_dev, 0, n_D,
+                                                fs.peak);
+            launched += 5;
         } else
             k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
@@ -1867,7 +1955,8 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
     // block size (64, 128 or 256 threads)
 #define NU_FB(KIND_, MAXT_, CTR_)                                                          \
     k_fold_batch<KIND_, MAXT_><<<grid, MAXT_, 0, st>>>(                                  \
-        segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.bucket,  \
+        segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.peak,    \
+        fs.bucket,                                                                         \
         fs.rec, n_D, dt, gap_factor, periods, n_P, CTR_, Q, T0, Didx, dep, sig, lnp)
 #define NU_FB_SIZE(KIND_, CTR_)                                                            \
     do {                                                                                   \
@@ -1991,8 +2080,9 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             float* lslot = (float*)(scratch + L.lslot);
             float* lwin = (float*)(scratch + L.lwin);
             unsigned* reg = (unsigned*)(flag + 1);
+            double2* peak = (double2*)(scratch + L.flag + 16);
             const ScreenGeom sg{nrec, vpair, srec, lwin, n_slots, reg,
-                                (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0};
+                                (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0, peak};
             e = cudaMemsetAsync(flag, 0, 256, st);
             if (e != cudaSuccess) {
                 count_launches(launched);
@@ -2014,6 +2104,8 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
                 t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, lslot, n_slots, slot_of,
                 vpair);
             k_lwin<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(lslot, n_slots * n_D, lwin);
+            k_gain_peak<<<1, 1024, 0, st>>>((const double*)dlnl_dev, t0s_dev, nullptr, n_t0, n_D,
+                                            peak);
             // One block per period.  With many periods, 2-warp blocks: 14 fit
             // on an SM (28 warps) and each period has 2 warps to seed; with
             // few, 8-warp blocks keep the GPU full (C2, 20 000 periods: 16.5 ms
@@ -2026,7 +2118,7 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
                 k_fold_screened<256><<<(unsigned)n_P, 256, 0, st>>>(
                     g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
                     D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-            launched += 7;
+            launched += 8;
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev,
