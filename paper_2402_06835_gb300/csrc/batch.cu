@@ -215,7 +215,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t f_reg = foff;   foff += al((size_t)n_lc * 2 * sizeof(unsigned));
     const size_t f_lslot = foff; foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
     const size_t f_lwin = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
-    const size_t f_peak = foff;  foff += al((size_t)n_lc * sizeof(double2));
+    const size_t f_peak = foff;  foff += al((size_t)n_lc * sizeof(unsigned long long));
     e = cudaMallocAsync((void**)&fold_mem, foff, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(fold_mem + f_segs, fbat.segs.data(), fbat.segs.size() * sizeof(FoldSeg),
@@ -230,7 +230,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
                           (Node4<float>*)(fold_mem + f_rec), (ScreenRec*)(fold_mem + f_srec),
                           (int*)(fold_mem + f_slot), (unsigned*)(fold_mem + f_reg),
                           (float*)(fold_mem + f_lslot), (float*)(fold_mem + f_lwin),
-                          (double2*)(fold_mem + f_peak)};
+                          (unsigned long long*)(fold_mem + f_peak)};
     unsigned long long* ctr = (unsigned long long*)(mem + o_ctr);
     const double* Ds_dev = (const double*)(mem + o_Ds);
     int dev = 0, n_sm = 152;

@@ -73,7 +73,7 @@ struct FoldScratch {
     unsigned* reg;          // FP64: two words per curve (zeroed by the prep)
     float* lslot;           // FP64: gain at each slot (rounded up), then
     float* lwin;            //       its windowed maximum (group bound)
-    double2* peak;          // FP64: per curve, the largest gain's epoch and duration
+    unsigned long long* peak;  // FP64: per curve, the key of its largest gain
 };
 
 // Host side of the batch fold: per-curve layout and launches.

@@ -676,8 +676,8 @@ struct ScreenGeom {
     const unsigned* reg;               // [0]: an epoch is off the slot grid,
                                        // [1]: max |offset from its slot| (float bits)
     int on;                            // screening allowed for this curve
-    const double2* peak;               // epoch time and duration index of the
-                                       // largest finite gain (y < 0: none)
+    const unsigned long long* peak;    // key of the largest finite gain (k_gain_peak);
+                                       // 0: none
 };
 
 // Node sigma of one (duration, epoch) in FP64 (NaN when invalid).
@@ -815,61 +815,6 @@ __global__ void k_lwin(const float* __restrict__ lslot, int64_t n, float* __rest
     const int64_t e = x + NU_LWIN < n ? x + NU_LWIN : n;
     for (int64_t t = x; t < e; ++t) m = fmaxf(m, lslot[t]);
     lwin[x] = m;
-}
-
-// Largest finite single-event gain of each curve (first maximum in
-// duration-major order): peak[g] = (its epoch time, its duration index), or
-// (NaN, -1) when no gain is finite.  One block per curve; s_off == nullptr
-// means one curve of n_t0 epochs.  The gains of curve g are the rows of ng
-// values starting at s_off[g] * n_D.
-__global__ void k_gain_peak(const double* __restrict__ gain, const double* __restrict__ t,
-                            const int64_t* __restrict__ s_off, int64_t n_t0, int n_D,
-                            double2* __restrict__ peak) {
-    const int g = blockIdx.x;
-    const int64_t s0 = s_off ? s_off[g] : 0;
-    const int64_t ng = s_off ? s_off[g + 1] - s0 : n_t0;
-    const int64_t base = s0 * n_D, n = ng * n_D;
-    double best = -INFINITY;
-    long long at = -1;
-    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-        const double v = gain[base + e];
-        if (v > best && v < INFINITY) {
-            best = v;
-            at = e;
-        }
-    }
-    auto better = [](double v2, long long a2, double v, long long a) {
-        return a2 >= 0 && (a < 0 || v2 > v || (v2 == v && a2 < a));
-    };
-    for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
-        const long long a2 = __shfl_xor_sync(0xffffffffu, at, o);
-        if (better(v2, a2, best, at)) {
-            best = v2;
-            at = a2;
-        }
-    }
-    __shared__ double sv[32];
-    __shared__ long long sa[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        sv[wid] = best;
-        sa[wid] = at;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-            if (better(sv[w], sa[w], best, at)) {
-                best = sv[w];
-                at = sa[w];
-            }
-        if (at >= 0) {
-            const int64_t d = at / ng, i = at - d * ng;
-            peak[g] = make_double2(t[s0 + i], (double)d);
-        } else {
-            peak[g] = make_double2(NAN, -1.0);
-        }
-    }
 }
 
 // Per-period constants of the screen.
@@ -1138,6 +1083,38 @@ __device__ __forceinline__ float from_fkey(unsigned k) {
     return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
 }
 
+// A large finite single-event gain of each curve, for the peak seed: key[g]
+// = (order key of the gain rounded to FP32) << 32 | (2^32 - 1 - e), the
+// maximum over the curve's grid entries e (duration-major, e < 2^32 - 1), so
+// the largest rounded gain wins and ties go to the first entry.  key[g] must
+// be zero on entry and stays zero when no gain is finite.  blockIdx.x is the
+// curve (s_off == nullptr: one curve of n_t0 epochs); the blocks along y
+// share a curve's entries.
+__global__ void k_gain_peak(const double* __restrict__ gain, const int64_t* __restrict__ s_off,
+                            int64_t n_t0, int n_D, unsigned long long* __restrict__ key) {
+    const int g = blockIdx.x;
+    const int64_t s0 = s_off ? s_off[g] : 0;
+    const int64_t ng = s_off ? s_off[g + 1] - s0 : n_t0;
+    const int64_t n = ng * n_D;
+    if (n >= 0xffffffffLL) return;
+    const double* row = gain + s0 * n_D;
+    unsigned long long best = 0;
+    for (int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.y * blockDim.x) {
+        const double v = row[e];
+        if (v > -INFINITY && v < INFINITY) {
+            const unsigned long long k = ((unsigned long long)fkey((float)v) << 32) |
+                                         (unsigned long long)(0xffffffffu - (unsigned)e);
+            best = k > best ? k : best;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
+        best = k2 > best ? k2 : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best != 0) atomicMax(key + g, best);
+}
+
 // Exact evaluation of a queued cell by one thread; the thread's best is kept
 // in shared memory and the block's thresholds are raised.
 __device__ __forceinline__ void evaluate_queued(const FoldGeom& g,
@@ -1268,19 +1245,24 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     const ScreenPeriod& sp = sh_sp;
     const CellCtx& c = sh_cc;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // cells of 32 or more epochs are evaluated warp-cooperatively
+    const bool coop = g.t_last - g.t_ref >= 32.0 * P;
     // Peak seed: the cell whose epochs pass through the epoch of the curve's
     // largest single-event gain (phase index nearest to it), evaluated
-    // exactly by warp 0.  When one event dominates (a deep transit), every
-    // cell that catches it would otherwise pass the screen until the
-    // threshold has risen.
-    if (sg.peak) {
-        const double2 pk = *sg.peak;
-        if (pk.y >= 0.0) {
+    // exactly by warp 0.  When one event dominates a short cell (a deep
+    // transit), every cell that catches it would otherwise pass the screen
+    // until the threshold has risen.  Long cells are left to the first-round
+    // seeds: there one event weighs less, and the seed costs a long walk.
+    if (sg.peak && !coop) {
+        const unsigned long long pk = *sg.peak;
+        if (pk != 0) {
             if (wid == 0) {
-                const double x = (pk.x - g.t_ref) / P;
+                const int64_t e = (int64_t)(0xffffffffu - (unsigned)(pk & 0xffffffffu));
+                const int64_t pd = e / g.n_t0;
+                const double x = (g.t0s[e - pd * g.n_t0] - g.t_ref) / P;
                 int64_t pj = (int64_t)rint((x - floor(x)) * (double)n_phi);
                 if (pj >= n_phi || pj < 0) pj = 0;
-                const double lnp = exact_cell_warp(g, nodes + (int64_t)pk.y * g.n_t0, c, pj);
+                const double lnp = exact_cell_warp(g, nodes + pd * g.n_t0, c, pj);
                 if (lane == 0 && lnp == lnp && lnp > -INFINITY) {
                     // the same margin as the first-round seed below
                     const double seed = lnp - 1e-9 * (1.0 + fabs(lnp));
@@ -1294,8 +1276,6 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     long long* qc = sh_qc[wid];
     int* qd = sh_qd[wid];
     int nq = 0;                              // warp-uniform queue length
-    // cells of 32 or more epochs are evaluated warp-cooperatively
-    const bool coop = g.t_last - g.t_ref >= 32.0 * P;
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
     bool first = true;
@@ -1688,7 +1668,7 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
              const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
              const ulonglong2* __restrict__ vpair, const ScreenRec* __restrict__ srec,
              const float* __restrict__ lwin, const unsigned* __restrict__ reg,
-             const double2* __restrict__ peak,
+             const unsigned long long* __restrict__ peak,
              const int* __restrict__ bucket,
              const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
              const double* __restrict__ periods, int64_t n_P, unsigned long long* counter,
@@ -1916,8 +1896,9 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
                 (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.lslot, fs.slot_of);
             k_lwin<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(fs.lslot, fb.n_srec_total,
                                                                     fs.lwin);
-            k_gain_peak<<<n_seg, 256, 0, st>>>((const double*)gain, t, s_off_dev, 0, n_D,
-                                                fs.peak);
+            cudaMemsetAsync(fs.peak, 0, (size_t)n_seg * sizeof(unsigned long long), st);
+            k_gain_peak<<<dim3(n_seg, 1), 256, 0, st>>>((const double*)gain, s_off_dev, 0, n_D,
+                                                       fs.peak);
             launched += 5;
         } else
             k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
@@ -2080,7 +2061,7 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             float* lslot = (float*)(scratch + L.lslot);
             float* lwin = (float*)(scratch + L.lwin);
             unsigned* reg = (unsigned*)(flag + 1);
-            double2* peak = (double2*)(scratch + L.flag + 16);
+            unsigned long long* peak = (unsigned long long*)(scratch + L.flag + 16);
             const ScreenGeom sg{nrec, vpair, srec, lwin, n_slots, reg,
                                 (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0, peak};
             e = cudaMemsetAsync(flag, 0, 256, st);
@@ -2104,8 +2085,8 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
                 t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, lslot, n_slots, slot_of,
                 vpair);
             k_lwin<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(lslot, n_slots * n_D, lwin);
-            k_gain_peak<<<1, 1024, 0, st>>>((const double*)dlnl_dev, t0s_dev, nullptr, n_t0, n_D,
-                                            peak);
+            k_gain_peak<<<dim3(1, (unsigned)std::min<int64_t>(div_up(ngrid, 2048), 608)), 256, 0,
+                          st>>>((const double*)dlnl_dev, nullptr, n_t0, n_D, peak);
             // One block per period.  With many periods, 2-warp blocks: 14 fit
             // on an SM (28 warps) and each period has 2 warps to seed; with
             // few, 8-warp blocks keep the GPU full (C2, 20 000 periods: 16.5 ms
