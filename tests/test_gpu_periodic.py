@@ -198,6 +198,33 @@ def test_fold_fp64_screen_hard_cases(offset, regular):
           f"Q err {wq:.2e}, ties {differ}")
 
 
+def test_fold_fp64_peak_seed_edges():
+    """One event dominates every cell that catches it (the case the FP64
+    fold's peak seed is for), placed at the last epoch of the last duration
+    row; an equal gain earlier in the grid (the seed takes the first), and
+    infinite gains (never a seed, dropped by both sides).  Periods short and
+    long against the span, so that the seeded periods (cells of fewer than 32
+    epochs) and the others are both compared."""
+    rng = np.random.default_rng(43)
+    dt = synth.CADENCE_DAYS
+    t0s = 3.0 + np.arange(1200) * dt
+    n = len(t0s)
+    var = rng.uniform(1e-8, 5e-8, (3, n))
+    depth = rng.normal(0, 1e-4, (3, n))
+    depth[2, -1] = 3e-3
+    depth[0, 500], var[0, 500] = depth[2, -1], var[2, -1]
+    dlnl = depth ** 2 / (2 * var)
+    dlnl[1, 10] = np.inf
+    dlnl[0, 900] = -np.inf
+    g = dict(depth=depth, var=var, dlnl=dlnl)
+    periods = np.concatenate([np.linspace(0.03, 0.06, 20), np.linspace(0.06, 1.6, 180)])
+    ora = periodic.periodic_search(t0s, depth, var, dlnl, periods, dt)
+    gpu = _gpu_fold(t0s, np.ones(3), g, periods, "fp64", phase_step=dt)
+    wl, wq, differ = periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, dt,
+                                      FP64_TOL, FP64_TOL, periodic.fold_period)
+    print(f"fp64 peak seed edges: lnP err {wl:.2e}, Q err {wq:.2e}, ties {differ}")
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_large_period_grid_kernels(precision):
     """Grids of 8192 periods or more run the small-block fold instances (FP64:
