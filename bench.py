@@ -91,9 +91,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
-    ap.add_argument("--case", default=None, choices=["fold_small"],
-                    help="profiling case: one periodic search per precision on a "
-                         "sector-shaped grid with 300 periods (for ncu captures)")
+    ap.add_argument("--case", default=None, choices=["fold_small", "batch_small"],
+                    help="profiling cases for ncu captures: fold_small = one periodic "
+                         "search per precision on the sector grid with 10 000 periods; "
+                         "batch_small = two batched searches per precision of 400 "
+                         "injection curves")
     return ap.parse_args()
 
 
@@ -405,10 +407,32 @@ def profile_case(args):
         print(prec, float(r["Q"].max()))
 
 
+def profile_batch_case(args):
+    """Small batched case for ncu: 400 curves of the injection workload (2880
+    samples, 1 duration, 4000 periods), nu_batch_search twice per precision
+    (mixed first, then FP64).  The first call of each precision tunes the
+    fold's launch shape; the second runs the chosen one."""
+    import torch
+    from paper_2402_06835_gb300 import api
+    w = synth.injection_4000(n_curves=400)
+    cu = lambda a: torch.as_tensor(a, device="cuda")
+    items = [(cu(lc.t), cu(lc.y), cu(lc.diag_var), lc.terms) for lc in w.curves]
+    per = cu(w.periods)
+    for prec in ("mixed", "fp64"):
+        for _ in range(2):
+            r = api.nu_batch_search(items, w.durations, per, k=2, precision=prec,
+                                    phase_step=synth.CADENCE_DAYS)
+        torch.cuda.synchronize()
+        print(prec, float(r["Q"].max()))
+
+
 def main():
     args = parse()
     if args.case == "fold_small":
         profile_case(args)
+        return
+    if args.case == "batch_small":
+        profile_batch_case(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
