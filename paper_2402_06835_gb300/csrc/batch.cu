@@ -216,6 +216,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t f_lslot = foff; foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
     const size_t f_lwin = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
     const size_t f_peak = foff;  foff += al((size_t)n_lc * sizeof(unsigned long long));
+    const size_t f_ptab = foff;  foff += al((size_t)n_P * period_const_bytes());
     e = cudaMallocAsync((void**)&fold_mem, foff, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(fold_mem + f_segs, fbat.segs.data(), fbat.segs.size() * sizeof(FoldSeg),
@@ -230,7 +231,8 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
                           (Node4<float>*)(fold_mem + f_rec), (ScreenRec*)(fold_mem + f_srec),
                           (int*)(fold_mem + f_slot), (unsigned*)(fold_mem + f_reg),
                           (float*)(fold_mem + f_lslot), (float*)(fold_mem + f_lwin),
-                          (unsigned long long*)(fold_mem + f_peak)};
+                          (unsigned long long*)(fold_mem + f_peak),
+                          (PeriodConst*)(fold_mem + f_ptab)};
     unsigned long long* ctr = (unsigned long long*)(mem + o_ctr);
     const double* Ds_dev = (const double*)(mem + o_Ds);
     int dev = 0, n_sm = 152;

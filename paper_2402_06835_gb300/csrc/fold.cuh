@@ -63,6 +63,9 @@ struct FoldSeg {
     int64_t srec_off;   // FP64 path: first slot-indexed screening record
 };
 
+struct PeriodConst;
+size_t period_const_bytes();
+
 // Device scratch of the batch fold.
 struct FoldScratch {
     void* nodes;            // exact-path records (exact_layout of all samples)
@@ -74,6 +77,7 @@ struct FoldScratch {
     float* lslot;           // FP64: gain at each slot (rounded up), then
     float* lwin;            //       its windowed maximum (group bound)
     unsigned long long* peak;  // FP64: per curve, the key of its largest gain
+    PeriodConst* ptab;      // FP64: per period, its curve-independent constants
 };
 
 // Host side of the batch fold: per-curve layout and launches.

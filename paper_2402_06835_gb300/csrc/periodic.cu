@@ -464,6 +464,75 @@ __device__ __forceinline__ CellCtx cell_ctx(const FoldGeom& g, double P, int64_t
     return c;
 }
 
+// The constants of one period that do not depend on the curve (phase count,
+// fixed-point walk steps and their reciprocals), computed as screen_period
+// and cell_ctx compute them.  The batched fold takes them from a table built
+// once per call, so that its (curve, period) items, bound by the FP64 pipe
+// when their cells are short, skip these divisions.
+struct PeriodConst {
+    int64_t n_phi;
+    double R;                          // P / dt
+    unsigned long long ustep, uph;     // screen steps (0 when R 2^40 >= 4e18)
+    float inv_ustep32;
+    float c_inv_ustep32;
+    SlotWalk swp, swk;
+    double nphi_d, rphi;
+};
+
+// The table entry of period P (P must not be a bad period of the curves).
+__device__ __forceinline__ PeriodConst period_const(double P, double dt, double inv_dt) {
+    PeriodConst pc;
+    const double SCALE = 1099511627776.0;   // 2^40
+    pc.n_phi = (int64_t)ceil(P / dt);
+    pc.R = P * inv_dt;
+    if (pc.R * SCALE < 4.0e18) {
+        pc.ustep = (unsigned long long)llrint(pc.R * SCALE);
+        pc.uph = (unsigned long long)llrint(pc.R / (double)pc.n_phi * SCALE);
+        pc.inv_ustep32 = (float)(4294967296.0 / (double)pc.ustep);
+    } else {
+        pc.ustep = pc.uph = 0;
+        pc.inv_ustep32 = 0.f;
+    }
+    pc.swp = slot_walk(1.0 / (double)pc.n_phi, pc.R);
+    pc.swk = slot_walk(0.0, pc.R);
+    pc.c_inv_ustep32 = (float)(4294967296.0 / (double)pc.swk.ustep);
+    pc.nphi_d = (double)pc.n_phi;
+    pc.rphi = 1.0 / pc.nphi_d;
+    return pc;
+}
+
+// cell_ctx from a table entry (the same values).
+__device__ __forceinline__ CellCtx cell_ctx(const FoldGeom& g, double P, const PeriodConst& pc) {
+    CellCtx c;
+    c.P = P;
+    c.swp = pc.swp;
+    c.swk = pc.swk;
+    const double SCALE = 1099511627776.0;   // 2^40
+    const double ulast_d = (g.t_last - g.t_ref) * g.inv_dt * SCALE;
+    c.ulast = ulast_d < 4.0e18 ? (unsigned long long)llrint(ulast_d) : 4000000000000000000ull;
+    c.inv_ustep32 = pc.c_inv_ustep32;
+    c.klast = okey(g.t_last);
+    c.nphi_d = pc.nphi_d;
+    c.rphi = pc.rphi;
+    return c;
+}
+
+// Table of period constants (invalid periods get placeholder entries; the
+// folds test a period before they read its entry).
+__global__ void k_period_consts(const double* __restrict__ periods, int64_t n_P, double dt,
+                                PeriodConst* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_P) return;
+    const double P = periods[i];
+    if (!(P > 0.0) || !isfinite(P) || P / dt > 1.0e9) {
+        out[i] = PeriodConst{1, 0.0, 0, 0, 0.f, 0.f, {0, 0}, {0, 0}, 1.0, 1.0};
+        return;
+    }
+    out[i] = period_const(P, dt, 1.0 / dt);
+}
+
+size_t period_const_bytes() { return sizeof(PeriodConst); }
+
 __device__ __forceinline__ double cell_phi(const CellCtx& c, int64_t j) {
     const double jd = (double)j;
     const double q0 = jd * c.rphi;
@@ -829,24 +898,14 @@ struct ScreenPeriod {
     bool slots;     // regular grid: events from the slot records
 };
 
-__device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const ScreenGeom& sg,
-                                                      double P, int64_t n_phi) {
-    ScreenPeriod sp;
+// The curve-dependent constants of the screen (the walk's error bound, the
+// band around epochs, the regular-grid test); sp holds the period's steps.
+__device__ __forceinline__ ScreenPeriod screen_period_curve(const FoldGeom& g,
+                                                            const ScreenGeom& sg, double P,
+                                                            int64_t n_phi, double R,
+                                                            double span, ScreenPeriod sp) {
     const double SCALE = 1099511627776.0;   // 2^40
-    const double R = P * g.inv_dt;
-    const double span = (g.t_last - g.t_ref) * g.inv_dt;
-    sp.on = sg.on != 0 && R * SCALE < 4.0e18 && span < 8388608.0;
-    sp.slots = false;
-    sp.uph = sp.ustep = sp.ulast = sp.delta = sp.uend = 0;
-    sp.inv_ustep32 = 0.f;
-    sp.cv = 0.f;
-    sp.dw = 0.f;
-    sp.hw = 0.5f;
-    if (!sp.on) return sp;
-    sp.ustep = (unsigned long long)llrint(R * SCALE);
-    sp.uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
     sp.ulast = sg.vpair[g.n_t0 - 1].x;
-    sp.inv_ustep32 = (float)(4294967296.0 / (double)sp.ustep);
     // position error of the walk against the FP64 epochs, in 2^-40 slots:
     // half a unit per phase and epoch step, the rounding of T, t0 and vpos
     const double kb = span / R + 2.0;
@@ -874,6 +933,47 @@ __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const S
     sp.cv = (float)(8.0 * 5.9604644775390625e-08 + 2.0 * e_w);
     sp.hw = 0.5f - sp.dw;
     return sp;
+}
+
+__device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const ScreenGeom& sg,
+                                                      double P, int64_t n_phi) {
+    ScreenPeriod sp;
+    const double SCALE = 1099511627776.0;   // 2^40
+    const double R = P * g.inv_dt;
+    const double span = (g.t_last - g.t_ref) * g.inv_dt;
+    sp.on = sg.on != 0 && R * SCALE < 4.0e18 && span < 8388608.0;
+    sp.slots = false;
+    sp.uph = sp.ustep = sp.ulast = sp.delta = sp.uend = 0;
+    sp.inv_ustep32 = 0.f;
+    sp.cv = 0.f;
+    sp.dw = 0.f;
+    sp.hw = 0.5f;
+    if (!sp.on) return sp;
+    sp.ustep = (unsigned long long)llrint(R * SCALE);
+    sp.uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
+    sp.inv_ustep32 = (float)(4294967296.0 / (double)sp.ustep);
+    return screen_period_curve(g, sg, P, n_phi, R, span, sp);
+}
+
+// screen_period from a table entry (the same values).
+__device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const ScreenGeom& sg,
+                                                      double P, const PeriodConst& pc) {
+    ScreenPeriod sp;
+    const double SCALE = 1099511627776.0;   // 2^40
+    const double R = pc.R;
+    const double span = (g.t_last - g.t_ref) * g.inv_dt;
+    sp.on = sg.on != 0 && R * SCALE < 4.0e18 && span < 8388608.0;
+    sp.slots = false;
+    sp.uph = sp.ustep = sp.ulast = sp.delta = sp.uend = 0;
+    sp.inv_ustep32 = 0.f;
+    sp.cv = 0.f;
+    sp.dw = 0.f;
+    sp.hw = 0.5f;
+    if (!sp.on) return sp;
+    sp.ustep = pc.ustep;
+    sp.uph = pc.uph;
+    sp.inv_ustep32 = pc.inv_ustep32;
+    return screen_period_curve(g, sg, P, pc.n_phi, R, span, sp);
 }
 
 // Sums of the screen (see above) and the bound they give.
@@ -1202,7 +1302,9 @@ __device__ __forceinline__ void evaluate_queued_warp(const FoldGeom& g,
 // gain, and in its first round each warp evaluates its best-bounded cell with
 // all its lanes when that bound is above the threshold.  The thresholds (best ln P, and its FP32
 // lower bound) are shared by the block through atomic maxima.
-template <int MAXT = 256>
+// With TAB the period's curve-independent constants come from the table
+// entry pc (k_period_consts), else they are computed here.
+template <int MAXT = 256, bool TAB = false>
 __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const ScreenGeom& sg,
                                                   const Node8<double>* __restrict__ nodes,
                                                   int n_D, double P, int64_t p,
@@ -1211,7 +1313,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                                                   int* __restrict__ Didx_out,
                                                   double* __restrict__ dep_out,
                                                   double* __restrict__ sig_out,
-                                                  double* __restrict__ lnp_out) {
+                                                  double* __restrict__ lnp_out,
+                                                  const PeriodConst* __restrict__ pc = nullptr) {
     __shared__ long long sh_qc[MAXT / 32][64];      // per-warp survivor queues
     __shared__ int sh_qd[MAXT / 32][64];
     __shared__ unsigned long long sh_sbest; // best ln P evaluated (max key)
@@ -1226,8 +1329,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     // the screen loop (most of these are read only on rare paths)
     __shared__ ScreenPeriod sh_sp;
     __shared__ CellCtx sh_cc;
-    const int64_t n_phi = (int64_t)ceil(P / g.dt);
-    if (threadIdx.x == 0) sh_sp = screen_period(g, sg, P, n_phi);
+    const int64_t n_phi = TAB ? pc->n_phi : (int64_t)ceil(P / g.dt);
+    if (threadIdx.x == 0) sh_sp = TAB ? screen_period(g, sg, P, *pc) : screen_period(g, sg, P, n_phi);
     __syncthreads();
     if (!sh_sp.on) {
         fold_exact_one<double, 8, MAXT>(g, nodes, n_D, P, p, Q_out, T0_out, Didx_out, dep_out,
@@ -1237,7 +1340,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     const int64_t n_cells = n_phi * n_D;
     sh_tb[threadIdx.x] = Best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (threadIdx.x == 0) {
-        sh_cc = cell_ctx(g, P, n_phi);
+        sh_cc = TAB ? cell_ctx(g, P, *pc) : cell_ctx(g, P, n_phi);
         sh_sbest = max_key(-INFINITY);
         sh_bfk = fkey(-INFINITY);
     }
@@ -1671,7 +1774,8 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
              const unsigned long long* __restrict__ peak,
              const int* __restrict__ bucket,
              const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
-             const double* __restrict__ periods, int64_t n_P, unsigned long long* counter,
+             const double* __restrict__ periods, const PeriodConst* __restrict__ ptab,
+             int64_t n_P, unsigned long long* counter,
              double* __restrict__ Q_out, double* __restrict__ T0_out,
              int* __restrict__ Didx_out, double* __restrict__ dep_out,
              double* __restrict__ sig_out, double* __restrict__ lnp_out) {
@@ -1699,9 +1803,10 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
                 const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off,
                                     srec + fs.srec_off, lwin + fs.srec_off, fs.n_slots,
                                     reg + 2 * g, fs.screen, peak + g};
-                fold_screened_one<MAXT>(gg, sg, (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
-                                  periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
-                                  lnp_out);
+                fold_screened_one<MAXT, true>(gg, sg,
+                                              (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
+                                              periods[p], o, Q_out, T0_out, Didx_out, dep_out,
+                                              sig_out, lnp_out, ptab + p);
             }
             else
                 fold_exact_one<float, 8, MAXT>(gg, (const Node8<float>*)nodes + fs.s_off * n_D, n_D,
@@ -1938,7 +2043,7 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
     k_fold_batch<KIND_, MAXT_><<<grid, MAXT_, 0, st>>>(                                  \
         segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.peak,    \
         fs.bucket,                                                                         \
-        fs.rec, n_D, dt, gap_factor, periods, n_P, CTR_, Q, T0, Didx, dep, sig, lnp)
+        fs.rec, n_D, dt, gap_factor, periods, fs.ptab, n_P, CTR_, Q, T0, Didx, dep, sig, lnp)
 #define NU_FB_SIZE(KIND_, CTR_)                                                            \
     do {                                                                                   \
         if (threads <= 64) NU_FB(KIND_, 64, CTR_);                                         \
@@ -1946,9 +2051,11 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
         else NU_FB(KIND_, 256, CTR_);                                                      \
     } while (0)
     if (fb.any_exact) {
-        if (fp64)
+        if (fp64) {
+            k_period_consts<<<div_up(n_P, 256), 256, 0, st>>>(periods, n_P, dt, fs.ptab);
+            ++launched;
             NU_FB_SIZE(0, counter);
-        else
+        } else
             NU_FB_SIZE(1, counter);
         ++launched;
     }
