@@ -73,7 +73,7 @@ FOLD_FLOPS_PER_VISIT = 55.0    # 25 in pass 1 + 30 in pass 2 (one log per visit)
 # DRAM bytes (read + write) of one fold launch on the bench workload (sector_19440,
 # FP64), from an ncu capture of the kernel as it stands
 # (profiles/k_fold_screened_sector_19440.md); other workloads report None
-FOLD_TRAFFIC_BYTES = {"sector_19440": 26942720}
+FOLD_TRAFFIC_BYTES = {"sector_19440": 26802176}
 FLUSH_BYTES = 512 << 20        # > 129 MB L2
 
 
