@@ -42,7 +42,7 @@ struct Blocks {
 
 // Keep freed stream-ordered allocations in the current device's default
 // memory pool (instead of returning them at every synchronisation), so that
-// repeated calls reuse memory without driver allocations.
+// repeated calls reuse memory without new device allocations.
 void pool_keep_memory();
 
 // Number of kernels this library has launched (nu_launch_count).
