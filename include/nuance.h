@@ -22,9 +22,11 @@
  *   - The return value is a nu_status; on anything but NU_OK a message is
  *     available from nu_last_error() in the calling thread.  Argument errors
  *     are detected on the host before any work is enqueued.  Errors that only
- *     the device can see (a non-positive pivot of the factor, unsorted times,
- *     a wait that ran out) are written to a status word that the next
- *     synchronising call (nu_factor_info, nu_batch_search) reads back.
+ *     the device can see (a non-positive pivot of the factor, unsorted times)
+ *     are written to a status word that the next synchronising call
+ *     (nu_factor_info, nu_batch_search) reads back.  No kernel of this library
+ *     waits on a flag set by another kernel or another device: persistent
+ *     kernels take work from an atomic counter and never spin.
  *   - The library keeps no global state except the thread-local error
  *     message; a nu_factor may be used from any thread but not concurrently.
  */
@@ -43,7 +45,8 @@ typedef enum {
     NU_ENOTPD = 2,    /* covariance not positive definite (pivot <= 0 or NaN)  */
     NU_ECUDA = 3,     /* a CUDA runtime call failed                            */
     NU_ENOMEM = 4,    /* device allocation failed                              */
-    NU_ETIMEOUT = 5   /* a bounded device wait ran out                         */
+    NU_ETIMEOUT = 5   /* reserved for a bounded device wait; no call of this
+                         version returns it (no kernel waits on a flag)         */
 } nu_status;
 
 typedef enum {
@@ -192,7 +195,7 @@ nu_status nu_periodic_search(const double* t0s_dev, int64_t n_t0,
                              double* lnP_dev);
 
 /* Masking of a found transit for the next search of a multi-planet system
- * (Sect. 3.5 and the TOI-540 comparison, Sect. 4.3: after a periodic search,
+ * (Sect. 2.5 and the TOI-540 comparison, Sect. 3.3: after a periodic search,
  * the linear-search products of the trial epochs in windows of width 2 D
  * centred on the detected transits are masked and the periodic search is
  * run again on the same grid).
@@ -279,8 +282,15 @@ nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev, const doub
  * them).  This call makes no cudaMalloc/cudaFree or other allocating call.
  *   - phase_step must be > 0 (the median-spacing default would need a host
  *     buffer).
+ *   - The array of the device that `stream` belongs to is used; that device
+ *     must be the current device and hold t0s_dev, else NU_EINVAL.
  *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *     that device current and keeps it for the process; make that first call
+ *     before any stream capture on the device.  After cudaDeviceReset the kept
+ *     address is stale: do not call this function again in that process.
+ *   - Every call copies the first and last epoch to the host and therefore
+ *     synchronises `stream`; the mixed-precision path reads one more flag
+ *     back in the same way.
  *   - Every call on a device shares the one array, which keeps the previous
  *     call's contents; the call clears what must start at zero.  Calls whose
  *     work overlaps on the GPU (different streams, threads or processes using

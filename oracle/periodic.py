@@ -163,8 +163,8 @@ def best(res, periods):
 
 
 def mask_transits(t0s, depth, var, dlnl, P, T0, half_width):
-    """Masking of a found candidate before the next search (Sect. 3.5, and
-    the TOI-540 comparison of Sect. 4.3: trial epochs in windows of width
+    """Masking of a found candidate before the next search (Sect. 2.5, and
+    the TOI-540 comparison of Sect. 3.3: trial epochs in windows of width
     2 D centred on the detected transits are masked in the linear-search
     products).  Entries of every duration whose epoch lies within
     half_width of T0 + n P (n the nearest integer, each operation rounded

@@ -304,10 +304,13 @@ def nu_periodic_search_noalloc(t0s, Ds, depth, var, dlnl, periods, precision="fp
                                phase_step=0.0, gap_factor=1.5, stream=None):
     """nu_periodic_search with the library's fixed scratch array (no device
     allocation inside the library call; phase_step must be > 0).  The output
-    tensors are still allocated here, by the caller side of the ABI."""
-    return nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision=precision,
-                              phase_step=phase_step, gap_factor=gap_factor, stream=stream,
-                              _entry=LIB.nu_periodic_search_noalloc)
+    tensors are still allocated here, by the caller side of the ABI.  The call
+    runs with the device of t0s current (the library uses the scratch array
+    of the current device and refuses a stream of another device)."""
+    with torch.cuda.device(t0s.device):
+        return nu_periodic_search(t0s, Ds, depth, var, dlnl, periods, precision=precision,
+                                  phase_step=phase_step, gap_factor=gap_factor, stream=stream,
+                                  _entry=LIB.nu_periodic_search_noalloc)
 
 
 def nu_periodic_search_noalloc_limit():

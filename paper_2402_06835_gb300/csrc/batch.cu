@@ -240,6 +240,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     // the enqueue of everything after setup (graph body)
     cudaStream_t side = thread_side_stream();
+    cudaError_t enq_err = cudaSuccess;      // first failed enqueue of a memset
     auto enqueue = [&](int grid, int threads, int64_t nP_run, int n_run,
                        cudaStream_t st) -> int {
         int l = 0;
@@ -257,9 +258,14 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
             l += launch_window_batch(nb, false, t_dev, k, &fv, s_off_dev, n_lc, N, Ds_dev, n_D,
                                      lin_d, lin_v, lin_l, st);
         }
-        l += launch_fold_prep(fbat, fsegs, s_off_dev, n_lc, N, fp64, t_dev, lin_d, lin_v,
-                              lin_l, n_D, phase_step, gap_factor, fsc, st);
-        cudaMemsetAsync(ctr, 0, 16, st);
+        int lp = 0;
+        const cudaError_t ep = launch_fold_prep(fbat, fsegs, s_off_dev, n_lc, N, fp64, t_dev,
+                                                lin_d, lin_v, lin_l, n_D, phase_step, gap_factor,
+                                                fsc, st, &lp);
+        l += lp;
+        if (ep != cudaSuccess && enq_err == cudaSuccess) enq_err = ep;
+        const cudaError_t ec = cudaMemsetAsync(ctr, 0, 16, st);
+        if (ec != cudaSuccess && enq_err == cudaSuccess) enq_err = ec;
         l += launch_fold_batch(fbat, fsegs, n_run, N, fp64, t_dev, fsc, n_D,
                                phase_step, gap_factor, periods_dev, nP_run, ctr, grid, threads,
                                Q_dev, T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev,
@@ -294,6 +300,12 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         launched += enqueue(n_sm * 2, 256, nP_run, n_run, st);    // warm the caches
+        if (enq_err != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cleanup();
+            return cuda_fail(enq_err, "nu_batch_search: memset");
+        }
         for (int c = 0; c < 6; ++c) {
             cudaMemsetAsync(ctr, 0, 16, st);
             cudaEventRecord(e0, st);
@@ -330,6 +342,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     if (e == cudaSuccess) {
         in_graph = enqueue(n_sm * tv.blocks_per_sm, tv.threads, n_P, n_lc, cs);
         e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess && enq_err != cudaSuccess) e = enq_err;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);

@@ -91,10 +91,14 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
                      const std::vector<double>& t_last, const std::vector<int>& irregular,
                      bool fp64, double dt, double gap_factor, int n_D, FoldBatch& fb);
 
-int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t* s_off_dev,
-                     int n_seg, int64_t n_total, bool fp64, const double* t, const void* depth,
-                     const void* var, const void* gain, int n_D, double dt, double gap_factor,
-                     const FoldScratch& fs, cudaStream_t st);
+// Enqueues the fold's preparation kernels; returns the first error of an
+// enqueued memset (the launches are checked by the caller) and the number of
+// kernels launched in *n_launched.
+cudaError_t launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev,
+                             const int64_t* s_off_dev, int n_seg, int64_t n_total, bool fp64,
+                             const double* t, const void* depth, const void* var,
+                             const void* gain, int n_D, double dt, double gap_factor,
+                             const FoldScratch& fs, cudaStream_t st, int* n_launched);
 
 int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
                       int64_t n_total, bool fp64, const double* t, const FoldScratch& fs,

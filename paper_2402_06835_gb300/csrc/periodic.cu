@@ -1976,24 +1976,37 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
     }
 }
 
-int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t* s_off_dev,
-                     int n_seg, int64_t n_total, bool fp64, const double* t, const void* depth,
-                     const void* var, const void* gain, int n_D, double dt, double gap_factor,
-                     const FoldScratch& fs, cudaStream_t st) {
+cudaError_t launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev,
+                             const int64_t* s_off_dev, int n_seg, int64_t n_total, bool fp64,
+                             const double* t, const void* depth, const void* var,
+                             const void* gain, int n_D, double dt, double gap_factor,
+                             const FoldScratch& fs, cudaStream_t st, int* n_launched) {
     int launched = 0;
+    *n_launched = 0;
     const int64_t ngrid = n_total * (int64_t)n_D;
+    cudaError_t e = cudaSuccess;
     if (fb.any_exact) {
         if (fp64) {
             const ExactLayout L = exact_layout(n_total, n_D, true);
             k_nodes_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
                 n_seg, s_off_dev, n_D, gap_factor * dt, (Node8<double>*)fs.nodes);
-            cudaMemsetAsync(fs.reg, 0, (size_t)n_seg * 2 * sizeof(unsigned), st);
+            ++launched;
+            e = cudaMemsetAsync(fs.reg, 0, (size_t)n_seg * 2 * sizeof(unsigned), st);
+            if (e != cudaSuccess) {
+                *n_launched = launched;
+                return e;
+            }
             k_slot_offsets_batch<<<div_up(n_total, 256), 256, 0, st>>>(
                 t, segs_dev, n_seg, s_off_dev, 1.0 / dt, fs.slot_of, fs.reg);
             k_fill_screen<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(
                 fs.srec, fb.n_srec_total);
-            cudaMemsetAsync(fs.lslot, 0, (size_t)(fb.n_srec_total + 1) * sizeof(float), st);
+            launched += 2;
+            e = cudaMemsetAsync(fs.lslot, 0, (size_t)(fb.n_srec_total + 1) * sizeof(float), st);
+            if (e != cudaSuccess) {
+                *n_launched = launched;
+                return e;
+            }
             k_screen_batch<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
                 n_seg, s_off_dev, n_D, gap_factor * dt, dt,
@@ -2001,17 +2014,24 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
                 (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.lslot, fs.slot_of);
             k_lwin<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(fs.lslot, fb.n_srec_total,
                                                                     fs.lwin);
-            cudaMemsetAsync(fs.peak, 0, (size_t)n_seg * sizeof(unsigned long long), st);
+            launched += 2;
+            e = cudaMemsetAsync(fs.peak, 0, (size_t)n_seg * sizeof(unsigned long long), st);
+            if (e != cudaSuccess) {
+                *n_launched = launched;
+                return e;
+            }
             k_gain_peak<<<dim3(n_seg, 1), 256, 0, st>>>((const double*)gain, s_off_dev, 0, n_D,
                                                        fs.peak);
-            launched += 5;
-        } else
+            ++launched;
+        } else {
             k_nodes_batch<float><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
                 s_off_dev, n_D, gap_factor * dt, (Node8<float>*)fs.nodes);
+            ++launched;
+        }
         k_buckets_batch<<<div_up(fb.n_bucket_total, 256), 256, 0, st>>>(
             t, segs_dev, n_seg, fb.n_bucket_total, dt, fs.bucket);
-        launched += 2;
+        ++launched;
     }
     if (fb.any_slots) {
         k_fill_nan<<<div_up(fb.n_rec_total, 256), 256, 0, st>>>(fs.rec, fb.n_rec_total);
@@ -2020,7 +2040,8 @@ int launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev, const int64_t
             s_off_dev, n_D, 1.0 / dt, fs.rec);
         launched += 2;
     }
-    return launched;
+    *n_launched = launched;
+    return cudaSuccess;
 }
 
 // The persistent fold kernels; counter[0..1] must be zero.  blocks_per_sm
@@ -2436,10 +2457,26 @@ std::mutex g_scratch_mu;
 void* g_scratch_ptr[64] = {};
 }
 
-static nu_status noalloc_scratch(void** out) {
-    int dev = 0;
+// The scratch of the device that runs the call: the stream's device, which
+// must be the current device (the symbol lookup and the launches use the
+// current device) and must hold the epochs.
+static nu_status noalloc_scratch(cudaStream_t st, const void* t0s_dev, void** out) {
+    int dev = 0, sdev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: cudaGetDevice");
+    e = cudaStreamGetDevice(st, &sdev);
+    if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_search_noalloc: cudaStreamGetDevice");
+    if (sdev != dev)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: the stream belongs to device %d but "
+                               "device %d is current; make the stream's device current", sdev,
+                    dev);
+    cudaPointerAttributes pa;
+    e = cudaPointerGetAttributes(&pa, t0s_dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "nu_periodic_search_noalloc: cudaPointerGetAttributes");
+    if (pa.type == cudaMemoryTypeDevice && pa.device != dev)
+        return fail(NU_EINVAL, "nu_periodic_search_noalloc: t0s is on device %d, the call runs "
+                               "on device %d", pa.device, dev);
     if (dev < 0 || dev >= 64)
         return fail(NU_EINVAL, "nu_periodic_search_noalloc: device index %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -2473,10 +2510,10 @@ extern "C" nu_status nu_periodic_search_noalloc(const double* t0s_dev, int64_t n
     if (s != NU_OK) return s;
     if (!(phase_step > 0.0) || !std::isfinite(phase_step))
         return fail(NU_EINVAL, "nu_periodic_search_noalloc: phase_step must be given (> 0)");
-    void* base = nullptr;
-    s = noalloc_scratch(&base);
-    if (s != NU_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    void* base = nullptr;
+    s = noalloc_scratch(st, t0s_dev, &base);
+    if (s != NU_OK) return s;
     double ends[2];
     cudaError_t e = cudaMemcpyAsync(&ends[0], t0s_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)

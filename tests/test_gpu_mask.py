@@ -1,5 +1,5 @@
 """GPU parity of nu_mask_transits (the masking step of the multi-planet
-search, Sect. 3.5 and Sect. 4.3) and of a second search after masking."""
+search, Sect. 2.5 and Sect. 3.3) and of a second search after masking."""
 import numpy as np
 import pytest
 
@@ -89,7 +89,7 @@ def test_second_planet_after_masking():
 
 
 def test_per_sector_factors_with_one_fold():
-    """The paper's multi-sector mode (Sect. 4.3): each sector gets its own GP
+    """The paper's multi-sector mode (Sect. 3.3): each sector gets its own GP
     factor and linear search, and one periodic search runs over the
     concatenated (t0, D) grids.  Both sides do the same; the periodograms
     agree and the common planet is found."""

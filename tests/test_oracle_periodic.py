@@ -228,7 +228,7 @@ def test_no_valid_cell():
 
 
 def test_mask_transits_matches_nearest_transit_distance():
-    """The oracle's mask (Sect. 4.3: windows of width 2 D centred on the
+    """The oracle's mask (Sect. 3.3: windows of width 2 D centred on the
     detected transits) equals the brute-force minimum distance to any
     transit T0 + n P, away from ties at the window edge."""
     rng = np.random.default_rng(91)
@@ -247,7 +247,7 @@ def test_mask_transits_matches_nearest_transit_distance():
 
 
 def test_mask_then_search_finds_the_second_planet():
-    """Multi-planet search on the oracle (Sect. 3.5): on a white-noise grid
+    """Multi-planet search on the oracle (Sect. 2.5): on a white-noise grid
     with two injected periodic signals the first search finds the stronger,
     and after masking its transits the second search finds the other."""
     rng = np.random.default_rng(5)

@@ -80,3 +80,17 @@ def test_noalloc_requires_explicit_phase_step():
     with pytest.raises(api.NuanceError):
         api.nu_periodic_search_noalloc(cu(t0s), np.ones(5), cu(g["depth"]), cu(g["var"]),
                                        cu(g["dlnl"]), cu([0.3]), phase_step=0.0)
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs two GPUs")
+def test_noalloc_refuses_a_stream_of_another_device():
+    """The fixed array of the current device is used; a stream that belongs to
+    another device is refused before any work is enqueued."""
+    t0s, g, dt = _grid(0.0)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
+    args = (cu(t0s), np.ones(5), cu(g["depth"]), cu(g["var"]), cu(g["dlnl"]), cu([0.3]))
+    other = torch.cuda.Stream(device="cuda:1")
+    with torch.cuda.device(0), pytest.raises(api.NuanceError) as exc:
+        api.nu_periodic_search(*args, phase_step=dt, stream=other,
+                               _entry=api.LIB.nu_periodic_search_noalloc)
+    assert exc.value.status == api.NU_EINVAL
