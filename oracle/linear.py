@@ -30,6 +30,13 @@ A (so that X'^T Sigma^-1 X' = R^T R is never formed and its condition number
 is not squared), and the chi-square of Eq. linear_search_ll is the squared
 norm of the whitened residual.  No blocking, recursion or closed form of the
 CUDA path is used.
+
+For a whole grid of box templates on a long light curve (tens of thousands of
+samples), whitening every template costs O(N^2) each; ``box_grid`` takes the
+other dense route: Sigma^-1 once (N^3), then per template the window's block
+sum of Sigma^-1 and the elimination of the transit column from the normal
+equations (O(L^2) per template).  It is pinned to the brute force, the
+weighted-BLS closed form, noiseless recovery and the QR route.
 """
 from __future__ import annotations
 
@@ -198,3 +205,76 @@ def sampled_linear_search(model, t0s, Ds, pairs, kind="box", ingress_frac=0.1,
     M = np.stack([template(model.t, t0s[i], Ds[j], kind, ingress_frac, ld)
                   for (j, i) in pairs], axis=1)
     return model.fit_templates(M)
+
+
+def box_windows(t, t0s, D):
+    """Sample index range [lo, hi) of the box window of each epoch: the
+    samples with t0 - D/2 <= t < t0 + D/2 (both ends evaluated in FP64 as
+    written)."""
+    t = np.asarray(t, dtype=np.float64)
+    t0s = np.asarray(t0s, dtype=np.float64)
+    lo = np.searchsorted(t, t0s - D * 0.5, side="left")
+    hi = np.searchsorted(t, t0s + D * 0.5, side="left")
+    return lo, hi
+
+
+def box_grid(model, t0s, Ds):
+    """Sect. 2.2 for the box template on a whole (t0s x Ds) grid, for light
+    curves whose every template cannot be whitened one by one.
+
+    Route (the dense alternative for long curves): Sigma^-1 is formed once
+    from the Cholesky factor (LAPACK dpotri), and Eq. ls for X' = [X, m] is
+    solved by eliminating the transit column (block Gaussian elimination of
+    the (k+1) x (k+1) normal matrix):
+        c   = m^T Sigma^-1 m   = the sum of the window's block of Sigma^-1
+                                  (m = -1 on the window, 0 elsewhere),
+        b   = X^T Sigma^-1 m   = -(column sums of Sigma^-1 X over the window),
+        num = m^T Sigma^-1 r0  = -(sum of Sigma^-1 r0 over the window),
+              r0 = f - X w_null the residual of the transit-free fit,
+        s   = c - b^T (X^T Sigma^-1 X)^-1 b,
+        depth = num / s, var = 1 / s (the last diagonal entry of
+        (X'^T Sigma^-1 X')^-1), gain = depth^2 / (2 var), which is
+        ln L - ln L_null of Eq. linear_search_ll at the GLS weights.
+    The transit-free fit w_null is the model's (QR of the whitened X).
+    Returns depth, var, dlnl of shape (n_D, n_t0); an empty window (or
+    s <= 0) gives NaN.
+    """
+    from scipy.linalg import lapack
+
+    t0s = np.asarray(t0s, dtype=np.float64)
+    Ds = np.asarray(Ds, dtype=np.float64)
+    C = model.C
+    inv, info = lapack.dpotri(C, lower=1)       # lower triangle of Sigma^-1
+    if info != 0:
+        raise np.linalg.LinAlgError(f"dpotri failed ({info})")
+    yw = model.yw
+    if model.k:
+        w0, _ = _ols_qr(model.Xw[None], yw[None])
+        r0w = yw - model.Xw @ w0[0]
+        SX = solve_triangular(C, model.Xw, lower=True, trans="T")    # Sigma^-1 X
+        A = model.Xw.T @ model.Xw                                    # X^T Sigma^-1 X
+    else:
+        r0w = yw
+    z0 = solve_triangular(C, r0w, lower=True, trans="T")              # Sigma^-1 r0
+    out = {name: np.full((len(Ds), len(t0s)), np.nan) for name in ("depth", "var", "dlnl")}
+    for j, D in enumerate(Ds):
+        lo, hi = box_windows(model.t, t0s, D)
+        for i in range(len(t0s)):
+            a, b_ = int(lo[i]), int(hi[i])
+            if b_ <= a:
+                continue
+            blk = inv[a:b_, a:b_]
+            c = 2.0 * np.tril(blk).sum() - np.trace(blk)
+            num = -z0[a:b_].sum()
+            s = c
+            if model.k:
+                bx = -SX[a:b_].sum(axis=0)
+                s = c - bx @ np.linalg.solve(A, bx)
+            if not s > 0.0:
+                continue
+            out["depth"][j, i] = num / s
+            out["var"][j, i] = 1.0 / s
+            out["dlnl"][j, i] = 0.5 * num * num / s
+    out["logdet"] = model.logdet
+    out["lnL_null"] = model.lnL_null
+    return out

@@ -230,3 +230,88 @@ def test_empty_window_gives_nan():
                                np.array([gap_mid]), np.array([0.01]))
     assert np.isnan(res["depth"][0, 0]) and np.isnan(res["var"][0, 0])
     assert np.isnan(res["dlnl"][0, 0])
+
+
+# --------------------------------------- whole-grid route (explicit Sigma^-1)
+def test_box_grid_brute_force_tiny():
+    """The block-elimination route against the extended-precision brute force."""
+    lc = synth.small_curve(n=48, seed=3, p_rot=0.2)
+    t, y, dv = lc.t, lc.y, lc.diag_var
+    terms = lc.terms + [(gp.EXP, (2e-3, 0.05))]
+    Sigma = gp.covariance(t, dv, terms)
+    t0s = t[[0, 5, 20, 33, 46, 47]]
+    Ds = np.array([0.003, 0.02, 0.05])
+    model = linear.DenseModel(t, y, dv, terms, lc.X)
+    res = linear.box_grid(model, t0s, Ds)
+    for j, D in enumerate(Ds):
+        for i, t0 in enumerate(t0s):
+            m = linear.box_template(t, t0, D)
+            d, v, l = _brute_force(Sigma, lc.X, y, m)
+            sd = np.sqrt(v)
+            assert rel_err(res["depth"][j, i], d, max(abs(d), sd)) < 1e-12
+            assert rel_err(res["var"][j, i], v, v) < 1e-12
+            assert rel_err(res["dlnl"][j, i], l, max(l, 1.0)) < 1e-12
+
+
+def test_box_grid_white_noise_is_weighted_bls():
+    rng = np.random.default_rng(13)
+    n = 500
+    t = np.arange(n) * synth.CADENCE_DAYS
+    dv = rng.uniform(0.5e-6, 3e-6, n)
+    y = 1.0 + rng.standard_normal(n) * np.sqrt(dv)
+    X = np.ones((n, 1))
+    Ds = np.array([0.01, 0.05, 0.11])
+    res = linear.box_grid(linear.DenseModel(t, y, dv, [], X), t, Ds)
+    w = 1.0 / dv
+    for j, D in enumerate(Ds):
+        for i in (0, 1, 37, 150, 250, 498, 499):
+            t0 = t[i]
+            inside = (t >= t0 - D / 2) & (t < t0 + D / 2)
+            W_in, W_out = w[inside].sum(), w[~inside].sum()
+            depth = ((w[~inside] * y[~inside]).sum() / W_out
+                     - (w[inside] * y[inside]).sum() / W_in)
+            var = 1.0 / W_in + 1.0 / W_out
+            assert res["depth"][j, i] == pytest.approx(depth, rel=1e-10, abs=1e-12)
+            assert res["var"][j, i] == pytest.approx(var, rel=1e-12)
+            assert res["dlnl"][j, i] == pytest.approx(0.5 * depth ** 2 / var,
+                                                      rel=1e-8, abs=1e-10)
+
+
+def test_box_grid_noiseless_recovery():
+    """y = X w* + Delta* m(t0*, D*) exactly: the grid's cell at (t0*, D*)
+    returns Delta* under a correlated covariance."""
+    lc = synth.small_curve(n=300, seed=5, gap=30)
+    t = lc.t
+    t0, D, delta = t[77], 0.05, 2.5e-3
+    y = lc.X @ np.array([1.0, -3e-3]) + delta * linear.box_template(t, t0, D)
+    model = linear.DenseModel(t, y, lc.diag_var, lc.terms, lc.X)
+    res = linear.box_grid(model, t[[76, 77, 78]], np.array([D]))
+    assert res["depth"][0, 1] == pytest.approx(delta, rel=1e-12)
+    assert np.isfinite(res["var"][0]).all()
+
+
+@pytest.mark.parametrize("case", ["rotation", "rotation+exp", "sho_overdamped", "white"])
+@pytest.mark.parametrize("design", [True, False])
+def test_box_grid_matches_qr_route(case, design):
+    """Both dense routes (QR of every whitened template; block elimination
+    with the explicit inverse) on a gapped curve, epochs in the gap and
+    beyond both ends included."""
+    lc = synth.small_curve(n=360, seed=21, gap=40, design=design)
+    terms = {"rotation": lc.terms,
+             "rotation+exp": lc.terms + [(gp.EXP, (2e-3, 0.08))],
+             "sho_overdamped": [(gp.SHO, (5e-3, 30.0, 0.3))],
+             "white": []}[case]
+    X = lc.X if design else np.zeros((len(lc.t), 0))
+    Ds = np.array([0.004, 0.035, 0.09])
+    t0s = np.concatenate([lc.t, [0.5 * (lc.t[179] + lc.t[180]), lc.t[0] - 0.01,
+                                 lc.t[-1] + 0.02]])
+    model = linear.DenseModel(lc.t, lc.y, lc.diag_var, terms, X)
+    g = linear.box_grid(model, t0s, Ds)
+    o = linear.linear_search(lc.t, lc.y, lc.diag_var, terms, X, t0s, Ds, model=model)
+    for a, b in ((g["depth"], o["depth"]), (g["var"], o["var"]), (g["dlnl"], o["dlnl"])):
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+    ok = ~np.isnan(o["depth"])
+    so = np.sqrt(o["var"][ok])
+    assert np.max(rel_err(g["depth"][ok], o["depth"][ok], np.maximum(np.abs(o["depth"][ok]), so))) < 1e-11
+    assert np.max(rel_err(g["var"][ok], o["var"][ok], o["var"][ok])) < 1e-11
+    assert np.max(rel_err(g["dlnl"][ok], o["dlnl"][ok], np.maximum(o["dlnl"][ok], 1.0))) < 1e-10
