@@ -256,25 +256,38 @@ def box_grid(model, t0s, Ds):
     else:
         r0w = yw
     z0 = solve_triangular(C, r0w, lower=True, trans="T")              # Sigma^-1 r0
+    N = model.N
+    diag = {}
+
+    def band(d):
+        """(Sigma^-1)[a + d, a] for a = 0 .. N-d-1 (from the lower triangle)."""
+        if d not in diag:
+            diag[d] = np.ascontiguousarray(np.diagonal(inv, offset=-d))
+        return diag[d]
+
     out = {name: np.full((len(Ds), len(t0s)), np.nan) for name in ("depth", "var", "dlnl")}
     for j, D in enumerate(Ds):
         lo, hi = box_windows(model.t, t0s, D)
-        for i in range(len(t0s)):
-            a, b_ = int(lo[i]), int(hi[i])
-            if b_ <= a:
-                continue
-            blk = inv[a:b_, a:b_]
-            c = 2.0 * np.tril(blk).sum() - np.trace(blk)
-            num = -z0[a:b_].sum()
+        L = hi - lo
+        for Lv in np.unique(L[L > 0]):
+            sel = np.nonzero(L == Lv)[0]
+            a0 = lo[sel][:, None]
+            win = a0 + np.arange(Lv)[None, :]
+            # block sum of Sigma^-1 over the window, diagonal by diagonal:
+            # the main diagonal once, every off-diagonal twice (symmetry)
+            c = band(0)[win].sum(axis=1)
+            for d in range(1, int(Lv)):
+                c = c + 2.0 * band(d)[a0 + np.arange(Lv - d)[None, :]].sum(axis=1)
+            num = -z0[win].sum(axis=1)
             s = c
             if model.k:
-                bx = -SX[a:b_].sum(axis=0)
-                s = c - bx @ np.linalg.solve(A, bx)
-            if not s > 0.0:
-                continue
-            out["depth"][j, i] = num / s
-            out["var"][j, i] = 1.0 / s
-            out["dlnl"][j, i] = 0.5 * num * num / s
+                bx = -SX[win].sum(axis=1)                       # (n_sel, k)
+                s = c - np.einsum("bk,bk->b", bx, np.linalg.solve(A, bx.T).T)
+            ok = s > 0.0
+            i = sel[ok]
+            out["depth"][j, i] = num[ok] / s[ok]
+            out["var"][j, i] = 1.0 / s[ok]
+            out["dlnl"][j, i] = 0.5 * num[ok] * num[ok] / s[ok]
     out["logdet"] = model.logdet
     out["lnL_null"] = model.lnL_null
     return out

@@ -6,6 +6,10 @@ is meaningless):
   var:   |v - v_or| / v_or
   gain:  |g - g_or| / max(g_or, 1)
 NaN must appear at the same places on both sides.
+
+The fold's per-period outputs are compared at the argmax cell: ln P and Q,
+and the combined depth Delta (norm |D - D_or| / max(|D_or|, sigma_or)) and its
+sigma (relative) of Eq. sigma_delta.
 """
 import numpy as np
 
@@ -36,12 +40,16 @@ def phase_index(T0, t_ref, P, n_phi):
 
 
 def periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, dt, tol_lnp,
-                     tol_q, fold_fn, max_reeval=200, q_abs=False):
+                     tol_q, fold_fn, max_reeval=200, q_abs=False, tol_ds=None):
     """Compare per-period results; near-ties in the argmax are checked by
-    evaluating the oracle at the GPU's cell.  Returns (worst lnP error,
-    worst Q error, number of periods whose argmax cell differs)."""
+    evaluating the oracle at the GPU's cell.  ln P, Q, the fold's depth and
+    sigma are compared (tol_ds, default tol_lnp, on depth and sigma).
+    Returns (worst lnP error, worst Q error, number of periods whose argmax
+    cell differs); the worst depth and sigma errors are in
+    periodic_compare.last."""
+    tol_ds = tol_lnp if tol_ds is None else tol_ds
     g = {k: np.asarray(v) for k, v in gpu.items()}
-    worst_l = worst_q = 0.0
+    worst_l = worst_q = worst_d = worst_s = 0.0
     differ = 0
     for p, P in enumerate(periods):
         lo_, lg_ = ora["lnP"][p], g["lnP"][p]
@@ -55,7 +63,7 @@ def periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, dt, tol_lnp,
         jg = phase_index(g["T0"][p], t0s[0], P, n_phi)
         dg = int(g["D_idx"][p])
         if dg == ora["D_idx"][p] and jg == ora["phase_idx"][p]:
-            eq = abs(g["Q"][p] - ora["Q"][p]) / (1.0 if q_abs else max(1.0, abs(ora["Q"][p])))
+            q_o, d_o, s_o = ora["Q"][p], ora["depth"][p], ora["sigma"][p]
         else:
             differ += 1
             assert differ <= max_reeval, "too many argmax differences"
@@ -63,8 +71,20 @@ def periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, dt, tol_lnp,
             l_cell = f["lnP"][dg, jg]
             assert abs(l_cell - lo_) / max(1.0, abs(lo_)) <= tol_lnp, (
                 f"period {P}: GPU cell ({dg},{jg}) lnP {l_cell} is not a tie of {lo_}")
-            q_cell = f["depth"][dg, jg] / f["sigma"][dg, jg]
-            eq = abs(g["Q"][p] - q_cell) / (1.0 if q_abs else max(1.0, abs(q_cell)))
+            d_o, s_o = f["depth"][dg, jg], f["sigma"][dg, jg]
+            q_o = d_o / s_o
+        eq = abs(g["Q"][p] - q_o) / (1.0 if q_abs else max(1.0, abs(q_o)))
         worst_q = max(worst_q, eq)
-        assert eq <= tol_q, f"period {P}: Q {g['Q'][p]} vs oracle"
+        assert eq <= tol_q, f"period {P}: Q {g['Q'][p]} vs oracle {q_o}"
+        if "depth" in g and "sigma" in g:
+            ed = abs(g["depth"][p] - d_o) / max(abs(d_o), s_o)
+            es = abs(g["sigma"][p] - s_o) / s_o
+            worst_d, worst_s = max(worst_d, ed), max(worst_s, es)
+            assert ed <= tol_ds, f"period {P}: depth {g['depth'][p]} vs oracle {d_o}"
+            assert es <= tol_ds, f"period {P}: sigma {g['sigma'][p]} vs oracle {s_o}"
+    periodic_compare.last = dict(lnP=worst_l, Q=worst_q, depth=worst_d, sigma=worst_s,
+                                 ties=differ)
     return worst_l, worst_q, differ
+
+
+periodic_compare.last = {}

@@ -253,7 +253,8 @@ def test_large_period_grid_kernels(precision):
         ora_lin = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t, Ds)
         ora = periodic.periodic_search(lc.t, ora_lin["depth"], ora_lin["var"], ora_lin["dlnl"],
                                        periods[sel], dt)
-        gpu = {k: whole[k].cpu().numpy()[sel] for k in ("Q", "T0", "D_idx", "lnP")}
+        gpu = {k: whole[k].cpu().numpy()[sel] for k in ("Q", "T0", "D_idx", "lnP", "depth",
+                                                      "sigma")}
         wl, wq, _ = periodic_compare(gpu, ora, lc.t, ora_lin["depth"], ora_lin["var"],
                                      ora_lin["dlnl"], periods[sel], dt, FP64_TOL, FP64_TOL,
                                      periodic.fold_period)
