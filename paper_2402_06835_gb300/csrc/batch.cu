@@ -134,6 +134,8 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t o_Ds = off;    off += al((size_t)n_D * 8);
     const size_t o_ctr = off;   off += 256;
     const size_t o_tune = off;  off += al(512 * 8);
+    const bool win_lo = n_D <= 4096;            // window-start recursion of the box search
+    const size_t o_wplan = off; off += win_lo ? al((size_t)n_lc * window_plan_ints(n_D) * 4) : 0;
     const size_t base_bytes = off;
     char* mem = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&mem, base_bytes, st);
@@ -213,8 +215,8 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t f_srec = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(ScreenRec));
     const size_t f_slot = foff;  foff += fp64 ? al((size_t)N * sizeof(int)) : 0;
     const size_t f_reg = foff;   foff += al((size_t)n_lc * 2 * sizeof(unsigned));
-    const size_t f_lslot = foff; foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
-    const size_t f_lwin = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
+    const size_t f_lint = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
+    const size_t f_lm3 = foff;   foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
     const size_t f_peak = foff;  foff += al((size_t)n_lc * sizeof(unsigned long long));
     const size_t f_ptab = foff;  foff += al((size_t)n_P * period_const_bytes());
     e = cudaMallocAsync((void**)&fold_mem, foff, st);
@@ -230,7 +232,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const FoldScratch fsc{fold_mem + f_nodes, (int*)(fold_mem + f_buck),
                           (Node4<float>*)(fold_mem + f_rec), (ScreenRec*)(fold_mem + f_srec),
                           (int*)(fold_mem + f_slot), (unsigned*)(fold_mem + f_reg),
-                          (float*)(fold_mem + f_lslot), (float*)(fold_mem + f_lwin),
+                          (float*)(fold_mem + f_lint), (float*)(fold_mem + f_lm3),
                           (unsigned long long*)(fold_mem + f_peak),
                           (PeriodConst*)(fold_mem + f_ptab)};
     unsigned long long* ctr = (unsigned long long*)(mem + o_ctr);
@@ -249,14 +251,16 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         int lf = 0;
         launch_factor(plan, fb, ws, diag_var_dev, nullptr, 0, y_dev, st, side, &lf);
         l += lf;
+        int* wplan = win_lo ? (int*)(mem + o_wplan) : nullptr;
+        const WindowShape wsh = default_window_shape(N);
         if (fp64) {
             FactorView<double> fv{fb.F, fb.kg, fb.invD, fb.G, fb.z0, fb.Zt};
             l += launch_window_batch(nb, true, t_dev, k, &fv, s_off_dev, n_lc, N, Ds_dev, n_D,
-                                     lin_d, lin_v, lin_l, st);
+                                     wplan, wsh, lin_d, lin_v, lin_l, st);
         } else {
             FactorView<float> fv{fb.F32, fb.kg32, fb.invD32, fb.G32, fb.z032, fb.Zt32};
             l += launch_window_batch(nb, false, t_dev, k, &fv, s_off_dev, n_lc, N, Ds_dev, n_D,
-                                     lin_d, lin_v, lin_l, st);
+                                     wplan, wsh, lin_d, lin_v, lin_l, st);
         }
         int lp = 0;
         const cudaError_t ep = launch_fold_prep(fbat, fsegs, s_off_dev, n_lc, N, fp64, t_dev,

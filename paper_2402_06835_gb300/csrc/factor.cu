@@ -515,6 +515,13 @@ extern "C" nu_status nu_gp_factor(const double* t_dev, const double* diag_var_de
                           thread_side_stream(), nullptr);
     }
     cudaFreeAsync(ws, st);
+    if (s == NU_OK) {
+        e = cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            f->ready = nullptr;
+            s = cuda_fail(e, "nu_gp_factor: event");
+        }
+    }
     if (s != NU_OK) {
         cudaFreeAsync(f->mem, st);
         delete f;
@@ -556,5 +563,6 @@ extern "C" int64_t nu_factor_size(const nu_factor* f, int* k) {
 extern "C" void nu_factor_free(nu_factor* f) {
     if (!f) return;
     cudaFreeAsync(f->mem, f->stream);     // stream-ordered: no host sync
+    if (f->ready) cudaEventDestroy(f->ready);
     delete f;
 }

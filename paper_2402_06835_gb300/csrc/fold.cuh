@@ -74,8 +74,8 @@ struct FoldScratch {
     ScreenRec* srec;        // FP64 slot-indexed screening records
     int* slot_of;           // FP64: slot of every sample
     unsigned* reg;          // FP64: two words per curve (zeroed by the prep)
-    float* lslot;           // FP64: gain at each slot (rounded up), then
-    float* lwin;            //       its windowed maximum (group bound)
+    float* lint;            // FP64: largest gain of the interval at each slot
+    float* lm3;             //       and its maximum over the slot and both neighbours
     unsigned long long* peak;  // FP64: per curve, the key of its largest gain
     PeriodConst* ptab;      // FP64: per period, its curve-independent constants
 };

@@ -68,10 +68,36 @@ template <typename T> struct FactorView {
     const T* Zt;
 };
 
+// Launch shape of the linear search's window-start kernel: tlo window
+// starts per block (32, 64, 128 or 256), ch samples of the recursion per
+// staged chunk of factor rows.
+struct WindowShape {
+    int tlo, ch;
+};
+#ifndef NU_WIN_TLO_SMALL
+#define NU_WIN_TLO_SMALL 32
+#endif
+#ifndef NU_WIN_CH
+#define NU_WIN_CH 64
+#endif
+// Default shape: small curves take NU_WIN_TLO_SMALL starts per block so that
+// their few warps spread over every SM sub-partition (the FP64 recursion
+// issues one warp instruction per 64 cycles per sub-partition).
+inline WindowShape default_window_shape(int64_t n_total) {
+    return WindowShape{n_total < 152 * 128 * 2 ? NU_WIN_TLO_SMALL : 128, NU_WIN_CH};
+}
+// Ints of device scratch the window-start plan needs per curve (four
+// window variants per duration).
+inline int window_plan_ints(int n_D) { return 2 + 20 * n_D; }
+
 // Linear search of packed light curves (batch path); no allocation, no sync.
+// plan: window_plan_ints(n_D) ints of device scratch per curve for the
+// window-start kernel, or nullptr for one recursion per template.  Returns
+// the number of kernels launched.
 int launch_window_batch(int nb, bool fp64, const double* t, int k, const void* fv,
                         const int64_t* s_off, int n_seg, int64_t n_total, const double* Ds,
-                        int n_D, void* d, void* v, void* l, cudaStream_t st);
+                        int n_D, int* plan, const WindowShape& ws, void* d, void* v, void* l,
+                        cudaStream_t st);
 
 }  // namespace nu
 
@@ -91,6 +117,7 @@ struct nu_factor {
     int nb;
     int k;
     cudaStream_t stream;
+    cudaEvent_t ready;   // recorded on `stream` to order other streams after the factor
     nu::Blocks blocks;
     void* mem;
     size_t mem_bytes;

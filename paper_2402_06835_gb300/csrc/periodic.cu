@@ -727,11 +727,6 @@ k_fold_exact(FoldGeom g, const Node8<T>* __restrict__ nodes, int n_D,
 // (triangle inequality in the 1/s^2-weighted norm for q).  Overflow or NaN
 // anywhere makes the bound +inf or NaN, which never skips a cell.
 
-// Width (slots) of the gain windows of the group bound: the events of 32
-// consecutive phases at one epoch step lie in at most 36 consecutive slots
-// (31 phase steps of at most one slot, the interval's right epoch, and the
-// interval before it, which an event taken exactly may use).
-#define NU_LWIN 40
 
 struct ScreenGeom {
     const ScreenRec* rec;              // duration-major rows of n_t0 records
@@ -739,14 +734,13 @@ struct ScreenGeom {
                                        // slots from t_ref; the last .y is 2^64 - 1
     const ScreenRec* srec;             // the same records placed at their epochs'
                                        // slots: duration-major rows of n_slots
-    const float* lwin;                 // rows of n_slots: max(0, largest gain of the
-                                       // epochs in slots [s, s + NU_LWIN)), rounded up
     int64_t n_slots;
     const unsigned* reg;               // [0]: an epoch is off the slot grid,
                                        // [1]: max |offset from its slot| (float bits)
     int on;                            // screening allowed for this curve
     const unsigned long long* peak;    // key of the largest finite gain (k_gain_peak);
                                        // 0: none
+    const float* lm3;                  // rows of n_slots: k_lmax3 of the interval gains
 };
 
 // Node sigma of one (duration, epoch) in FP64 (NaN when invalid).
@@ -791,8 +785,7 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
                                             int64_t i, int64_t n, int64_t d, double gap_max,
                                             double dt, ScreenRec* __restrict__ out,
                                             ScreenRec* __restrict__ sout,
-                                            float* __restrict__ lslot, int64_t n_slots,
-                                            const int* __restrict__ slot_of,
+                                            float* __restrict__ lint, int64_t n_slots, const int* __restrict__ slot_of,
                                             ulonglong2* __restrict__ vpair) {
     // an interval needs both ends valid and a gap in (0, gap_max]
     bool v0 = i + 1 < n;
@@ -803,6 +796,7 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
     }
     ScreenRec r;
     unsigned flags = 0u;
+    float lmax = 0.f;      // largest gain an event on the interval can take
     const double d0 = (double)depth[gid], l0 = (double)gain[gid];
     r.d = (float)d0;
     r.l = (float)l0;
@@ -829,6 +823,12 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
             r.s = INFINITY;
             r.ds = 0.f;
         }
+        // the exact event's gain fma(w, l1 - l0, l0) with w in [0, 1] (to a few
+        // units of FP64 rounding) is at most max(l0, l1) + 2^-50 (|l0| + |l1|);
+        // rounded up, and +inf when the interval is not screened
+        lmax = odd ? INFINITY
+                   : __double2float_ru(fmax(0.0, fmax(l0, l1)) +
+                                       8.881784197001252e-16 * (fabs(l0) + fabs(l1)));
     } else {
         r.s = NAN;
         r.dd = 0.f;
@@ -841,9 +841,7 @@ __device__ __forceinline__ void make_screen(const T* __restrict__ depth,
     const int sl = slot_of[i];
     if (sl >= 0 && sl < n_slots) {
         sout[d * n_slots + sl] = r;
-        // gain at the slot, rounded up (an invalid epoch never adds to S_L)
-        const bool ok = !isnan(sigma_at<T>(depth, var, gain, gid));
-        lslot[d * n_slots + sl] = ok ? fmaxf(0.f, __double2float_ru(l0)) : 0.f;
+        lint[d * n_slots + sl] = lmax;
     }
     if (d == 0) {
         auto pos = [&](int64_t k) -> unsigned long long {
@@ -866,24 +864,26 @@ __global__ void k_screen(const T* __restrict__ depth, const T* __restrict__ var,
                          const T* __restrict__ gain, const double* __restrict__ t0s,
                          int64_t n_t0, int n_D, double gap_max, double dt,
                          ScreenRec* __restrict__ rec, ScreenRec* __restrict__ srec,
-                         float* __restrict__ lslot, int64_t n_slots,
+                         float* __restrict__ lint, int64_t n_slots,
                          const int* __restrict__ slot_of, ulonglong2* __restrict__ vpair) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= n_t0 * (int64_t)n_D) return;
     const int64_t d = gid / n_t0, i = gid - d * n_t0;
-    make_screen<T>(depth, var, gain, t0s, gid, i, n_t0, d, gap_max, dt, rec, srec, lslot,
-                   n_slots, slot_of, vpair);
+    make_screen<T>(depth, var, gain, t0s, gid, i, n_t0, d, gap_max, dt, rec, srec, lint, n_slots,
+                   slot_of, vpair);
 }
 
-// lwin[x] = max(0, lslot[x .. x + NU_LWIN)) over the flat array (a window that
-// runs into the next row only raises the bound).
-__global__ void k_lwin(const float* __restrict__ lslot, int64_t n, float* __restrict__ lwin) {
+// lm3[x] = max(lint[x - 1], lint[x], lint[x + 1]) over the flat array: the
+// largest gain of an event whose walk position lies in slot x (its interval
+// starts at the epoch of slot x - 1, x or x + 1, see gain_bound_cell).  A
+// neighbour in the next row only raises the bound.
+__global__ void k_lmax3(const float* __restrict__ lint, int64_t n, float* __restrict__ lm3) {
     const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (x >= n) return;
-    float m = 0.f;
-    const int64_t e = x + NU_LWIN < n ? x + NU_LWIN : n;
-    for (int64_t t = x; t < e; ++t) m = fmaxf(m, lslot[t]);
-    lwin[x] = m;
+    float m = lint[x];
+    if (x > 0) m = fmaxf(m, lint[x - 1]);
+    if (x + 1 < n) m = fmaxf(m, lint[x + 1]);
+    lm3[x] = m;
 }
 
 // Per-period constants of the screen.
@@ -1144,6 +1144,57 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
     return acc.bound(sp.cv, bf);
 }
 
+// Gain bound of a cell on a regular grid, from 4 bytes per epoch.  By the
+// bound above, ln P <= S_L + 1/2, and every event's gain is at most the
+// larger gain of its interval's two nodes.  The walk's position u of epoch k
+// lies within e_pos << 1 slot of the exact epoch, and on a regular grid every
+// epoch is within 2^-26 slot of its slot, so the exact interval starts at
+// the epoch of slot floor(u) - 1, floor(u) or floor(u) + 1: lm3 at floor(u)
+// bounds the event's gain (0 for a dropped epoch, +inf on an interval outside
+// the screen's error model).  Extra walk positions past t_last (u < uend)
+// only add terms >= 0.  The FP32 sum of K terms >= 0 is rounded up by
+// (K + 16) 2^-23 of itself, and 1e-6 covers the exact path's own rounding.
+// The walk is bound by the latency of its gathers, so four epochs' loads
+// are issued before their sums (a position past uend loads a clamped slot
+// and is not added; ustep < 2^60 keeps u + 3 ustep from wrapping).
+__device__ __forceinline__ float gain_bound_cell(const float* __restrict__ lm, unsigned ns1,
+                                                 unsigned long long u, unsigned long long ustep,
+                                                 unsigned long long uend) {
+    float s0 = 0.f, s1 = 0.f, K = 0.f;
+    const unsigned long long u4 = 4ull * ustep;
+    for (; u < uend; u += u4) {
+        const unsigned long long ua = u + ustep, ub = ua + ustep, uc = ub + ustep;
+        const float a = lm[min((unsigned)(u >> 40), ns1)];
+        const float b = lm[min((unsigned)(ua >> 40), ns1)];
+        const float c = lm[min((unsigned)(ub >> 40), ns1)];
+        const float d = lm[min((unsigned)(uc >> 40), ns1)];
+        s0 += a;
+        K += 1.f;
+        if (ua < uend) {
+            s1 += b;
+            K += 1.f;
+        }
+        if (ub < uend) {
+            s0 += c;
+            K += 1.f;
+        }
+        if (uc < uend) {
+            s1 += d;
+            K += 1.f;
+        }
+    }
+    return (s0 + s1) * fmaf(K + 16.f, 1.1920929e-7f, 1.f) + 0.5f + 1e-6f;
+}
+
+// A warp whose gain bounds pass at least NU_GAIN_PASS_MAX of its 32 cells
+// screens its next NU_GAIN_DIRECT_ROUNDS rounds in full without them.
+#ifndef NU_GAIN_PASS_MAX
+#define NU_GAIN_PASS_MAX 28
+#endif
+#ifndef NU_GAIN_DIRECT_ROUNDS
+#define NU_GAIN_DIRECT_ROUNDS 16
+#endif
+
 // Exact ln P of one cell computed by a whole warp (lanes over epochs); used
 // only to seed the pruning threshold.
 __device__ __forceinline__ double exact_cell_warp(const FoldGeom& g,
@@ -1317,6 +1368,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                                                   const PeriodConst* __restrict__ pc = nullptr) {
     __shared__ long long sh_qc[MAXT / 32][64];      // per-warp survivor queues
     __shared__ int sh_qd[MAXT / 32][64];
+    __shared__ long long sh_qa[MAXT / 32][64];      // per-warp cells for the full screen
+    __shared__ int sh_qad[MAXT / 32][64];
     __shared__ unsigned long long sh_sbest; // best ln P evaluated (max key)
     __shared__ unsigned sh_bfk;             // its FP32 lower bound (float key)
     __shared__ Best sh_tb[MAXT];            // each thread's best evaluated cell (kept
@@ -1376,12 +1429,80 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
             __syncthreads();
         }
     }
+    const unsigned FULL = 0xffffffffu;
     long long* qc = sh_qc[wid];
     int* qd = sh_qd[wid];
-    int nq = 0;                              // warp-uniform queue length
+    int nq = 0;                              // warp-uniform queue lengths
+    long long* qa = sh_qa[wid];
+    int* qad = sh_qad[wid];
+    int na = 0;
+    // Cascade on regular grids: after the warp's first round every cell is
+    // bounded from its gains alone (gain_bound_cell, 4 bytes per epoch); the
+    // cells that bound does not rule out are queued and screened in full 32
+    // at a time, and the full screen's survivors are evaluated exactly.
+    const bool cascade = sp.slots && sg.lm3 != nullptr && sp.ustep < (1ull << 60);
+    const unsigned ns1 = (unsigned)(sg.n_slots - 1);
+    // append this lane's cell to a queue when keep (positions by ballot)
+    auto push = [&](long long* qx, int* qy, int& n, bool keep, long long cl, int dl) {
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) {
+            const int pos = n + __popc(m & ((1u << lane) - 1u));
+            qx[pos] = cl;
+            qy[pos] = dl;
+        }
+        n += __popc(m);
+        __syncwarp();
+    };
+    // drop the first 32 entries of a queue
+    auto pop32 = [&](long long* qx, int* qy, int& n) {
+        n -= 32;
+        long long c2 = 0;
+        int d2 = 0;
+        if (lane < n) {
+            c2 = qx[32 + lane];
+            d2 = qy[32 + lane];
+        }
+        __syncwarp();
+        if (lane < n) {
+            qx[lane] = c2;
+            qy[lane] = d2;
+        }
+        __syncwarp();
+    };
+    // exact evaluation of the first 32 entries of the survivor queue
+    auto evaluate32 = [&]() {
+        if (coop) {
+            for (int q = 0; q < 32; ++q)
+                evaluate_queued_warp(g, nodes, c, n_phi, qc[q], qd[q], &sh_sbest, &sh_bfk,
+                                     &sh_tb[threadIdx.x]);
+        } else {
+            evaluate_queued(g, nodes, c, n_phi, qc[lane], qd[lane], &sh_sbest, &sh_bfk,
+                            &sh_tb[threadIdx.x]);
+        }
+        __syncwarp();
+        pop32(qc, qd, nq);
+    };
+    // full screen of the first cnt entries of queue A (one per lane); the
+    // survivors join the survivor queue
+    auto screen_queued = [&](int cnt) {
+        float ub = -INFINITY;
+        long long cl = 0;
+        int dl = 0;
+        if (lane < cnt) {
+            cl = qa[lane];
+            dl = qad[lane];
+            const int64_t jl = cl - (int64_t)dl * n_phi;
+            ub = screen_cell(g, sg, nodes + (int64_t)dl * g.n_t0, sg.rec + (int64_t)dl * g.n_t0,
+                             sg.srec + (int64_t)dl * sg.n_slots, sp, c, jl,
+                             (unsigned long long)jl * sp.uph, from_fkey(sh_bfk));
+        }
+        push(qc, qd, nq, lane < cnt && !(ub == -INFINITY) && !(ub < from_fkey(sh_bfk)), cl,
+             dl);
+    };
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
     bool first = true;
+    int direct = 0;                          // rounds left to screen in full directly
     for (int64_t base = (int64_t)wid * 32; base < n_cells; base += blockDim.x,
                  j += blockDim.x) {
         while (j >= n_phi) {
@@ -1390,109 +1511,69 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         }
         const int64_t cell = base + lane;
         float ub = -INFINITY;
-        bool skip = false;
-        if (!first && sp.slots && sp.ustep < (1ull << 58)) {
-            // Group bound: the warp's 32 cells, when they are consecutive
-            // phases of one duration, all have S_L <= sum over epoch steps of
-            // the largest gain in the window their events can touch, and
-            // ln P <= S_L + 1/2; if that is below the threshold, none of the
-            // 32 cells is screened.
-            const int d0 = __shfl_sync(0xffffffffu, d, 0);
-            const long long j0 = __shfl_sync(0xffffffffu, (long long)j, 0);
-            if (__all_sync(0xffffffffu, d == d0 && cell < n_cells)) {
-                const float* lw = sg.lwin + (int64_t)d0 * sg.n_slots;
-                const unsigned ns1 = (unsigned)(sg.n_slots - 1);
-                const unsigned long long st32 = 32ull * sp.ustep;
-                float sum = 0.f, cnt = 0.f;
-                for (unsigned long long u = (unsigned long long)j0 * sp.uph +
-                                            (unsigned long long)lane * sp.ustep;
-                     u < sp.uend; u += st32) {
-                    const unsigned s0 = (unsigned)(u >> 40);
-                    sum += lw[min(s0 > 0u ? s0 - 1u : 0u, ns1)];
-                    cnt += 1.f;
-                }
+        if (!first && cascade && direct == 0) {
+            float gb = -INFINITY;
+            if (cell < n_cells)
+                gb = gain_bound_cell(sg.lm3 + (int64_t)d * sg.n_slots, ns1,
+                                     (unsigned long long)j * sp.uph, sp.ustep, sp.uend);
+            const bool pass = cell < n_cells && !(gb < from_fkey(sh_bfk));
+            // where the gain bound rules out almost nothing (cells of many
+            // epochs, whose bound needs the depth terms) the warp screens
+            // its next rounds in full directly
+            if (__popc(__ballot_sync(FULL, pass)) >= NU_GAIN_PASS_MAX) direct = NU_GAIN_DIRECT_ROUNDS;
+            push(qa, qad, na, pass, cell, d);
+            if (na >= 32) {
+                screen_queued(32);
+                pop32(qa, qad, na);
+            }
+        } else {
+            if (direct > 0) --direct;
+            if (cell < n_cells)
+                ub = screen_cell(g, sg, nodes + (int64_t)d * g.n_t0,
+                                 sg.rec + (int64_t)d * g.n_t0,
+                                 sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c,
+                                 j, (unsigned long long)j * sp.uph, from_fkey(sh_bfk));
+            if (first) {
+                // seed: the warp evaluates its lane with the largest finite
+                // bound, unless that bound is already below the threshold
+                // (the cell cannot raise it)
+                first = false;
+                float v = (ub < INFINITY) ? ub : -INFINITY;
+                int src = lane;
                 for (int o = 16; o > 0; o >>= 1) {
-                    sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                    const float v2 = __shfl_xor_sync(FULL, v, o);
+                    const int s2 = __shfl_xor_sync(FULL, src, o);
+                    if (v2 > v || (v2 == v && s2 < src)) {
+                        v = v2;
+                        src = s2;
+                    }
                 }
-                // the window maxima are rounded up and non-negative: the FP32
-                // sum errs by far less than (cnt + 64) 2^-23 of itself
-                const float ubg = sum * fmaf(cnt + 64.f, 1.1920929e-7f, 1.f) + 0.5f + 1e-6f;
-                skip = ubg < from_fkey(sh_bfk);
-            }
-        }
-        if (cell < n_cells && !skip)
-            ub = screen_cell(g, sg, nodes + (int64_t)d * g.n_t0, sg.rec + (int64_t)d * g.n_t0,
-                             sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c, j,
-                             (unsigned long long)j * sp.uph, from_fkey(sh_bfk));
-        if (first) {
-            // seed: the warp evaluates its lane with the largest finite bound,
-            // unless that bound is already below the threshold (the cell
-            // cannot raise it)
-            first = false;
-            float v = (ub < INFINITY) ? ub : -INFINITY;
-            int src = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                const int s2 = __shfl_xor_sync(0xffffffffu, src, o);
-                if (v2 > v || (v2 == v && s2 < src)) {
-                    v = v2;
-                    src = s2;
+                // (the threshold is broadcast so that the branch is warp-uniform)
+                const float thr = __shfl_sync(FULL, from_fkey(sh_bfk), 0);
+                if (v > -INFINITY && !(v < thr)) {
+                    const int pd = __shfl_sync(FULL, d, src);
+                    const long long pj = __shfl_sync(FULL, (long long)j, src);
+                    const double lnp = exact_cell_warp(g, nodes + (int64_t)pd * g.n_t0, c, pj);
+                    if (lane == 0 && lnp == lnp && lnp > -INFINITY) {
+                        // a 1e-9 margin: the seeding cell itself stays above
+                        // the threshold and is evaluated again by the thread
+                        // code
+                        const double seed = lnp - 1e-9 * (1.0 + fabs(lnp));
+                        atomicMax(&sh_sbest, max_key(seed));
+                        atomicMax(&sh_bfk, fkey(__double2float_rd(seed)));
+                    }
+                    __syncwarp();
                 }
             }
-            // (the threshold is broadcast so that the branch is warp-uniform)
-            const float thr = __shfl_sync(0xffffffffu, from_fkey(sh_bfk), 0);
-            if (v > -INFINITY && !(v < thr)) {
-                const int pd = __shfl_sync(0xffffffffu, d, src);
-                const long long pj = __shfl_sync(0xffffffffu, (long long)j, src);
-                const double lnp = exact_cell_warp(g, nodes + (int64_t)pd * g.n_t0, c, pj);
-                if (lane == 0 && lnp == lnp && lnp > -INFINITY) {
-                    // a 1e-9 margin: the seeding cell itself stays above the
-                    // threshold and is evaluated again by the thread code
-                    const double seed = lnp - 1e-9 * (1.0 + fabs(lnp));
-                    atomicMax(&sh_sbest, max_key(seed));
-                    atomicMax(&sh_bfk, fkey(__double2float_rd(seed)));
-                }
-                __syncwarp();
-            }
+            // a cell without events (bound -inf) is never the argmax; NaN
+            // survives.  The FP32 threshold is at most every evaluated ln P.
+            push(qc, qd, nq, cell < n_cells && !(ub == -INFINITY) && !(ub < from_fkey(sh_bfk)),
+                 cell, d);
         }
-        // a cell without events (bound -inf) is never the argmax; NaN survives.
-        // The FP32 threshold is at most every evaluated ln P.
-        const bool keep =
-            cell < n_cells && !(ub == -INFINITY) && !(ub < from_fkey(sh_bfk));
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const int pos = nq + __popc(m & ((1u << lane) - 1u));
-            qc[pos] = cell;
-            qd[pos] = d;
-        }
-        nq += __popc(m);
-        __syncwarp();
-        if (nq >= 32) {
-            if (coop) {
-                for (int q = 0; q < 32; ++q)
-                    evaluate_queued_warp(g, nodes, c, n_phi, qc[q], qd[q], &sh_sbest, &sh_bfk,
-                                         &sh_tb[threadIdx.x]);
-            } else {
-                evaluate_queued(g, nodes, c, n_phi, qc[lane], qd[lane], &sh_sbest, &sh_bfk,
-                                &sh_tb[threadIdx.x]);
-            }
-            __syncwarp();
-            nq -= 32;
-            long long c2 = 0;
-            int d2 = 0;
-            if (lane < nq) {
-                c2 = qc[32 + lane];
-                d2 = qd[32 + lane];
-            }
-            __syncwarp();
-            if (lane < nq) {
-                qc[lane] = c2;
-                qd[lane] = d2;
-            }
-            __syncwarp();
-        }
+        if (nq >= 32) evaluate32();
     }
+    if (na > 0) screen_queued(na);
+    if (nq >= 32) evaluate32();
     if (coop) {
         for (int q = 0; q < nq; ++q)
             evaluate_queued_warp(g, nodes, c, n_phi, qc[q], qd[q], &sh_sbest, &sh_bfk,
@@ -1514,10 +1595,13 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
 #define NU_SCREEN_MIN_BLOCKS 3
 #endif
 
-// 256-thread blocks: 3 per SM (about 80 registers); 64-thread blocks: 14 per
-// SM (72 registers, no spills; the shared arrays are sized for 2 warps).
+// 256-thread blocks: 3 per SM (about 80 registers); 64-thread blocks:
+// NU_SCREEN_SMALL_BLOCKS per SM (the shared arrays are sized for 2 warps).
+#ifndef NU_SCREEN_SMALL_BLOCKS
+#define NU_SCREEN_SMALL_BLOCKS 14
+#endif
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT, MAXT <= 64 ? 14 : NU_SCREEN_MIN_BLOCKS)
+__global__ void __launch_bounds__(MAXT, MAXT <= 64 ? NU_SCREEN_SMALL_BLOCKS : NU_SCREEN_MIN_BLOCKS)
 k_fold_screened(FoldGeom g, ScreenGeom sg, const Node8<double>* __restrict__ nodes, int n_D,
                 const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
                 double* __restrict__ T0_out, int* __restrict__ Didx_out,
@@ -1770,7 +1854,8 @@ __global__ void __launch_bounds__(MAXT, BatchBlocks<KIND, MAXT>::value)
 k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restrict__ t,
              const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
              const ulonglong2* __restrict__ vpair, const ScreenRec* __restrict__ srec,
-             const float* __restrict__ lwin, const unsigned* __restrict__ reg,
+             const float* __restrict__ lm3,
+             const unsigned* __restrict__ reg,
              const unsigned long long* __restrict__ peak,
              const int* __restrict__ bucket,
              const Node4<float>* __restrict__ rec, int n_D, double dt, double gap_factor,
@@ -1801,8 +1886,8 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
                         gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
             if (KIND == 0) {
                 const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off,
-                                    srec + fs.srec_off, lwin + fs.srec_off, fs.n_slots,
-                                    reg + 2 * g, fs.screen, peak + g};
+                                    srec + fs.srec_off, fs.n_slots,
+                                    reg + 2 * g, fs.screen, peak + g, lm3 + fs.srec_off};
                 fold_screened_one<MAXT, true>(gg, sg,
                                               (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
                                               periods[p], o, Q_out, T0_out, Didx_out, dep_out,
@@ -1842,7 +1927,8 @@ __global__ void k_screen_batch(const T* __restrict__ depth, const T* __restrict_
                                const int64_t* __restrict__ s_off, int n_D, double gap_max,
                                double dt, ScreenRec* __restrict__ rec,
                                ulonglong2* __restrict__ vpair, ScreenRec* __restrict__ srec,
-                               float* __restrict__ lslot, const int* __restrict__ slot_of) {
+                               float* __restrict__ lint,
+                               const int* __restrict__ slot_of) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= s_off[n_seg] * (int64_t)n_D) return;
     int lo = 0, hi = n_seg;
@@ -1856,8 +1942,8 @@ __global__ void k_screen_batch(const T* __restrict__ depth, const T* __restrict_
     const int64_t w = gid - s0 * n_D;
     const int64_t d = w / ng, i = w - d * ng;
     make_screen<T>(depth, var, gain, t + s0, gid, i, ng, d, gap_max, dt, rec,
-                   srec + fs.srec_off, lslot + fs.srec_off, fs.n_slots, slot_of + s0,
-                   vpair + s0);
+                   srec + fs.srec_off, lint + fs.srec_off, fs.n_slots,
+                   slot_of + s0, vpair + s0);
 }
 
 // Slots of every sample of the screened curves (reg: two words per curve).
@@ -2002,7 +2088,7 @@ cudaError_t launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev,
             k_fill_screen<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(
                 fs.srec, fb.n_srec_total);
             launched += 2;
-            e = cudaMemsetAsync(fs.lslot, 0, (size_t)(fb.n_srec_total + 1) * sizeof(float), st);
+            e = cudaMemsetAsync(fs.lint, 0, (size_t)(fb.n_srec_total + 1) * sizeof(float), st);
             if (e != cudaSuccess) {
                 *n_launched = launched;
                 return e;
@@ -2011,9 +2097,9 @@ cudaError_t launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev,
                 (const double*)depth, (const double*)var, (const double*)gain, t, segs_dev,
                 n_seg, s_off_dev, n_D, gap_factor * dt, dt,
                 (ScreenRec*)((char*)fs.nodes + L.off_screen),
-                (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.lslot, fs.slot_of);
-            k_lwin<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(fs.lslot, fb.n_srec_total,
-                                                                    fs.lwin);
+                (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.lint, fs.slot_of);
+            k_lmax3<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(fs.lint, fb.n_srec_total,
+                                                                     fs.lm3);
             launched += 2;
             e = cudaMemsetAsync(fs.peak, 0, (size_t)n_seg * sizeof(unsigned long long), st);
             if (e != cudaSuccess) {
@@ -2062,8 +2148,8 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
     // block size (64, 128 or 256 threads)
 #define NU_FB(KIND_, MAXT_, CTR_)                                                          \
     k_fold_batch<KIND_, MAXT_><<<grid, MAXT_, 0, st>>>(                                  \
-        segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lwin, fs.reg, fs.peak,    \
-        fs.bucket,                                                                         \
+        segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lm3, fs.reg,              \
+        fs.peak, fs.bucket,                                                                \
         fs.rec, n_D, dt, gap_factor, periods, fs.ptab, n_P, CTR_, Q, T0, Didx, dep, sig, lnp)
 #define NU_FB_SIZE(KIND_, CTR_)                                                            \
     do {                                                                                   \
@@ -2104,7 +2190,7 @@ namespace nu {
 // Scratch layout of the single-curve fold.
 struct SingleLayout {
     ExactLayout el;
-    size_t exact, bucket, slot_of, flag, rec, srec, lslot, lwin, total;
+    size_t exact, bucket, slot_of, flag, rec, srec, lint, lm3, total;
 };
 
 static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool fp64) {
@@ -2118,9 +2204,9 @@ static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool 
     L.flag = L.slot_of + al((size_t)n_t0 * sizeof(int));
     L.rec = L.flag + 256;
     L.srec = L.rec + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>)));
-    L.lslot = L.srec + (fp64 ? al((size_t)n_slots * n_D * sizeof(ScreenRec)) : 0);
-    L.lwin = L.lslot + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
-    L.total = L.lwin + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
+    L.lint = L.srec + (fp64 ? al((size_t)n_slots * n_D * sizeof(ScreenRec)) : 0);
+    L.lm3 = L.lint + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
+    L.total = L.lm3 + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
     return L;
 }
 
@@ -2186,12 +2272,12 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             ScreenRec* nrec = (ScreenRec*)(scratch + L.exact + L.el.off_screen);
             ulonglong2* vpair = (ulonglong2*)(scratch + L.exact + L.el.off_vpos);
             ScreenRec* srec = (ScreenRec*)(scratch + L.srec);
-            float* lslot = (float*)(scratch + L.lslot);
-            float* lwin = (float*)(scratch + L.lwin);
+            float* lint = (float*)(scratch + L.lint);
+            float* lm3 = (float*)(scratch + L.lm3);
             unsigned* reg = (unsigned*)(flag + 1);
             unsigned long long* peak = (unsigned long long*)(scratch + L.flag + 16);
-            const ScreenGeom sg{nrec, vpair, srec, lwin, n_slots, reg,
-                                (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0, peak};
+            const ScreenGeom sg{nrec, vpair, srec, n_slots, reg,
+                                (gap_factor < 2.0 && span_steps < 8.0e6) ? 1 : 0, peak, lm3};
             e = cudaMemsetAsync(flag, 0, 256, st);
             if (e != cudaSuccess) {
                 count_launches(launched);
@@ -2200,7 +2286,7 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             k_slot_offsets<<<div_up(n_t0, 256), 256, 0, st>>>(t0s_dev, n_t0, 1.0 / phase_step,
                                                               n_slots, slot_of, reg);
             k_fill_screen<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(srec, n_slots * n_D);
-            e = cudaMemsetAsync(lslot, 0, (size_t)n_slots * n_D * sizeof(float), st);
+            e = cudaMemsetAsync(lint, 0, (size_t)n_slots * n_D * sizeof(float), st);
             if (e != cudaSuccess) {
                 count_launches(launched + 2);
                 return cuda_fail(e, (std::string(who) + ": memset").c_str());
@@ -2210,9 +2296,9 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
                 t0s_dev, n_t0, n_D, g.gap_max, (Node8<double>*)nodes);
             k_screen<double><<<div_up(ngrid, 256), 256, 0, st>>>(
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
-                t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, lslot, n_slots, slot_of,
+                t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, lint, n_slots, slot_of,
                 vpair);
-            k_lwin<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(lslot, n_slots * n_D, lwin);
+            k_lmax3<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(lint, n_slots * n_D, lm3);
             k_gain_peak<<<dim3(1, (unsigned)std::min<int64_t>(div_up(ngrid, 2048), 608)), 256, 0,
                           st>>>((const double*)dlnl_dev, nullptr, n_t0, n_D, peak);
             // One block per period.  With many periods, 2-warp blocks: 14 fit

@@ -473,11 +473,12 @@ extern "C" nu_status nu_periodic_refine(const nu_factor* f, const double* P_dev,
     e = cudaMemcpyAsync(Ds_dev, Ds_host, n_D * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "nu_periodic_refine: copy");
     if (f->stream != st) {
-        cudaEvent_t ev;
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        cudaEventRecord(ev, f->stream);
-        cudaStreamWaitEvent(st, ev, 0);
-        cudaEventDestroy(ev);
+        e = cudaEventRecord(f->ready, f->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, f->ready, 0);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(mem, st);
+            return cuda_fail(e, "nu_periodic_refine: stream order");
+        }
     }
     switch (f->nb) {
         case 1: launch_refine<1>(f, Phi, Mq, n_blk, Pseg, P_dev, T0_dev, D_idx_dev, n_cand, Ds_dev, n_D, tmpl, ta, depth_dev, var_dev, dlnl_dev, snr_dev, st); break;

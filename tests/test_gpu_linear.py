@@ -184,3 +184,40 @@ def test_sector_19440_fp64_sampled():
     assert max(err["depth"], err["var"], err["dlnl"]) <= FP64_TOL, err
     assert info["logdet"] == pytest.approx(model.logdet, rel=1e-12)
     assert info["lnL_null"] == pytest.approx(model.lnL_null, rel=1e-12)
+
+
+@pytest.mark.parametrize("case", ["rotation", "white_only", "sho_overdamped", "two_rotations",
+                                  "rotation+exp"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_linear_window_start_path(case, precision):
+    """Epochs at the samples (the window-start recursion serves the box
+    windows that are not clipped; the per-template kernel the others): a
+    gapped curve with durations that give equal window lengths, one shorter
+    than the cadence (no sample in most windows), several longer than one
+    staged chunk (64 samples) and one close to the whole span."""
+    lc = synth.small_curve(n=700, seed=29, gap=55)
+    terms = CASES[case]["terms"]
+    terms = lc.terms if terms is None else terms
+    dt = synth.CADENCE_DAYS
+    Ds = np.array([0.5 * dt, 7.2 * dt, 7.4 * dt, 7.3 * dt, 0.06, 70.5 * dt, 131 * dt,
+                   0.45, 660 * dt])
+    gpu, _, _ = gpu_search(lc, lc.t, Ds, terms=terms, precision=precision)
+    ora = linear.linear_search(lc.t, lc.y, lc.diag_var, terms, lc.X, lc.t, Ds)
+    err = linear_errors(gpu, (ora["depth"], ora["var"], ora["dlnl"]))
+    print(f"window-start path {case} {precision}:", err)
+    if precision == "fp64":
+        assert max(err["depth"], err["var"], err["dlnl"]) <= FP64_TOL, err
+    else:
+        assert err["depth"] <= MIXED_DEPTH_TOL and err["var"] <= 1e-4, err
+
+
+@pytest.mark.parametrize("n", [5, 40, 64, 65, 200])
+def test_linear_window_start_short_curves(n):
+    """Curves shorter than, equal to and just above one block of window
+    starts (64 on small curves)."""
+    lc = synth.small_curve(n=n, seed=31)
+    Ds = np.array([1.5 * synth.CADENCE_DAYS, 0.02, 0.05])
+    gpu, _, _ = gpu_search(lc, lc.t, Ds)
+    ora = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t, Ds)
+    err = linear_errors(gpu, (ora["depth"], ora["var"], ora["dlnl"]))
+    assert max(err["depth"], err["var"], err["dlnl"]) <= FP64_TOL, err
