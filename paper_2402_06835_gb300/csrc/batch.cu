@@ -212,6 +212,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t f_nodes = foff; foff += fbat.any_exact ? exact_layout(N, n_D, fp64).total : 0;
     const size_t f_buck = foff;  foff += al((size_t)(fbat.n_bucket_total + 1) * 4);
     const size_t f_rec = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(Node4<float>));
+    const size_t f_lgm = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(float));
     const size_t f_srec = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(ScreenRec));
     const size_t f_slot = foff;  foff += fp64 ? al((size_t)N * sizeof(int)) : 0;
     const size_t f_reg = foff;   foff += al((size_t)n_lc * 2 * sizeof(unsigned));
@@ -230,7 +231,8 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     }
     const FoldSeg* fsegs = (const FoldSeg*)(fold_mem + f_segs);
     const FoldScratch fsc{fold_mem + f_nodes, (int*)(fold_mem + f_buck),
-                          (Node4<float>*)(fold_mem + f_rec), (ScreenRec*)(fold_mem + f_srec),
+                          (Node4<float>*)(fold_mem + f_rec), (float*)(fold_mem + f_lgm),
+                          (ScreenRec*)(fold_mem + f_srec),
                           (int*)(fold_mem + f_slot), (unsigned*)(fold_mem + f_reg),
                           (float*)(fold_mem + f_lint), (float*)(fold_mem + f_lm3),
                           (unsigned long long*)(fold_mem + f_peak),

@@ -71,6 +71,7 @@ struct FoldScratch {
     void* nodes;            // exact-path records (exact_layout of all samples)
     int* bucket;            // bucket tables
     Node4<float>* rec;      // mixed slot records
+    float* lgm;             // mixed: the larger gain of each slot and the next
     ScreenRec* srec;        // FP64 slot-indexed screening records
     int* slot_of;           // FP64: slot of every sample
     unsigned* reg;          // FP64: two words per curve (zeroed by the prep)

@@ -875,7 +875,7 @@ __global__ void k_screen(const T* __restrict__ depth, const T* __restrict__ var,
 
 // lm3[x] = max(lint[x - 1], lint[x], lint[x + 1]) over the flat array: the
 // largest gain of an event whose walk position lies in slot x (its interval
-// starts at the epoch of slot x - 1, x or x + 1, see gain_bound_cell).  A
+// starts at the epoch of slot x - 1, x or x + 1, see the gain bound).  A
 // neighbour in the next row only raises the bound.
 __global__ void k_lmax3(const float* __restrict__ lint, int64_t n, float* __restrict__ lm3) {
     const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1144,7 +1144,7 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
     return acc.bound(sp.cv, bf);
 }
 
-// Gain bound of a cell on a regular grid, from 4 bytes per epoch.  By the
+// The gain bound of a cell on a regular grid, from 4 bytes per epoch.  By the
 // bound above, ln P <= S_L + 1/2, and every event's gain is at most the
 // larger gain of its interval's two nodes.  The walk's position u of epoch k
 // lies within e_pos << 1 slot of the exact epoch, and on a regular grid every
@@ -1154,14 +1154,44 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
 // the screen's error model).  Extra walk positions past t_last (u < uend)
 // only add terms >= 0.  The FP32 sum of K terms >= 0 is rounded up by
 // (K + 16) 2^-23 of itself, and 1e-6 covers the exact path's own rounding.
-// The walk is bound by the latency of its gathers, so four epochs' loads
-// are issued before their sums (a position past uend loads a clamped slot
-// and is not added; ustep < 2^60 keeps u + 3 ustep from wrapping).
-__device__ __forceinline__ float gain_bound_cell(const float* __restrict__ lm, unsigned ns1,
-                                                 unsigned long long u, unsigned long long ustep,
-                                                 unsigned long long uend) {
+// The walk is bound by the latency of its gathers, so its terms are loaded
+// four at a time before they are added (gain_ahead loads the first four; a
+// position past uend loads a clamped slot and is not added; ustep < 2^60
+// keeps u + 3 ustep from wrapping).  gain_sum returns the sum of the terms
+// and their number.  (Loading the next round's terms a round ahead was
+// slower: the registers it holds cost more than the latency it hides.)
+struct GainAhead {
+    float a, b, c, e;
+};
+__device__ __forceinline__ GainAhead gain_ahead(const float* __restrict__ lm, unsigned ns1,
+                                                unsigned long long u, unsigned long long ustep) {
+    const unsigned long long ua = u + ustep, ub = ua + ustep, uc = ub + ustep;
+    return GainAhead{lm[min((unsigned)(u >> 40), ns1)], lm[min((unsigned)(ua >> 40), ns1)],
+                     lm[min((unsigned)(ub >> 40), ns1)], lm[min((unsigned)(uc >> 40), ns1)]};
+}
+__device__ __forceinline__ float2 gain_sum(const GainAhead& ga, const float* __restrict__ lm,
+                                           unsigned ns1, unsigned long long u,
+                                           unsigned long long ustep, unsigned long long uend) {
     float s0 = 0.f, s1 = 0.f, K = 0.f;
     const unsigned long long u4 = 4ull * ustep;
+    if (u < uend) {
+        const unsigned long long ua = u + ustep, ub = ua + ustep, uc = ub + ustep;
+        s0 = ga.a;
+        K = 1.f;
+        if (ua < uend) {
+            s1 = ga.b;
+            K += 1.f;
+        }
+        if (ub < uend) {
+            s0 += ga.c;
+            K += 1.f;
+        }
+        if (uc < uend) {
+            s1 += ga.e;
+            K += 1.f;
+        }
+        u += u4;
+    }
     for (; u < uend; u += u4) {
         const unsigned long long ua = u + ustep, ub = ua + ustep, uc = ub + ustep;
         const float a = lm[min((unsigned)(u >> 40), ns1)];
@@ -1183,7 +1213,7 @@ __device__ __forceinline__ float gain_bound_cell(const float* __restrict__ lm, u
             K += 1.f;
         }
     }
-    return (s0 + s1) * fmaf(K + 16.f, 1.1920929e-7f, 1.f) + 0.5f + 1e-6f;
+    return make_float2(s0 + s1, K);
 }
 
 // A warp whose gain bounds pass at least NU_GAIN_PASS_MAX of its 32 cells
@@ -1437,7 +1467,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     int* qad = sh_qad[wid];
     int na = 0;
     // Cascade on regular grids: after the warp's first round every cell is
-    // bounded from its gains alone (gain_bound_cell, 4 bytes per epoch); the
+    // bounded from its gains alone (the gain bound, 4 bytes per epoch); the
     // cells that bound does not rule out are queued and screened in full 32
     // at a time, and the full screen's survivors are evaluated exactly.
     const bool cascade = sp.slots && sg.lm3 != nullptr && sp.ustep < (1ull << 60);
@@ -1513,9 +1543,14 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         float ub = -INFINITY;
         if (!first && cascade && direct == 0) {
             float gb = -INFINITY;
-            if (cell < n_cells)
-                gb = gain_bound_cell(sg.lm3 + (int64_t)d * sg.n_slots, ns1,
-                                     (unsigned long long)j * sp.uph, sp.ustep, sp.uend);
+            if (cell < n_cells) {
+                // ln P <= S_L + 1/2, with the gain bound's margins
+                const float* lr = sg.lm3 + (int64_t)d * sg.n_slots;
+                const unsigned long long u0 = (unsigned long long)j * sp.uph;
+                const float2 sk = gain_sum(gain_ahead(lr, ns1, u0, sp.ustep), lr, ns1, u0,
+                                           sp.ustep, sp.uend);
+                gb = sk.x * fmaf(sk.y + 16.f, 1.1920929e-7f, 1.f) + 0.5f + 1e-6f;
+            }
             const bool pass = cell < n_cells && !(gb < from_fkey(sh_bfk));
             // where the gain bound rules out almost nothing (cells of many
             // epochs, whose bound needs the depth terms) the warp screens
@@ -1687,16 +1722,43 @@ struct SCell {
     int d, kmax, pad;
 };
 
+// Gain table of the slot path: lgm[x] = the larger gain of slots x and x + 1
+// of a duration row when both records are valid (0 otherwise, a dropped
+// event), rounded up: the interpolated gain of an event in slot x is at most
+// that (to the FP32 rounding of the interpolation).  Every row ends with
+// padding slots (NaN), so a pair never reaches into the next row.
+__global__ void k_slot_gain(const Node4<float>* __restrict__ rec, int64_t n,
+                            float* __restrict__ lgm) {
+    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    float m = 0.f;
+    if (x + 1 < n) {
+        const Node4<float> a = rec[x], b = rec[x + 1];
+        if (!isnan(a.s) && !isnan(b.s)) m = __fmul_ru(fmaxf(0.f, fmaxf(a.l, b.l)), 1.0000005f);
+    }
+    lgm[x] = m;
+}
+
 // Epochs walk the slot grid in 24.40 fixed point: u = (T - t_ref)/dt =
 // (j/n_phi + k) P/dt.  The interval is (slot, slot+1) and the weight is the
 // fractional part; on a grid whose epochs sit on the slots this is the
 // interpolation between the bracketing epochs up to their offsets from the
-// slot centres (checked to be below 1e-3 slot).  Each warp runs the first
-// pass of its cells and queues those the bound keeps in its own shared
-// queue; 32 queued cells get their second passes, one per lane, from that
-// warp alone (no block barriers until the final argmax).
+// slot centres (checked to be below 1e-3 slot).
+//
+// Cascade per warp (no block barriers until the final argmax):
+//   1. gain bound of each cell from lgm (4 bytes per epoch): with the bound
+//      of cannot_win, ln P <= S_L + 1/2, and S_L is at most the sum of the
+//      epochs' lgm; cells below the threshold stop here;
+//   2. queued, 32 at a time: the first pass (FP32 sums) and the bound of
+//      cannot_win_f;
+//   3. queued, 32 at a time: the second pass, whose ln P raises the threshold.
+// In its first round a warp runs the first pass on its own cells, and the
+// lane with the largest bound evaluates its cell at once (the threshold's
+// seed).  Warps whose gain bounds pass almost every cell (cells of many
+// epochs) skip step 1 for their next rounds.
 template <int KC, int MAXT = 256>
 __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ rec,
+                                               const float* __restrict__ lgm,
                                                int64_t n_slots, int n_D, double dt,
                                                double t_ref, double t_last, double P, int64_t p,
                                                double* __restrict__ Q_out,
@@ -1706,12 +1768,15 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                                                double* __restrict__ sig_out,
                                                double* __restrict__ lnp_out) {
     __shared__ SCell sh_q[MAXT / 32][64];
+    __shared__ long long sh_qa[MAXT / 32][64];     // cells for the first pass
+    __shared__ int sh_qad[MAXT / 32][64];
     __shared__ unsigned int sh_best;
     FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
     if (bad_period(P, gg)) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
     }
+    const unsigned FULL = 0xffffffffu;
     const int64_t n_phi = (int64_t)ceil(P / dt);
     const int64_t n_cells = n_phi * n_D;
     const double R = P / dt;                                   // slots per period
@@ -1728,7 +1793,19 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     SCell* q = sh_q[wid];
-    int nq = 0;                              // warp-uniform queue length
+    int nq = 0;                              // warp-uniform queue lengths
+    long long* qa = sh_qa[wid];
+    int* qad = sh_qad[wid];
+    int na = 0;
+    const unsigned ns1 = (unsigned)(n_slots - 1);
+    // the gain walk adds 4 positions past ulast at most: ustep < 2^60 keeps
+    // them from wrapping (ulast < 2^62)
+    const bool cascade = lgm != nullptr && ustep < (1ull << 60);
+    auto best_now = [&]() {
+        const unsigned int kb = sh_best;
+        return fmaxf(bl, kb ? __uint_as_float((kb >> 31) ? (kb & 0x7fffffffu) : ~kb)
+                            : -INFINITY);
+    };
     // second pass of queued cell e, by one lane
     auto pass2 = [&](const SCell& e) {
         const Node4<float>* rd = rec + (int64_t)e.d * n_slots;
@@ -1750,8 +1827,74 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         const unsigned int b32 = __float_as_uint(lnp);
         atomicMax(&sh_best, (b32 >> 31) ? ~b32 : (b32 | 0x80000000u));
     };
+    // first pass and bound of cell (dl, jl); *ub receives the bound (-inf:
+    // no event) and e the queue entry; returns whether the cell is kept
+    auto pass1 = [&](int dl, int64_t jl, long long cl, SCell& e, float* ub) -> bool {
+        *ub = -INFINITY;
+        const unsigned long long u0 = (unsigned long long)jl * uph;
+        if (u0 > ulast) return false;
+        // epochs with u <= ulast, counted as they are walked
+        const Node4<float>* rd = rec + (int64_t)dl * n_slots;
+        SlotPass1 p1;
+        p1.init();
+        int kmax = 0;
+        // two epochs' record loads in flight
+#pragma unroll 2
+        for (unsigned long long u = u0; u <= ulast; u += ustep, ++kmax) p1.add(slot_event(rd, u));
+        if (p1.K == 0) return false;
+        *ub = p1.s_l.s + 0.5f;
+        if (cannot_win_f(p1.s_l.s, p1.s_inv.s, p1.s_d.s, p1.s_dd, p1.ivmax, best_now()))
+            return false;
+        const float s2 = 1.0f / p1.s_inv.s;
+        e = SCell{u0, cl, p1.s_l.s, s2, s2 * p1.s_d.s, dl, kmax, 0};
+        return true;
+    };
+    auto push_b = [&](bool keep, const SCell& e) {
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) q[nq + __popc(m & ((1u << lane) - 1u))] = e;
+        nq += __popc(m);
+        __syncwarp();
+    };
+    auto flush_b = [&]() {
+        pass2(q[lane]);
+        __syncwarp();
+        nq -= 32;
+        SCell e2;
+        if (lane < nq) e2 = q[32 + lane];
+        __syncwarp();
+        if (lane < nq) q[lane] = e2;
+        __syncwarp();
+    };
+    // first passes of the first cnt entries of queue A, one per lane
+    auto flush_a = [&](int cnt) {
+        SCell e;
+        float ub;
+        bool keep = false;
+        if (lane < cnt) {
+            const long long cl = qa[lane];
+            const int dl = qad[lane];
+            keep = pass1(dl, cl - (int64_t)dl * n_phi, cl, e, &ub);
+        }
+        push_b(keep, e);
+        __syncwarp();
+        na -= cnt;
+        long long c2 = 0;
+        int d2 = 0;
+        if (lane < na) {
+            c2 = qa[cnt + lane];
+            d2 = qad[cnt + lane];
+        }
+        __syncwarp();
+        if (lane < na) {
+            qa[lane] = c2;
+            qad[lane] = d2;
+        }
+        __syncwarp();
+    };
     int d = (int)(threadIdx.x / n_phi);
     int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
+    bool first = true;
+    int direct = 0;                          // rounds left without the gain bound
     for (int64_t base = (int64_t)wid * 32; base < n_cells; base += blockDim.x,
                  j += blockDim.x) {
         while (j >= n_phi) {
@@ -1759,47 +1902,57 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
             ++d;
         }
         const int64_t cell = base + lane;
-        bool keep = false;
-        SCell e;
-        if (cell < n_cells) {
-            const unsigned long long u0 = (unsigned long long)j * uph;
-            if (u0 <= ulast) {
-                // epochs with u <= ulast, counted as they are walked
-                const Node4<float>* rd = rec + (int64_t)d * n_slots;
-                SlotPass1 p1;
-                p1.init();
-                int kmax = 0;
-                // two epochs' record loads in flight (C3: 16.6 -> 16.1 ms)
-#pragma unroll 2
-                for (unsigned long long u = u0; u <= ulast; u += ustep, ++kmax)
-                    p1.add(slot_event(rd, u));
-                const unsigned int kb = sh_best;
-                const float best_now =
-                    fmaxf(bl, kb ? __uint_as_float((kb >> 31) ? (kb & 0x7fffffffu) : ~kb)
-                                 : -INFINITY);
-                if (p1.K > 0 &&
-                    !cannot_win_f(p1.s_l.s, p1.s_inv.s, p1.s_d.s, p1.s_dd, p1.ivmax, best_now)) {
-                    const float s2 = 1.0f / p1.s_inv.s;
-                    keep = true;
-                    e = SCell{u0, (long long)cell, p1.s_l.s, s2, s2 * p1.s_d.s, d, kmax, 0};
-                }
+        if (!first && cascade && direct == 0) {
+            bool pass = false;
+            if (cell < n_cells) {
+                // epochs with u <= ulast
+                const float* lr = lgm + (int64_t)d * n_slots;
+                const unsigned long long u0 = (unsigned long long)j * uph;
+                const float2 sk = gain_sum(gain_ahead(lr, ns1, u0, ustep), lr, ns1, u0, ustep,
+                                           ulast + 1);
+                // the margins of cannot_win_f on top of the rounding of the sum
+                const float gb = sk.x * fmaf(sk.y + 16.f, 1.1920929e-7f, 1.f) + 0.5f;
+                pass = sk.y > 0.f && !(gb + 1e-4f * fmaxf(1.f, fabsf(gb)) < best_now());
             }
+            if (__popc(__ballot_sync(FULL, pass)) >= NU_GAIN_PASS_MAX)
+                direct = NU_GAIN_DIRECT_ROUNDS;
+            const unsigned m = __ballot_sync(FULL, pass);
+            if (pass) {
+                const int pos = na + __popc(m & ((1u << lane) - 1u));
+                qa[pos] = cell;
+                qad[pos] = d;
+            }
+            na += __popc(m);
+            __syncwarp();
+            if (na >= 32) flush_a(32);
+        } else {
+            if (direct > 0) --direct;
+            SCell e;
+            float ub = -INFINITY;
+            const bool keep = cell < n_cells && pass1(d, j, cell, e, &ub);
+            if (first) {
+                // seed: the kept lane with the largest S_L + 1/2 evaluates its
+                // cell now (it is evaluated again from the queue, same result)
+                first = false;
+                float v = keep ? ub : -INFINITY;
+                int src = lane;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float v2 = __shfl_xor_sync(FULL, v, o);
+                    const int s2 = __shfl_xor_sync(FULL, src, o);
+                    if (v2 > v || (v2 == v && s2 < src)) {
+                        v = v2;
+                        src = s2;
+                    }
+                }
+                if (v > -INFINITY && lane == src) pass2(e);
+                __syncwarp();
+            }
+            push_b(keep, e);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) q[nq + __popc(m & ((1u << lane) - 1u))] = e;
-        nq += __popc(m);
-        __syncwarp();
-        if (nq >= 32) {
-            pass2(q[lane]);
-            __syncwarp();
-            nq -= 32;
-            SCell e2;
-            if (lane < nq) e2 = q[32 + lane];
-            __syncwarp();
-            if (lane < nq) q[lane] = e2;
-            __syncwarp();
-        }
+        if (nq >= 32) flush_b();
     }
+    if (na > 0) flush_a(na);
+    if (nq >= 32) flush_b();
     if (lane < nq) pass2(q[lane]);
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (bc != LLONG_MAX) best = Best{(double)bl, bc, (double)bD, sqrt((double)bs2)};
@@ -1820,15 +1973,16 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
 
 template <int KC, int MAXT>
 __global__ void __launch_bounds__(MAXT, NU_SLOTS_MIN_BLOCKS * 256 / MAXT)
-k_fold_slots(const Node4<float>* __restrict__ rec, int64_t n_slots, int n_D, double dt,
-             double t_ref, double t_last, const double* __restrict__ periods, int64_t n_P,
-             double* __restrict__ Q_out, double* __restrict__ T0_out,
-             int* __restrict__ Didx_out, double* __restrict__ dep_out,
-             double* __restrict__ sig_out, double* __restrict__ lnp_out) {
+k_fold_slots(const Node4<float>* __restrict__ rec, const float* __restrict__ lgm,
+             int64_t n_slots, int n_D, double dt, double t_ref, double t_last,
+             const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
+             double* __restrict__ T0_out, int* __restrict__ Didx_out,
+             double* __restrict__ dep_out, double* __restrict__ sig_out,
+             double* __restrict__ lnp_out) {
     const int64_t p = blockIdx.x;
     if (p >= n_P) return;
-    fold_slots_one<KC, MAXT>(rec, n_slots, n_D, dt, t_ref, t_last, periods[p], p, Q_out, T0_out,
-                       Didx_out, dep_out, sig_out, lnp_out);
+    fold_slots_one<KC, MAXT>(rec, lgm, n_slots, n_D, dt, t_ref, t_last, periods[p], p, Q_out,
+                             T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
 // ------------------------------------------------------------ batch path
@@ -1854,7 +2008,7 @@ __global__ void __launch_bounds__(MAXT, BatchBlocks<KIND, MAXT>::value)
 k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restrict__ t,
              const void* __restrict__ nodes, const ScreenRec* __restrict__ screen,
              const ulonglong2* __restrict__ vpair, const ScreenRec* __restrict__ srec,
-             const float* __restrict__ lm3,
+             const float* __restrict__ lm3, const float* __restrict__ lgm,
              const unsigned* __restrict__ reg,
              const unsigned long long* __restrict__ peak,
              const int* __restrict__ bucket,
@@ -1878,7 +2032,8 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
         if ((KIND == 2) != (fs.use_slots != 0)) continue;
         const int64_t o = (int64_t)g * n_P + p;
         if (KIND == 2) {
-            fold_slots_one<8, MAXT>(rec + fs.rec_off, fs.n_slots, n_D, dt, fs.t_ref, fs.t_last,
+            fold_slots_one<8, MAXT>(rec + fs.rec_off, lgm + fs.rec_off, fs.n_slots, n_D, dt,
+                                    fs.t_ref, fs.t_last,
                               periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                               lnp_out);
         } else {
@@ -2124,7 +2279,9 @@ cudaError_t launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev,
         k_slot_fill_batch<<<div_up(ngrid, 256), 256, 0, st>>>(
             (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
             s_off_dev, n_D, 1.0 / dt, fs.rec);
-        launched += 2;
+        k_slot_gain<<<div_up(fb.n_rec_total + 1, 256), 256, 0, st>>>(fs.rec, fb.n_rec_total,
+                                                                     fs.lgm);
+        launched += 3;
     }
     *n_launched = launched;
     return cudaSuccess;
@@ -2148,7 +2305,7 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
     // block size (64, 128 or 256 threads)
 #define NU_FB(KIND_, MAXT_, CTR_)                                                          \
     k_fold_batch<KIND_, MAXT_><<<grid, MAXT_, 0, st>>>(                                  \
-        segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lm3, fs.reg,              \
+        segs_dev, n_seg, t, fs.nodes, screen, vpair, fs.srec, fs.lm3, fs.lgm, fs.reg,      \
         fs.peak, fs.bucket,                                                                \
         fs.rec, n_D, dt, gap_factor, periods, fs.ptab, n_P, CTR_, Q, T0, Didx, dep, sig, lnp)
 #define NU_FB_SIZE(KIND_, CTR_)                                                            \
@@ -2190,7 +2347,7 @@ namespace nu {
 // Scratch layout of the single-curve fold.
 struct SingleLayout {
     ExactLayout el;
-    size_t exact, bucket, slot_of, flag, rec, srec, lint, lm3, total;
+    size_t exact, bucket, slot_of, flag, rec, srec, lint, lm3, lgm, total;
 };
 
 static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool fp64) {
@@ -2206,7 +2363,8 @@ static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool 
     L.srec = L.rec + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>)));
     L.lint = L.srec + (fp64 ? al((size_t)n_slots * n_D * sizeof(ScreenRec)) : 0);
     L.lm3 = L.lint + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
-    L.total = L.lm3 + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
+    L.lgm = L.lm3 + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
+    L.total = L.lgm + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(float)));
     return L;
 }
 
@@ -2254,15 +2412,17 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
         k_slot_fill<<<div_up(ngrid, 256), 256, 0, st>>>(
             (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
             n_t0, n_D, n_slots, rec);
+        float* lgm = (float*)(scratch + L.lgm);
+        k_slot_gain<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec, lgm);
         if (n_P >= NU_SLOTS_SMALL_FROM)
             k_fold_slots<8, NU_SLOTS_SMALL><<<(unsigned)n_P, NU_SLOTS_SMALL, 0, st>>>(
-                rec, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev, T0_dev,
-                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+                rec, lgm, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev,
+                T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
         else
             k_fold_slots<8, 256><<<(unsigned)n_P, 256, 0, st>>>(
-                rec, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev, T0_dev,
-                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-        launched += 3;
+                rec, lgm, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev,
+                T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+        launched += 4;
     } else {
         k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,
                                                         n_bucket, bucket);
