@@ -4,18 +4,28 @@
 A step is one full pass of the hot path over one light curve of the workload:
 nu_gp_factor (covariance factor and null fit), nu_linear_search (every
 (t0, D) template) and nu_periodic_search (every trial period), inputs resident
-in HBM.  Default workload: one TESS-sector-shaped light curve, N = 19 440 with
+in HBM.  Headline workload: one TESS-sector-shaped light curve, N = 19 440 with
 a 1-day mid-sector gap, 10 durations (20 min - 3 h), 20 000 periods
-(0.2 - 13.5 d), FP64.  The same sector with 16 durations in mixed precision is
-measured beside it ("mixed").
+(0.2 - 13.5 d), FP64.  Measured beside it, as keys of the same line:
+
+* mixed_c2:    the same sector in mixed precision (mixed vs FP64 per curve);
+* mixed:       the sector with 16 durations in mixed precision;
+* multisector: seven sectors (N = 136 080, 20 durations, 100 000 periods),
+               FP64 and mixed side by side;
+* batch_fp64 / batch_mixed: the 438-curve survey through nu_batch_search;
+* cpu_baseline (rank 0, one GPU): the CPU oracle on bounded samples,
+               extrapolated, the small light curve's oracle timed in full as
+               an anchor, and the mixed path's per-output error against the
+               oracle's whole grid of the 16-duration sector.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With --impl reference the CPU oracle (dense FP64 covariance, one GLS per
-template, literal Eq. result fold) is timed on the host cores on bounded
-samples of the same workload and extrapolated to a full step.
-Multi-GPU (torchrun): every rank searches its own replica (independent light
-curves, no data-path collective; weak scaling).
+template, literal Eq. result fold) is timed on the host cores: every step is a
+bounded sample of the headline workload (the same sample as cpu_baseline) and
+the throughput is extrapolated to a full step.  Multi-GPU (torchrun): every
+rank searches its own replica (independent light curves, no data-path
+collective; weak scaling).
 """
 from __future__ import annotations
 
@@ -36,45 +46,72 @@ from paper_2402_06835_gb300 import synth  # noqa: E402
 
 METRIC = "linear-search (t0,D) fits/s + period trials/s, %HBM roofline, mixed vs FP64"
 MEASURED_FP64_TFLOPS = 1.197   # DFMA microbenchmark on this machine's GB300 (2 DFMA/clk/SM)
-# FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-L2_READ_GBS = 17700.0          # L2-resident read microbenchmark on this machine's GB300
+N_SMSP = 152 * 4               # SM sub-partitions (one warp instruction issued per clock each)
+# Per launch of the FP64 fold on the headline workload, from a one-pass ncu
+# capture of the kernel as it stands (the launch list and counters are
+# summarised under profiles/): DRAM bytes read + written, warp instructions.
+FOLD_NCU = {"sector_19440": {"traffic": 27120384, "inst": 7895867159}}
+FLUSH_BYTES = 512 << 20        # > 129 MB L2
+ORACLE_TEMPLATES = 256         # bounded oracle sample per step (both CPU legs)
+ORACLE_PERIODS = 8
 
 
-def measured_hbm_gbs():
+def measured_peaks():
     """HBM copy bandwidth from the machine's measured peaks, else the fallback."""
     try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                               "MEASURED_PEAKS.json")) as fh:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
 
 
 def linear_search_roofline(lc, Ds, ms, nb=2, k=2):
-    """Algorithmic bytes and FP64 flops of one nu_linear_search: per sample
-    the factor arrays it reads (t, F, kg, 1/D, G, z0, Zt), per template the
-    three FP64 outputs; per window sample about 8 + 6 J flops of the forward
-    solve and sums, per template the tail s^T G s and the epilogue."""
+    """Algorithmic bytes and FP64 flops of one box nu_linear_search with the
+    window-start recursion: per sample the factor arrays it reads (t, F, kg,
+    1/D, G, z0, Zt), per template the three FP64 outputs; per window start one
+    recursion over the longest window (8 + 6 J flops per step: innovation,
+    its square, the sums and the gain and transition updates), per template
+    the tail s^T G s and the epilogue."""
     J = 2 * nb
     JJ = J * (J + 1) // 2
     n = len(lc.t)
     dt = float(np.median(np.diff(lc.t)))
-    steps = sum(int(round(D / dt)) for D in Ds) * n
-    flops = steps * (8 + 6 * J) + n * len(Ds) * (2 * JJ + 2 * J + 30)
+    lmax = max(int(round(D / dt)) for D in Ds)
+    flops = n * lmax * (8 + 6 * J) + n * len(Ds) * (2 * JJ + 2 * J + 20)
     bytes_ = n * 8 * (1 + 4 * nb + J + 1 + JJ + 1 + k) + n * len(Ds) * 24
-    hbm, src = measured_hbm_gbs()
+    hbm, src = measured_peaks()
     gbs = bytes_ / (ms / 1e3) / 1e9
     tfl = flops / (ms / 1e3) / 1e12
     return {"bytes": bytes_, "GB/s": gbs, "hbm_frac": gbs / hbm, "hbm_peak": hbm,
-            "hbm_peak_source": src, "fp64_tflops": tfl,
-            "fp64_pipe_frac": tfl / MEASURED_FP64_TFLOPS, "flops": flops}
-FOLD_FLOPS_PER_VISIT = 55.0    # 25 in pass 1 + 30 in pass 2 (one log per visit)
-# DRAM bytes (read + write) of one fold launch on the bench workload (sector_19440,
-# FP64), from an ncu capture of the kernel as it stands
-# (profiles/k_fold_screened_sector_19440.md); other workloads report None
-FOLD_TRAFFIC_BYTES = {"sector_19440": 26802176}
-FLUSH_BYTES = 512 << 20        # > 129 MB L2
+            "hbm_peak_source": src, "fp64_flops": flops, "fp64_tflops": tfl,
+            "fp64_pipe_frac": tfl / MEASURED_FP64_TFLOPS,
+            "fp64_peak_source": "builder-measured DFMA microbenchmark (1.197 TFLOP/s)"}
+
+
+def fold_roofline(n_t0, n_D, n_P, ms, visits, value_bytes, kernel, ncu=None, clock_mhz=None):
+    """The fold against HBM on its compulsory bytes (the single-event grid read
+    once: 3 values of value_bytes per (duration, epoch); 44 bytes of outputs
+    per period) and, where an ncu instruction count is at hand, its
+    instruction issue rate (the fold is bound by issue and gather latency, not
+    by memory bandwidth)."""
+    hbm, src = measured_peaks()
+    comp = 3 * n_D * n_t0 * value_bytes + 44 * n_P
+    gbs = comp / (ms / 1e3) / 1e9
+    out = {"kernel": kernel, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+           "frac": gbs / hbm, "traffic": None, "algorithmic_bytes": comp,
+           "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+           "timing": "nu_periodic_search stage (the fold kernel and its small prep kernels), "
+                     "CUDA events over the timed steps"}
+    out["visits"] = visits
+    if ncu and ncu.get("traffic"):
+        out["traffic"] = ncu["traffic"]
+    if ncu and ncu.get("inst") and clock_mhz:
+        cyc = ms / 1e3 * clock_mhz * 1e6
+        out["issue"] = {"warp_inst_per_launch": ncu["inst"],
+                        "frac": ncu["inst"] / (cyc * N_SMSP),
+                        "peak": "one warp instruction per clock per sub-partition, "
+                                "608 sub-partitions at the sampled SM clock"}
+    return out
 
 
 def parse():
@@ -85,8 +122,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sector_19440")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--mixed-workload", default="sector_19440_16d")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-multisector", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -162,11 +199,13 @@ class Pipeline:
     def __init__(self, api, torch, lc, Ds, periods, precision, dev):
         self.api, self.torch = api, torch
         f64 = torch.float64
+        self.lc = lc
         self.t = torch.as_tensor(lc.t, dtype=f64, device=dev)
         self.y = torch.as_tensor(lc.y, dtype=f64, device=dev)
         self.dv = torch.as_tensor(lc.diag_var, dtype=f64, device=dev)
         self.X = torch.as_tensor(lc.X, dtype=f64, device=dev)
         self.t0s = self.t
+        self.periods_np = np.asarray(periods, dtype=np.float64)
         self.periods = torch.as_tensor(periods, dtype=f64, device=dev)
         self.Ds = [float(d) for d in Ds]
         self.terms = lc.terms
@@ -175,7 +214,7 @@ class Pipeline:
         self.n_templates = len(lc.t) * len(Ds)
         self.n_periods = len(periods)
 
-    def step(self, events=None):
+    def step(self, events=None, keep=False):
         api = self.api
         if events:
             events[0].record()
@@ -190,6 +229,8 @@ class Pipeline:
         if events:
             events[3].record()
         f.free()
+        if keep:
+            res["grid"] = (d, v, l)
         return res
 
 
@@ -207,13 +248,34 @@ def time_pipeline(pipe, torch, steps, warmup, flush):
     return stages                                 # (steps, 3) ms
 
 
+def pipeline_entry(name, pipe, stages, world, ncu=None, clock_mhz=None):
+    """The JSON of one single-curve workload measured with time_pipeline."""
+    ms = float(stages.sum(axis=1).mean())
+    sm = stages.mean(axis=0)
+    lc = pipe.lc
+    n_D = len(pipe.Ds)
+    fp64 = pipe.precision == "fp64"
+    visits = fold_visits(lc.t, pipe.periods_np, pipe.dt, n_D)
+    return {"workload": name, "precision": pipe.precision, "ms_per_step": ms,
+            "value": world * pipe.n_templates / (ms / 1e3), "unit": "(t0,D) fits/s",
+            "period_trials_per_s": world * pipe.n_periods / (ms / 1e3),
+            "stages_ms": {"factor": float(sm[0]), "linear_search": float(sm[1]),
+                          "periodic_search": float(sm[2])},
+            "linear_search_fits_per_s": pipe.n_templates / (float(sm[1]) / 1e3),
+            "fold_visits_per_s": visits / (float(sm[2]) / 1e3),
+            "roofline": fold_roofline(len(lc.t), n_D, pipe.n_periods, float(sm[2]), visits,
+                                      8 if fp64 else 4,
+                                      "k_fold_screened" if fp64 else "k_fold_slots",
+                                      ncu, clock_mhz)}
+
+
 def run_e2e(pipe, api, torch, lc, steps):
     """Same step through the public API with inputs from pinned host memory,
     outputs read back to the host, copies inside the timed region."""
     f64 = torch.float64
     host = {k: torch.as_tensor(np.ascontiguousarray(v), dtype=f64).pin_memory()
             for k, v in (("t", lc.t), ("y", lc.y), ("dv", lc.diag_var), ("X", lc.X),
-                         ("P", pipe.periods.cpu().numpy()))}
+                         ("P", pipe.periods_np))}
     dev = {k: torch.empty_like(v, device="cuda") for k, v in host.items()}
     nP = pipe.n_periods
     out_host = torch.empty((5, nP), dtype=f64).pin_memory()
@@ -294,7 +356,6 @@ def recovery(w, r):
             "curves": int(len(hit))}
 
 
-
 def run_batch(api, torch, w, precision, steps, warmup, flush):
     """nu_batch_search over all curves of a survey workload; one step = one
     batched call (factor, linear search and fold of every curve)."""
@@ -316,16 +377,24 @@ def run_batch(api, torch, w, precision, steps, warmup, flush):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    n_templates = sum(len(lc.t) for lc in w.curves) * len(w.durations)
+    n_samples = sum(len(lc.t) for lc in w.curves)
+    n_templates = n_samples * len(w.durations)
     ms = float(np.mean(times))
     out_rec = recovery(w, r)
-    return {**out_rec, "workload": f"{w.name}: {len(w.curves)} curves, "
-                        f"{sum(len(lc.t) for lc in w.curves)} samples, "
-                        f"{len(w.durations)} durations, {len(w.periods)} periods",
-            "precision": precision, "ms_per_step": ms,
+    hbm, src = measured_peaks()
+    comp = n_samples * 8 * 3 + 44 * len(w.periods) * len(w.curves)
+    return {**out_rec, "workload": f"{w.name}: {len(w.curves)} curves, {n_samples} samples, "
+                                   f"{len(w.durations)} durations, {len(w.periods)} periods",
+            "precision": precision, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "value": n_templates / (ms / 1e3), "unit": "(t0,D) fits/s",
             "period_trials_per_s": len(w.curves) * len(w.periods) / (ms / 1e3),
-            "failed_curves": int(sum(1 for s_ in r["status"] if s_ != 0))}
+            "failed_curves": int(sum(1 for s_ in r["status"] if s_ != 0)),
+            "roofline": {"bound": "hbm", "unit": "GB/s", "algorithmic_bytes": comp,
+                         "achieved": comp / (ms / 1e3) / 1e9, "peak": hbm,
+                         "frac": comp / (ms / 1e3) / 1e9 / hbm, "peak_source": src,
+                         "note": "compulsory bytes of the whole batched call: the light "
+                                 "curves (t, y, variance) once and 44 B of outputs per "
+                                 "(curve, period); one CUDA graph, timed with CUDA events"}}
 
 
 # ---------------------------------------------------------------- ranks
@@ -345,22 +414,19 @@ def weak_scaling_value(units_per_rank, world, ms):
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(lc, Ds, periods, n_templates=256, n_periods=8, seed=0, model=None,
-                  t_setup=None):
-    """Time the oracle on a bounded sample and extrapolate to one full step.
-    A dense model built earlier may be passed with the time its factor took;
-    that time is still counted in the step."""
+def oracle_sample(lc, Ds, periods, model, t_setup, n_templates=ORACLE_TEMPLATES,
+                  n_periods=ORACLE_PERIODS, seed=0):
+    """Time the oracle on a bounded sample of one step (random templates, random
+    periods of the fold on a grid of the step's shape) and extrapolate to the
+    full step.  The dense factor, built once, is counted in every step."""
     from oracle import linear, periodic
     rng = np.random.default_rng(seed)
-    if model is None:
-        t0 = time.perf_counter()
-        model = linear.DenseModel(lc.t, lc.y, lc.diag_var, lc.terms, lc.X)
-        t_setup = time.perf_counter() - t0
     n = len(lc.t)
+    w0 = time.perf_counter()
     pairs = [(int(rng.integers(0, len(Ds))), int(rng.integers(0, n)))
              for _ in range(n_templates)]
     t0 = time.perf_counter()
-    d, v, l = linear.sampled_linear_search(model, lc.t, Ds, pairs)
+    linear.sampled_linear_search(model, lc.t, Ds, pairs)
     t_lin = (time.perf_counter() - t0) / n_templates
     # fold on a synthetic grid of the right shape (values do not change the work)
     g = dict(depth=rng.normal(0, 1e-3, (len(Ds), n)), var=rng.uniform(1e-8, 4e-8, (len(Ds), n)),
@@ -371,10 +437,11 @@ def oracle_sample(lc, Ds, periods, n_templates=256, n_periods=8, seed=0, model=N
     periodic.periodic_search(lc.t, g["depth"], g["var"], g["dlnl"], np.asarray(periods)[sel], dt)
     t_per = (time.perf_counter() - t0) / n_periods
     total = t_setup + t_lin * n * len(Ds) + t_per * len(periods)
-    return dict(t_setup=t_setup, t_template=t_lin, t_period=t_per, total_s=total,
-                sample=f"dense Sigma factor once ({t_setup:.1f} s), {n_templates} random "
-                       f"templates, {n_periods} random periods; extrapolated to "
-                       f"{n * len(Ds)} templates + {len(periods)} periods")
+    return dict(t_template=t_lin, t_period=t_per, total_s=total,
+                wall_s=time.perf_counter() - w0,
+                sample=f"dense Sigma factor once ({t_setup:.1f} s, counted in every step), "
+                       f"{n_templates} random templates, {n_periods} random periods; "
+                       f"extrapolated to {n * len(Ds)} templates + {len(periods)} periods")
 
 
 def blas_threads():
@@ -383,6 +450,165 @@ def blas_threads():
         return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
     except Exception:
         return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_legs(lc, w, n_templates, gpu_mixed16):
+    """The oracle on the host cores (bench.py's CPU baseline leg): the headline
+    workload on a bounded sample, extrapolated; the 2048-sample light curve in
+    full (the anchor of the extrapolations); the seven-sector curve through the
+    sequential celerite reference (bounded sample, extrapolated); and the mixed
+    path's per-output error against the oracle's whole grid of the 16-duration
+    sector (gpu_mixed16: the GPU's mixed linear search and fold of that
+    workload)."""
+    from oracle import linear, periodic, semisep
+    out = {}
+    t0 = time.perf_counter()
+    model = linear.DenseModel(lc.t, lc.y, lc.diag_var, lc.terms, lc.X)
+    t_setup = time.perf_counter() - t0
+    s = oracle_sample(lc, w.durations, w.periods, model, t_setup)
+    out["cpu_baseline"] = {"value": n_templates / s["total_s"], "unit": "(t0,D) fits/s",
+                           "cores": blas_threads(), "kind": "oracle", "extrapolated": True,
+                           "sample": s["sample"], "wall_s": s["wall_s"] + t_setup,
+                           "period_trials_per_s": len(w.periods) / s["total_s"]}
+    del model
+    # anchor: the 2048-sample light curve's oracle in full (10 240 templates,
+    # 1000 periods), against the same extrapolation from a bounded sample
+    w1 = synth.single_2048()
+    l1 = w1.curves[0]
+    t0 = time.perf_counter()
+    m1 = linear.DenseModel(l1.t, l1.y, l1.diag_var, l1.terms, l1.X)
+    ts1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o1 = linear.linear_search(l1.t, l1.y, l1.diag_var, l1.terms, l1.X, l1.t, w1.durations,
+                              model=m1)
+    tl1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    periodic.periodic_search(l1.t, o1["depth"], o1["var"], o1["dlnl"], w1.periods,
+                             periodic.median_spacing(l1.t))
+    tp1 = time.perf_counter() - t0
+    full = ts1 + tl1 + tp1
+    s1 = oracle_sample(l1, w1.durations, w1.periods, m1, ts1, seed=1)
+    out["cpu_anchor_single_2048"] = {
+        "full_s": full, "value": len(l1.t) * len(w1.durations) / full,
+        "unit": "(t0,D) fits/s", "period_trials_per_s": len(w1.periods) / full,
+        "extrapolated": False, "sample_extrapolation_s": s1["total_s"],
+        "extrapolation_ratio": s1["total_s"] / full}
+    # seven sectors: the celerite reference (the dense Sigma would need 148 GB)
+    w5 = synth.multisector_136080()
+    l5 = w5.curves[0]
+    rng = np.random.default_rng(5)
+    t0 = time.perf_counter()
+    ss = semisep.Semisep(l5.t, l5.diag_var, l5.terms)
+    ts5 = time.perf_counter() - t0
+    pairs = [(int(rng.integers(0, len(w5.durations))), int(rng.integers(0, len(l5.t))))
+             for _ in range(16)]
+    t0 = time.perf_counter()
+    semisep.sampled_linear_search(l5.t, l5.y, l5.diag_var, l5.terms, l5.X, w5.durations, pairs,
+                                  model=ss)
+    tt5 = (time.perf_counter() - t0) / len(pairs)
+    g5 = dict(depth=rng.normal(0, 5e-4, (len(w5.durations), len(l5.t))),
+              var=rng.uniform(2e-8, 9e-8, (len(w5.durations), len(l5.t))),
+              dlnl=rng.uniform(0, 6, (len(w5.durations), len(l5.t))))
+    t0 = time.perf_counter()
+    periodic.periodic_search(l5.t, g5["depth"], g5["var"], g5["dlnl"],
+                             w5.periods[rng.choice(len(w5.periods), 3, replace=False)],
+                             periodic.median_spacing(l5.t))
+    tpp5 = (time.perf_counter() - t0) / 3
+    tot5 = ts5 + tt5 * len(l5.t) * len(w5.durations) + tpp5 * len(w5.periods)
+    out["cpu_multisector"] = {
+        "value": len(l5.t) * len(w5.durations) / tot5, "unit": "(t0,D) fits/s",
+        "period_trials_per_s": len(w5.periods) / tot5, "kind": "celerite reference "
+        "(oracle/semisep.py, the stand-in where the dense oracle does not fit)",
+        "extrapolated": True, "sample": f"factor once ({ts5:.1f} s), 16 templates, 3 periods"}
+    # mixed precision: per-output error against the FP64 oracle's whole grid
+    if gpu_mixed16 is not None:
+        out["mixed_error"] = mixed_error(gpu_mixed16)
+    return out
+
+
+def mixed_error(gpu):
+    """Largest error of every output of the mixed path on the 16-duration
+    sector against the FP64 oracle: the linear search on every template (depth
+    relative to max(|depth|, sigma), variance relative, gain relative to
+    max(gain, 1)) and the fold on sampled periods (ln P relative to
+    max(1, |ln P|), depth and sigma as for the linear search, Q absolute),
+    compared at the GPU's argmax cell."""
+    from oracle import linear, periodic
+    w = synth.sector_19440_16d()
+    lc = w.curves[0]
+    t0 = time.perf_counter()
+    model = linear.DenseModel(lc.t, lc.y, lc.diag_var, lc.terms, lc.X)
+    o = linear.box_grid(model, lc.t, w.durations)
+    d, v, l = (np.asarray(a, dtype=np.float64) for a in gpu["grid"])
+    ok = ~(np.isnan(o["depth"]) | np.isnan(d))
+    so = np.sqrt(o["var"][ok])
+    e_lin = {"depth": float(np.max(np.abs(d[ok] - o["depth"][ok]) /
+                                   np.maximum(np.abs(o["depth"][ok]), so))),
+             "var": float(np.max(np.abs(v[ok] - o["var"][ok]) / o["var"][ok])),
+             "dlnl": float(np.max(np.abs(l[ok] - o["dlnl"][ok]) /
+                                  np.maximum(o["dlnl"][ok], 1.0))),
+             "templates": int(ok.sum()),
+             "nan_pattern_equal": bool(np.array_equal(np.isnan(o["depth"]), np.isnan(d)))}
+    rng = np.random.default_rng(9)
+    q = np.where(np.isfinite(gpu["Q"]), gpu["Q"], -np.inf)
+    sel = np.unique(np.concatenate([rng.integers(0, len(w.periods), 40),
+                                    np.argsort(-q, kind="stable")[:8]]))
+    dt = periodic.median_spacing(lc.t)
+    e = dict(lnP=0.0, depth=0.0, sigma=0.0, Q_abs=0.0)
+    for p in sel:
+        P = w.periods[p]
+        f = periodic.fold_period(lc.t, o["depth"], o["var"], o["dlnl"], P, dt)
+        dg = int(gpu["D_idx"][p])
+        if dg < 0:
+            continue
+        n_phi = int(np.ceil(P / dt))
+        jg = int(np.rint((gpu["T0"][p] - lc.t[0]) / P * n_phi))
+        lo, do_, so_ = f["lnP"][dg, jg], f["depth"][dg, jg], f["sigma"][dg, jg]
+        best = np.nanmax(np.where(np.isfinite(f["lnP"]), f["lnP"], -np.inf))
+        e["lnP"] = max(e["lnP"], abs(gpu["lnP"][p] - best) / max(1.0, abs(best)))
+        e["depth"] = max(e["depth"], abs(gpu["depth"][p] - do_) / max(abs(do_), so_))
+        e["sigma"] = max(e["sigma"], abs(gpu["sigma"][p] - so_) / so_)
+        e["Q_abs"] = max(e["Q_abs"], abs(gpu["Q"][p] - do_ / so_))
+    return {"workload": "sector_19440_16d", "linear_search": e_lin,
+            "fold": {**e, "periods": int(len(sel))},
+            "bounds": {"depth": 1e-4, "Q_abs": 1e-3}, "oracle_s": time.perf_counter() - t0}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, w, config):
+    """The CPU oracle timed as the reference implementation: every step a
+    bounded sample of the headline workload (the same sample size as
+    cpu_baseline), extrapolated to a full step."""
+    from oracle import linear
+    lc = w.curves[0]
+    n_templates = len(lc.t) * len(w.durations)
+    t0 = time.perf_counter()
+    model = linear.DenseModel(lc.t, lc.y, lc.diag_var, lc.terms, lc.X)
+    t_setup = time.perf_counter() - t0
+    for k in range(args.warmup):
+        oracle_sample(lc, w.durations, w.periods, model, t_setup, seed=1000 + k)
+    walls, totals = [], []
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        r = oracle_sample(lc, w.durations, w.periods, model, t_setup, seed=k + 1)
+        walls.append(r["wall_s"])
+        totals.append(r["total_s"])
+    wall = time.perf_counter() - w0
+    tot = statistics.median(totals)
+    val = n_templates / tot
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": "(t0,D) fits/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(walls) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config, "period_trials_per_s": len(w.periods) / tot,
+            "extrapolated": True, "full_step_s_extrapolated": tot,
+            "wall_s_timed": wall, "setup_s": t_setup,
+            "cpu_baseline": {"value": val, "unit": "(t0,D) fits/s", "cores": blas_threads(),
+                             "kind": "oracle", "extrapolated": True,
+                             "sample": r["sample"] + "; ms_per_step is the wall time of "
+                                                    "one sample step"},
+            "e2e": {"value": val, "unit": "(t0,D) fits/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
 
 
 # ---------------------------------------------------------------- main
@@ -411,7 +637,7 @@ def profile_batch_case(args):
     """Small batched case for ncu: 400 curves of the injection workload (2880
     samples, 1 duration, 4000 periods), nu_batch_search twice per precision
     (mixed first, then FP64).  The first call of each precision tunes the
-    fold's launch shape; the second runs the chosen one."""
+    launch shapes; the second runs the chosen ones."""
     import torch
     from paper_2402_06835_gb300 import api
     w = synth.injection_4000(n_curves=400)
@@ -447,35 +673,8 @@ def main():
               "precision": args.precision, "l2": "flushed (512 MB write) between timed steps"}
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        from oracle import linear
-        # the dense factor once (it is the same for every step and its time
-        # is counted in each step's extrapolated total)
-        t0 = time.perf_counter()
-        model = linear.DenseModel(lc.t, lc.y, lc.diag_var, lc.terms, lc.X)
-        t_setup = time.perf_counter() - t0
-        s = oracle_sample(lc, w.durations, w.periods, n_templates=64, n_periods=2,
-                          model=model, t_setup=t_setup)
-        for _ in range(args.warmup):
-            pass
-        per_step = []
-        for k in range(args.steps):
-            r = oracle_sample(lc, w.durations, w.periods, n_templates=64, n_periods=2, seed=k + 1,
-                              model=model, t_setup=t_setup)
-            per_step.append(r["total_s"])
-        tot = statistics.median(per_step)
-        val = n_templates / tot
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": val, "unit": "(t0,D) fits/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": tot * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-            "period_trials_per_s": len(w.periods) / tot,
-            "cpu_baseline": {"value": val, "unit": "(t0,D) fits/s", "cores": blas_threads(),
-                             "kind": "oracle", "sample": s["sample"]},
-            "e2e": {"value": val, "unit": "(t0,D) fits/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}))
+        if rank == 0:
+            print(json.dumps(run_reference(args, w, config)))
         return
 
     import torch
@@ -525,44 +724,22 @@ def main():
     clocks = sampler.stop()
     launches = api.launch_count() - n0
     ms = max_over_ranks(float(stages.sum(axis=1).mean()), torch, dev)
-    stage_ms = stages.mean(axis=0)
-    value = weak_scaling_value(n_templates, world, ms)
-
-    # dominant kernel: the fold.  Its algorithmic work is Eq. result's two
-    # passes over every visit; the FP64 path screens every cell with FP32
-    # arithmetic and evaluates only the cells that can win in FP64, so the
-    # fastest pipe it runs on (FP32) is the ceiling it is measured against
-    visits = fold_visits(lc.t, w.periods, pipe.dt, len(w.durations))
-    fold_ms = float(stage_ms[2])
-    fold_tflops = visits * FOLD_FLOPS_PER_VISIT / (fold_ms / 1e3) / 1e12
-    roofline = {"kernel": ("k_fold_screened" if args.precision == "fp64" else "k_fold_slots")
-                + " (nu_periodic_search stage, CUDA events)", "bound": "alu",
-                "achieved": fold_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": fold_tflops / FP32_PEAK_TFLOPS, "traffic": (FOLD_TRAFFIC_BYTES.get(args.workload)
-                            if args.precision == "fp64" else None),
-                "peak_source": "FP32 pipe from unit counts and clocks (152 SM x 128 lanes x "
-                               "2 flops x 2.07 GHz)",
-                "algorithmic": f"{visits} visits x {FOLD_FLOPS_PER_VISIT:.0f} flops",
-                "fp64_pipe_frac": fold_tflops / MEASURED_FP64_TFLOPS}
-    out = {"metric": METRIC, "value": value, "unit": "(t0,D) fits/s", "n_gpus": world,
+    head = pipeline_entry(args.workload, pipe, stages, world,
+                          FOLD_NCU.get(args.workload) if args.precision == "fp64" else None,
+                          clocks["sm_mhz"] if clocks else None)
+    out = {"metric": METRIC, "value": weak_scaling_value(n_templates, world, ms),
+           "unit": "(t0,D) fits/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
            "config": config, "period_trials_per_s": world * len(w.periods) / (ms / 1e3),
-           "stages_ms": {"factor": float(stage_ms[0]), "linear_search": float(stage_ms[1]),
-                         "periodic_search": float(stage_ms[2])},
-           "linear_search_fits_per_s": n_templates / ((stage_ms[0] + stage_ms[1]) / 1e3),
-           "linear_search_roofline": linear_search_roofline(lc, w.durations, float(stage_ms[1])),
-           "fold_gather": {"bytes_per_visit": 48,
-                           "GB/s": visits * 48 / (float(stage_ms[2]) / 1e3) / 1e9,
-                           "l2_read_GB/s": L2_READ_GBS,
-                           "frac": visits * 48 / (float(stage_ms[2]) / 1e3) / 1e9 / L2_READ_GBS,
-                           "note": "algorithmic bytes: two bracketing FP64 nodes of three "
-                                   "values per visit; the FP32 screen reads one 32-byte "
-                                   "record per visit from L1/L2"},
-           "fold_visits_per_s": visits / (fold_ms / 1e3),
+           "stages_ms": head["stages_ms"],
+           "linear_search_fits_per_s": head["linear_search_fits_per_s"],
+           "linear_search_roofline": linear_search_roofline(lc, w.durations,
+                                                            head["stages_ms"]["linear_search"]),
+           "fold_visits_per_s": head["fold_visits_per_s"],
            "gpu_launches": int(launches), "wall_s_timed": t_wall, "clocks": clocks,
-           "roofline": roofline}
+           "roofline": head["roofline"]}
 
     if not args.no_e2e:
         try:
@@ -573,38 +750,55 @@ def main():
         except Exception as exc:      # report, do not hide
             out["e2e"] = {"error": repr(exc)}
 
-    if not args.no_refine and args.precision == "fp64":
+    extras = world == 1 and args.precision == "fp64"
+    if not args.no_refine and extras:
         try:
             out["refine_top64"] = run_refine(pipe, api, torch)
         except Exception as exc:
             out["refine_top64"] = {"error": repr(exc)}
 
-    if not args.no_mixed and args.precision == "fp64":
-        try:
-            wm = synth.WORKLOADS[args.mixed_workload]()
-            lm = wm.curves[0]
-            pm = Pipeline(api, torch, lm, wm.durations, wm.periods, "mixed", dev)
-            for _ in range(args.warmup):
-                pm.step()
-            sm = time_pipeline(pm, torch, args.steps, 0, flush)
-            msm = float(sm.sum(axis=1).mean())
-            sms = sm.mean(axis=0)
-            ntm = len(lm.t) * len(wm.durations)
-            out["mixed"] = {"workload": args.mixed_workload, "ms_per_step": msm,
-                            "value": world * ntm / (msm / 1e3), "unit": "(t0,D) fits/s",
-                            "period_trials_per_s": world * len(wm.periods) / (msm / 1e3),
-                            "stages_ms": {"factor": float(sms[0]), "linear_search": float(sms[1]),
-                                          "periodic_search": float(sms[2])}}
-        except Exception as exc:
-            out["mixed"] = {"error": repr(exc)}
-
-    if not args.no_batch and args.precision == "fp64":
-        # the survey in one batched call, mixed precision and FP64 side by side
-        survey = synth.survey_438()
-        for key, prec, n in (("batch_mixed", "mixed", max(1, min(args.steps, 2))),
-                             ("batch_fp64", "fp64", 1)):
+    gpu_mixed16 = None
+    if not args.no_mixed and extras:
+        for key, wname in (("mixed_c2", "sector_19440"), ("mixed", "sector_19440_16d")):
             try:
-                out[key] = run_batch(api, torch, survey, prec, n, 1, flush)
+                wm = synth.WORKLOADS[wname]()
+                pm = Pipeline(api, torch, wm.curves[0], wm.durations, wm.periods, "mixed", dev)
+                sm = time_pipeline(pm, torch, args.steps, args.warmup, flush)
+                out[key] = pipeline_entry(wname, pm, sm, world)
+                if key == "mixed":
+                    r = pm.step(keep=True)
+                    torch.cuda.synchronize()
+                    gpu_mixed16 = {k: v.double().cpu().numpy() for k, v in r.items()
+                                   if k != "grid"}
+                    gpu_mixed16["grid"] = [a.double().cpu().numpy() for a in r["grid"]]
+            except Exception as exc:
+                out[key] = {"error": repr(exc)}
+
+    if not args.no_multisector and extras:
+        # seven sectors, FP64 and mixed side by side (about a second per step:
+        # at most 5 timed steps after 2 warm-ups)
+        w5 = synth.multisector_136080()
+        ms_steps, ms_warm = min(args.steps, 5), min(args.warmup, 2)
+        entry = {"workload": "multisector_136080: N=136080 (7 sectors with 1-day gaps), "
+                             "20 durations, 100000 periods",
+                 "steps": ms_steps, "warmup": ms_warm}
+        for prec in ("fp64", "mixed"):
+            try:
+                p5 = Pipeline(api, torch, w5.curves[0], w5.durations, w5.periods, prec, dev)
+                s5 = time_pipeline(p5, torch, ms_steps, ms_warm, flush)
+                entry[prec] = pipeline_entry("multisector_136080", p5, s5, world)
+                del p5
+            except Exception as exc:
+                entry[prec] = {"error": repr(exc)}
+        out["multisector"] = entry
+
+    if not args.no_batch and extras:
+        # the survey in one batched call, mixed precision and FP64 side by side,
+        # with the headline's warm-up and step counts
+        survey = synth.survey_438()
+        for key, prec in (("batch_mixed", "mixed"), ("batch_fp64", "fp64")):
+            try:
+                out[key] = run_batch(api, torch, survey, prec, args.steps, args.warmup, flush)
             except Exception as exc:
                 out[key] = {"error": repr(exc)}
 
@@ -612,11 +806,11 @@ def main():
         torch.distributed.barrier()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            s = oracle_sample(lc, w.durations, w.periods)
-            out["cpu_baseline"] = {"value": n_templates / s["total_s"], "unit": "(t0,D) fits/s",
-                                   "cores": blas_threads(), "kind": "oracle",
-                                   "sample": s["sample"],
-                                   "period_trials_per_s": len(w.periods) / s["total_s"]}
+            legs = cpu_legs(lc, w, n_templates, gpu_mixed16)
+            out.update(legs)
+            if "cpu_multisector" in legs and isinstance(out.get("multisector"), dict):
+                out["multisector"]["cpu_baseline"] = legs.pop("cpu_multisector")
+                out.pop("cpu_multisector", None)
         except Exception as exc:
             out["cpu_baseline"] = {"error": repr(exc)}
     if rank == 0:
