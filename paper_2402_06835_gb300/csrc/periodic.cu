@@ -1216,6 +1216,94 @@ __device__ __forceinline__ float2 gain_sum(const GainAhead& ga, const float* __r
     return make_float2(s0 + s1, K);
 }
 
+// 32-bit form of the gain walk (fewer instructions per epoch): positions in
+// units of 2^-F slot, started from the 64-bit position of a cell's first
+// epoch (truncated) and advanced by the rounded step, so that epoch k is at
+// most 1 + k/2 units from the 64-bit walk.  F is chosen per period so that
+// no position the walk loads (up to end + 11 steps: two cells walked
+// together, four epochs a round, one cell a round longer) exceeds 2^31, and the
+// walk is used only when that error stays below half a slot for every epoch
+// (the gain bound tolerates the exact interval starting one slot either side
+// of the walk's slot).  The end is widened by the same error, so every epoch
+// of the 64-bit walk is counted; positions past it add terms >= 0 (the walk
+// adds four terms at a time; a position past the row is clamped to the
+// padding slot zs, whose term is 0).
+struct GainWalk32 {
+    unsigned step, end;
+    int shift;            // 40 - F
+    int F;
+    int ok;
+};
+__device__ __forceinline__ GainWalk32 gain_walk32(unsigned long long ustep,
+                                                  unsigned long long uend) {
+    GainWalk32 w{0u, 0u, 0, 0, 0};
+    const double S40 = 9.094947017729282e-13;               // 2^-40
+    const double R = (double)ustep * S40;                    // slots per period
+    if (!(R > 0.0)) return w;
+    const double span = (double)uend * S40;
+    const double kmax = span / R + 2.0;                      // epochs walked, at most
+    const double top = span + 12.0 * R + kmax + 8.0;         // slots a position can reach
+    int F = 30 - ilogb(top);                                 // 2^F top < 2^31
+    if (F > 24) F = 24;
+    if (F < 8 || (kmax + 2.0) * ldexp(1.0, -F) > 0.5) return w;
+    w.F = F;
+    w.shift = 40 - F;
+    w.step = (unsigned)((ustep + (1ull << (w.shift - 1))) >> w.shift);
+    w.end = (unsigned)((uend >> w.shift) + 2ull + (unsigned long long)(kmax + 2.0));
+    w.ok = w.step > 0u;
+    return w;
+}
+// Two cells of one period walked together (eight loads in flight): their
+// sums and counts.  A cell that is not valid (v = false) walks the other's
+// positions and adds nothing, so no position exceeds the other cell's last
+// round by more than one (the cells' epoch counts differ by at most one).
+__device__ __forceinline__ float4 gain_sum32x2(const float* __restrict__ l1,
+                                               const float* __restrict__ l2, unsigned zs,
+                                               unsigned u1, unsigned u2, bool v1, bool v2,
+                                               const GainWalk32& w) {
+    float a = 0.f, ka = 0.f, b = 0.f, kb = 0.f;
+    const unsigned st = w.step;
+    if (!v1) u1 = u2;
+    if (!v2) u2 = u1;
+    while ((v1 && u1 < w.end) || (v2 && u2 < w.end)) {
+        const float x0 = l1[min(u1 >> w.F, zs)];
+        const float x1 = l1[min((u1 + st) >> w.F, zs)];
+        const float x2 = l1[min((u1 + 2u * st) >> w.F, zs)];
+        const float x3 = l1[min((u1 + 3u * st) >> w.F, zs)];
+        const float y0 = l2[min(u2 >> w.F, zs)];
+        const float y1 = l2[min((u2 + st) >> w.F, zs)];
+        const float y2 = l2[min((u2 + 2u * st) >> w.F, zs)];
+        const float y3 = l2[min((u2 + 3u * st) >> w.F, zs)];
+        if (v1 && u1 < w.end) {
+            a += (x0 + x2) + (x1 + x3);
+            ka += 4.f;
+        }
+        if (v2 && u2 < w.end) {
+            b += (y0 + y2) + (y1 + y3);
+            kb += 4.f;
+        }
+        u1 += 4u * st;
+        u2 += 4u * st;
+    }
+    return make_float4(a, ka, b, kb);
+}
+
+__device__ __forceinline__ float2 gain_sum32(const float* __restrict__ lm, unsigned zs,
+                                             unsigned u, const GainWalk32& w) {
+    float s0 = 0.f, s1 = 0.f, K = 0.f;
+    const unsigned st = w.step;
+    for (; u < w.end; u += 4u * st) {
+        const float a = lm[min(u >> w.F, zs)];
+        const float b = lm[min((u + st) >> w.F, zs)];
+        const float c = lm[min((u + 2u * st) >> w.F, zs)];
+        const float e = lm[min((u + 3u * st) >> w.F, zs)];
+        s0 += a + c;
+        s1 += b + e;
+        K += 4.f;
+    }
+    return make_float2(s0 + s1, K);
+}
+
 // A warp whose gain bounds pass at least NU_GAIN_PASS_MAX of its 32 cells
 // screens its next NU_GAIN_DIRECT_ROUNDS rounds in full without them.
 #ifndef NU_GAIN_PASS_MAX
@@ -1412,6 +1500,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     // the screen loop (most of these are read only on rare paths)
     __shared__ ScreenPeriod sh_sp;
     __shared__ CellCtx sh_cc;
+    __shared__ GainWalk32 sh_gw;
     const int64_t n_phi = TAB ? pc->n_phi : (int64_t)ceil(P / g.dt);
     if (threadIdx.x == 0) sh_sp = TAB ? screen_period(g, sg, P, *pc) : screen_period(g, sg, P, n_phi);
     __syncthreads();
@@ -1423,6 +1512,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     const int64_t n_cells = n_phi * n_D;
     sh_tb[threadIdx.x] = Best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (threadIdx.x == 0) {
+        sh_gw = gain_walk32(sh_sp.ustep, sh_sp.uend);
         sh_cc = TAB ? cell_ctx(g, P, *pc) : cell_ctx(g, P, n_phi);
         sh_sbest = max_key(-INFINITY);
         sh_bfk = fkey(-INFINITY);
@@ -1544,11 +1634,14 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         if (!first && cascade && direct == 0) {
             float gb = -INFINITY;
             if (cell < n_cells) {
-                // ln P <= S_L + 1/2, with the gain bound's margins
+                // ln P <= S_L + 1/2, with the gain bound's margins (one cell
+                // per lane: walking two at once spills in this kernel)
                 const float* lr = sg.lm3 + (int64_t)d * sg.n_slots;
                 const unsigned long long u0 = (unsigned long long)j * sp.uph;
-                const float2 sk = gain_sum(gain_ahead(lr, ns1, u0, sp.ustep), lr, ns1, u0,
-                                           sp.ustep, sp.uend);
+                const float2 sk =
+                    sh_gw.ok ? gain_sum32(lr, ns1 - 1u, (unsigned)(u0 >> sh_gw.shift), sh_gw)
+                             : gain_sum(gain_ahead(lr, ns1, u0, sp.ustep), lr, ns1, u0,
+                                        sp.ustep, sp.uend);
                 gb = sk.x * fmaf(sk.y + 16.f, 1.1920929e-7f, 1.f) + 0.5f + 1e-6f;
             }
             const bool pass = cell < n_cells && !(gb < from_fkey(sh_bfk));
@@ -1801,6 +1894,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     // the gain walk adds 4 positions past ulast at most: ustep < 2^60 keeps
     // them from wrapping (ulast < 2^62)
     const bool cascade = lgm != nullptr && ustep < (1ull << 60);
+    const GainWalk32 gw = gain_walk32(ustep, ulast + 1);
     auto best_now = [&]() {
         const unsigned int kb = sh_best;
         return fmaxf(bl, kb ? __uint_as_float((kb >> 31) ? (kb & 0x7fffffffu) : ~kb)
@@ -1903,28 +1997,61 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         }
         const int64_t cell = base + lane;
         if (!first && cascade && direct == 0) {
-            bool pass = false;
-            if (cell < n_cells) {
-                // epochs with u <= ulast
+            // two rounds at once where the 32-bit walk applies (epochs with
+            // u <= ulast): this round's cells and the next round's
+            const bool pair = gw.ok != 0;
+            int64_t j2 = j + (pair ? (int64_t)blockDim.x : 0);
+            int d2 = d;
+            while (j2 >= n_phi) {
+                j2 -= n_phi;
+                ++d2;
+            }
+            const int64_t cell2 = cell + blockDim.x;
+            float2 sk = make_float2(0.f, 0.f), sk2 = make_float2(0.f, 0.f);
+            if (pair) {
+                const bool v1 = cell < n_cells, v2 = cell2 < n_cells;
+                if (v1 || v2) {
+                    const float4 s4 = gain_sum32x2(
+                        lgm + (int64_t)d * n_slots, lgm + (int64_t)d2 * n_slots, ns1 - 1u,
+                        (unsigned)(((unsigned long long)j * uph) >> gw.shift),
+                        (unsigned)(((unsigned long long)j2 * uph) >> gw.shift), v1, v2, gw);
+                    sk = make_float2(s4.x, s4.y);
+                    sk2 = make_float2(s4.z, s4.w);
+                }
+            } else if (cell < n_cells) {
                 const float* lr = lgm + (int64_t)d * n_slots;
                 const unsigned long long u0 = (unsigned long long)j * uph;
-                const float2 sk = gain_sum(gain_ahead(lr, ns1, u0, ustep), lr, ns1, u0, ustep,
-                                           ulast + 1);
-                // the margins of cannot_win_f on top of the rounding of the sum
-                const float gb = sk.x * fmaf(sk.y + 16.f, 1.1920929e-7f, 1.f) + 0.5f;
-                pass = sk.y > 0.f && !(gb + 1e-4f * fmaxf(1.f, fabsf(gb)) < best_now());
+                sk = gain_sum(gain_ahead(lr, ns1, u0, ustep), lr, ns1, u0, ustep, ulast + 1);
             }
+            // the margins of cannot_win_f on top of the rounding of the sum
+            const float thr = best_now();
+            auto passes = [&](const float2& v) {
+                const float gb = v.x * fmaf(v.y + 16.f, 1.1920929e-7f, 1.f) + 0.5f;
+                return v.y > 0.f && !(gb + 1e-4f * fmaxf(1.f, fabsf(gb)) < thr);
+            };
+            const bool pass = cell < n_cells && passes(sk);
+            const bool pass2 = pair && cell2 < n_cells && passes(sk2);
             if (__popc(__ballot_sync(FULL, pass)) >= NU_GAIN_PASS_MAX)
                 direct = NU_GAIN_DIRECT_ROUNDS;
-            const unsigned m = __ballot_sync(FULL, pass);
-            if (pass) {
-                const int pos = na + __popc(m & ((1u << lane) - 1u));
-                qa[pos] = cell;
-                qad[pos] = d;
+            auto push_a = [&](bool keep, long long cl, int dl) {
+                const unsigned m = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int pos = na + __popc(m & ((1u << lane) - 1u));
+                    qa[pos] = cl;
+                    qad[pos] = dl;
+                }
+                na += __popc(m);
+                __syncwarp();
+                if (na >= 32) flush_a(32);
+            };
+            push_a(pass, cell, d);
+            if (pair) {
+                push_a(pass2, cell2, d2);
+                // the loop's increment moves past the second round
+                base += blockDim.x;
+                j = j2;
+                d = d2;
             }
-            na += __popc(m);
-            __syncwarp();
-            if (na >= 32) flush_a(32);
         } else {
             if (direct > 0) --direct;
             SCell e;
