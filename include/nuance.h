@@ -321,10 +321,16 @@ uint64_t nu_periodic_search_noalloc_limit(void);
  *                 tb_c = sum of n_terms_host[0..c-1]
  *   k             1 or 2: X = [1] or [1, t] per curve
  *   Ds_host (n_D), periods_dev (n_P): shared grids
- *   phase_step    > 0 (shared by all curves)
+ *   phase_step    > 0 (shared by all curves), or 0 for the median sample
+ *                 spacing of the first curve (computed on the host from a
+ *                 copy of that curve's times)
  *   outputs, [n_lc][n_P] each: Q, T0, D_idx, depth, sigma, lnP (as in
  *   nu_periodic_search); status_host (n_lc) per-curve factor status.
  * Synchronises the stream before returning (the statuses are host data).
+ * The launch shapes of the fold and of the linear search are tuned the first
+ * time a configuration (state size, k, precision, n_D) is seen in the process
+ * and cached; the executable graph of a configuration (the same and n_lc,
+ * total samples, n_P) is kept and updated with the next call's parameters.
  * Errors: NU_EINVAL, NU_ENOMEM, NU_ECUDA. */
 nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
                           const double* t_dev, const double* y_dev,

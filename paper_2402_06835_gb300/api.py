@@ -324,9 +324,9 @@ def nu_batch_search(curves, Ds, periods, k=2, precision="fp64", phase_step=None,
 
     curves: list of (t, y, diag_var, terms); arrays may be numpy or CUDA
     tensors (float64).  The design matrix of every curve is [1, t][:k].
-    phase_step: shared phase step (default: the median spacing of the first
-    curve).  Returns a dict of (n_lc, n_P) tensors and 'status' (list of
-    per-curve factor statuses, 0 = OK).
+    phase_step: shared phase step (None or 0: the library takes the median
+    sample spacing of the first curve).  Returns a dict of (n_lc, n_P)
+    tensors and 'status' (list of per-curve factor statuses, 0 = OK).
     """
     dev = torch.device("cuda", torch.cuda.current_device())
     as_dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev).reshape(-1)
@@ -347,7 +347,7 @@ def nu_batch_search(curves, Ds, periods, k=2, precision="fp64", phase_step=None,
     periods = as_dev(periods).contiguous()
     n_P = periods.numel()
     if phase_step is None:
-        phase_step = float(torch.median(ts[0][1:] - ts[0][:-1]).item())
+        phase_step = 0.0
     res = {name: torch.empty((n_lc, n_P), dtype=torch.float64, device=dev)
            for name in ("Q", "T0", "depth", "sigma", "lnP")}
     res["D_idx"] = torch.empty((n_lc, n_P), dtype=torch.int32, device=dev)

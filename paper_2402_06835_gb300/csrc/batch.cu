@@ -8,10 +8,15 @@
 // balances curves of different spans.  Host work (validation, layout, a
 // regularity test of each curve's cadence, uploads of the small tables)
 // happens before capture; the kernels are captured into one CUDA graph and
-// launched once.  The fold's launch shape (threads per block, resident
-// blocks per SM) is chosen by a small autotuner the first time a
-// configuration is seen: the candidates are timed on a slice of the batch
-// and the fastest is cached for the process.
+// launched once.  The instantiated graph of a configuration is kept and, on
+// later calls, updated in place with the new call's parameters
+// (cudaGraphExecUpdate) instead of being instantiated again.  The launch
+// shapes of the fold (threads per block, resident blocks per SM) and of the
+// linear search's window-start kernel (window starts per block, staged chunk)
+// are chosen by a small autotuner the first time a configuration is seen:
+// the candidates are timed on a slice of the batch and the fastest are
+// cached for the process.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -55,11 +60,46 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int blocks_per_sm, threads;
+    int blocks_per_sm, threads;     // fold
+    WindowShape win;                // linear search
 };
 
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
+
+// Instantiated graphs by configuration (device, state size, k, precision,
+// grid sizes, batch shape and tuned launch shapes).  A call takes its entry
+// out of the cache while it uses it, so two threads never launch one
+// executable graph at once.
+struct GraphKey {
+    int dev, nb, k, prec, n_D, n_lc, bps, threads, tlo, ch;
+    int64_t N, n_P;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(dev, nb, k, prec, n_D, n_lc, bps, threads, tlo, ch, N, n_P) <
+               std::tie(o.dev, o.nb, o.k, o.prec, o.n_D, o.n_lc, o.bps, o.threads, o.tlo, o.ch,
+                        o.N, o.n_P);
+    }
+};
+std::mutex g_graph_mu;
+std::map<GraphKey, cudaGraphExec_t> g_graphs;
+constexpr size_t GRAPH_CACHE_MAX = 8;
+
+cudaGraphExec_t take_graph(const GraphKey& key) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) return nullptr;
+    cudaGraphExec_t e = it->second;
+    g_graphs.erase(it);
+    return e;
+}
+void put_graph(const GraphKey& key, cudaGraphExec_t exec) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    if (g_graphs.count(key) || g_graphs.size() >= GRAPH_CACHE_MAX) {
+        cudaGraphExecDestroy(exec);
+        return;
+    }
+    g_graphs[key] = exec;
+}
 
 }  // namespace nu
 
@@ -81,8 +121,8 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         return fail(NU_EINVAL, "nu_batch_search: null argument or n_lc < 1");
     if (k < 0 || k > 2) return fail(NU_EINVAL, "nu_batch_search: k must be 0, 1 or 2");
     if (n_D < 1 || n_P < 1) return fail(NU_EINVAL, "nu_batch_search: empty grid");
-    if (!(phase_step > 0.0) || !std::isfinite(phase_step))
-        return fail(NU_EINVAL, "nu_batch_search: phase_step must be > 0");
+    if (!(phase_step >= 0.0) || !std::isfinite(phase_step))
+        return fail(NU_EINVAL, "nu_batch_search: phase_step must be >= 0");
     if (prec != NU_FP64 && prec != NU_MIXED)
         return fail(NU_EINVAL, "nu_batch_search: unknown precision");
     if (offsets_host[0] != 0) return fail(NU_EINVAL, "nu_batch_search: offsets[0] must be 0");
@@ -112,6 +152,23 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     for (int g = 0; g < n_lc; ++g) n_per[g] = offsets_host[g + 1] - offsets_host[g];
     const FactorPlan plan = plan_factor(n_per.data(), blocks.data(), n_lc, k);
     cudaStream_t st = (cudaStream_t)stream;
+    if (phase_step == 0.0) {
+        // default phase step: the median sample spacing of the first curve
+        // (a host copy of its times; this synchronises the stream)
+        const int64_t n0 = offsets_host[1];
+        std::vector<double> h(n0);
+        cudaError_t ec = cudaMemcpyAsync(h.data(), t_dev, n0 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, st);
+        if (ec == cudaSuccess) ec = cudaStreamSynchronize(st);
+        if (ec != cudaSuccess) return cuda_fail(ec, "nu_batch_search: copy of curve 0");
+        std::vector<double> d(n0 - 1);
+        for (int64_t i = 0; i + 1 < n0; ++i) d[i] = h[i + 1] - h[i];
+        std::sort(d.begin(), d.end());
+        const size_t m = d.size();
+        phase_step = (m % 2) ? d[m / 2] : 0.5 * (d[m / 2 - 1] + d[m / 2]);
+        if (!(phase_step > 0.0) || !std::isfinite(phase_step))
+            return fail(NU_EINVAL, "nu_batch_search: curve 0 gives no positive median spacing");
+    }
     pool_keep_memory();
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     // ------------------------------------------------------- factor memory
@@ -245,6 +302,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     // the enqueue of everything after setup (graph body)
     cudaStream_t side = thread_side_stream();
     cudaError_t enq_err = cudaSuccess;      // first failed enqueue of a memset
+    WindowShape win_shape = default_window_shape(N);
     auto enqueue = [&](int grid, int threads, int64_t nP_run, int n_run,
                        cudaStream_t st) -> int {
         int l = 0;
@@ -254,7 +312,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         launch_factor(plan, fb, ws, diag_var_dev, nullptr, 0, y_dev, st, side, &lf);
         l += lf;
         int* wplan = win_lo ? (int*)(mem + o_wplan) : nullptr;
-        const WindowShape wsh = default_window_shape(N);
+        const WindowShape wsh = win_shape;
         if (fp64) {
             FactorView<double> fv{fb.F, fb.kg, fb.invD, fb.G, fb.z0, fb.Zt};
             l += launch_window_batch(nb, true, t_dev, k, &fv, s_off_dev, n_lc, N, Ds_dev, n_D,
@@ -281,7 +339,7 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     };
     // ------------------------------------------------------- autotuning
     const TuneKey key{nb, k, (int)prec, n_D};
-    TuneVal tv{0, 0};
+    TuneVal tv{0, 0, win_shape};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(key);
@@ -328,7 +386,41 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best_ms) {
                 best_ms = ms;
-                tv = TuneVal{cand[c][0], cand[c][1]};
+                tv.blocks_per_sm = cand[c][0];
+                tv.threads = cand[c][1];
+            }
+        }
+        // the linear search's window-start kernel on the same curves: window
+        // starts per block x samples per staged chunk
+        if (win_lo) {
+            const WindowShape wc[6] = {{32, 64}, {64, 64}, {64, 32}, {128, 64}, {128, 128},
+                                       {256, 64}};
+            const int64_t n_part = offsets_host[n_run];
+            float best_lin = 1e30f;
+            for (int c = 0; c < 6; ++c) {
+                cudaEventRecord(e0, st);
+                int lt;
+                if (fp64) {
+                    FactorView<double> fv{fb.F, fb.kg, fb.invD, fb.G, fb.z0, fb.Zt};
+                    lt = launch_window_batch(nb, true, t_dev, k, &fv, s_off_dev, n_run, n_part,
+                                             Ds_dev, n_D, (int*)(mem + o_wplan), wc[c], lin_d,
+                                             lin_v, lin_l, st);
+                } else {
+                    FactorView<float> fv{fb.F32, fb.kg32, fb.invD32, fb.G32, fb.z032, fb.Zt32};
+                    lt = launch_window_batch(nb, false, t_dev, k, &fv, s_off_dev, n_run, n_part,
+                                             Ds_dev, n_D, (int*)(mem + o_wplan), wc[c], lin_d,
+                                             lin_v, lin_l, st);
+                }
+                count_launches(lt);
+                launched += lt;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_lin) {
+                    best_lin = ms;
+                    tv.win = wc[c];
+                }
             }
         }
         cudaEventDestroy(e0);
@@ -336,11 +428,16 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune[key] = tv;
     }
+    win_shape = tv.win;
     // ------------------------------------------------ capture and launch
     // capture on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured), launch on the caller's stream
+    // the executable graph of this configuration, when a previous call left
+    // one, takes this call's parameters (buffers, outputs) by an update
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    const GraphKey gkey{dev, nb, k, (int)prec, n_D, n_lc, tv.blocks_per_sm, tv.threads,
+                        win_shape.tlo, win_shape.ch, N, n_P};
+    cudaGraphExec_t exec = take_graph(gkey);
     cudaStream_t cs = nullptr;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     int in_graph = 0;
@@ -350,10 +447,20 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
         e = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess && enq_err != cudaSuccess) e = enq_err;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess && exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();                 // clear the failed update
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    }
+    if (e == cudaSuccess && !exec) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (exec) cudaGraphExecDestroy(exec);
+    if (exec) {
+        if (e == cudaSuccess) put_graph(gkey, exec); else cudaGraphExecDestroy(exec);
+    }
     if (graph) cudaGraphDestroy(graph);
     if (cs) cudaStreamDestroy(cs);
     if (e != cudaSuccess) {

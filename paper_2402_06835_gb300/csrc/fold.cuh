@@ -86,6 +86,7 @@ struct FoldBatch {
     std::vector<FoldSeg> segs;
     int64_t n_bucket_total = 0, n_rec_total = 0, n_srec_total = 0;
     bool any_slots = false, any_exact = false;
+    bool slot_cascade = false;   // some curve's grid is large enough for the mixed cascade
 };
 
 void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double>& t_first,

@@ -1255,16 +1255,23 @@ __device__ __forceinline__ GainWalk32 gain_walk32(unsigned long long ustep,
 }
 // Two cells of one period walked together (eight loads in flight): their
 // sums and counts.  A cell that is not valid (v = false) walks the other's
-// positions and adds nothing, so no position exceeds the other cell's last
-// round by more than one (the cells' epoch counts differ by at most one).
+// row and positions and adds nothing (its own row pointer may lie past the
+// table), so no position exceeds the other cell's last round by more than
+// one (the cells' epoch counts differ by at most one).
 __device__ __forceinline__ float4 gain_sum32x2(const float* __restrict__ l1,
                                                const float* __restrict__ l2, unsigned zs,
                                                unsigned u1, unsigned u2, bool v1, bool v2,
                                                const GainWalk32& w) {
     float a = 0.f, ka = 0.f, b = 0.f, kb = 0.f;
     const unsigned st = w.step;
-    if (!v1) u1 = u2;
-    if (!v2) u2 = u1;
+    if (!v1) {
+        u1 = u2;
+        l1 = l2;
+    }
+    if (!v2) {
+        u2 = u1;
+        l2 = l1;
+    }
     while ((v1 && u1 < w.end) || (v2 && u2 < w.end)) {
         const float x0 = l1[min(u1 >> w.F, zs)];
         const float x1 = l1[min((u1 + st) >> w.F, zs)];
@@ -1303,6 +1310,12 @@ __device__ __forceinline__ float2 gain_sum32(const float* __restrict__ lm, unsig
     }
     return make_float2(s0 + s1, K);
 }
+
+// The mixed fold's cascade runs on periods with at least NU_CASCADE_ROUNDS
+// rounds of cells per warp.
+#ifndef NU_CASCADE_ROUNDS
+#define NU_CASCADE_ROUNDS 32
+#endif
 
 // A warp whose gain bounds pass at least NU_GAIN_PASS_MAX of its 32 cells
 // screens its next NU_GAIN_DIRECT_ROUNDS rounds in full without them.
@@ -1845,11 +1858,15 @@ __global__ void k_slot_gain(const Node4<float>* __restrict__ rec, int64_t n,
 //   2. queued, 32 at a time: the first pass (FP32 sums) and the bound of
 //      cannot_win_f;
 //   3. queued, 32 at a time: the second pass, whose ln P raises the threshold.
-// In its first round a warp runs the first pass on its own cells, and the
-// lane with the largest bound evaluates its cell at once (the threshold's
-// seed).  Warps whose gain bounds pass almost every cell (cells of many
-// epochs) skip step 1 for their next rounds.
-template <int KC, int MAXT = 256>
+// A warp's first round runs the first pass directly.  Warps whose gain
+// bounds pass almost every cell (cells of many epochs) skip step 1 for their
+// next rounds, and periods with few cells per warp (short curves) skip it
+// throughout: their threshold does not rise in time for the bound to pay.
+// CASC = false compiles the fold without the cascade (its registers spill
+// the plain path's), for grids too small for it (the host decides).
+// (Evaluating the best-bounded cell of the first round at once, as a seed
+// of the threshold, did not pay either.)
+template <int KC, int MAXT = 256, bool CASC = true>
 __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ rec,
                                                const float* __restrict__ lgm,
                                                int64_t n_slots, int n_D, double dt,
@@ -1892,8 +1909,11 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     int na = 0;
     const unsigned ns1 = (unsigned)(n_slots - 1);
     // the gain walk adds 4 positions past ulast at most: ustep < 2^60 keeps
-    // them from wrapping (ulast < 2^62)
-    const bool cascade = lgm != nullptr && ustep < (1ull << 60);
+    // them from wrapping (ulast < 2^62).  The cascade needs the threshold to
+    // rise before it pays: periods of fewer than NU_CASCADE_ROUNDS rounds of
+    // cells per warp (short light curves) run the first pass on every cell.
+    const bool cascade = CASC && lgm != nullptr && ustep < (1ull << 60) &&
+                         n_cells >= (int64_t)NU_CASCADE_ROUNDS * blockDim.x;
     const GainWalk32 gw = gain_walk32(ustep, ulast + 1);
     auto best_now = [&]() {
         const unsigned int kb = sh_best;
@@ -1959,7 +1979,10 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         if (lane < nq) q[lane] = e2;
         __syncwarp();
     };
-    // first passes of the first cnt entries of queue A, one per lane
+    // first passes of the first cnt entries of queue A, one per lane; the
+    // survivors join queue B, which is flushed at once when it holds 32
+    // (queue B never holds more than 63 entries: a round can flush queue A
+    // twice)
     auto flush_a = [&](int cnt) {
         SCell e;
         float ub;
@@ -1970,6 +1993,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
             keep = pass1(dl, cl - (int64_t)dl * n_phi, cl, e, &ub);
         }
         push_b(keep, e);
+        if (nq >= 32) flush_b();
         __syncwarp();
         na -= cnt;
         long long c2 = 0;
@@ -2057,23 +2081,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
             SCell e;
             float ub = -INFINITY;
             const bool keep = cell < n_cells && pass1(d, j, cell, e, &ub);
-            if (first) {
-                // seed: the kept lane with the largest S_L + 1/2 evaluates its
-                // cell now (it is evaluated again from the queue, same result)
-                first = false;
-                float v = keep ? ub : -INFINITY;
-                int src = lane;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float v2 = __shfl_xor_sync(FULL, v, o);
-                    const int s2 = __shfl_xor_sync(FULL, src, o);
-                    if (v2 > v || (v2 == v && s2 < src)) {
-                        v = v2;
-                        src = s2;
-                    }
-                }
-                if (v > -INFINITY && lane == src) pass2(e);
-                __syncwarp();
-            }
+            first = false;
             push_b(keep, e);
         }
         if (nq >= 32) flush_b();
@@ -2098,7 +2106,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
 #define NU_SLOTS_MIN_BLOCKS 4
 #endif
 
-template <int KC, int MAXT>
+template <int KC, int MAXT, bool CASC>
 __global__ void __launch_bounds__(MAXT, NU_SLOTS_MIN_BLOCKS * 256 / MAXT)
 k_fold_slots(const Node4<float>* __restrict__ rec, const float* __restrict__ lgm,
              int64_t n_slots, int n_D, double dt, double t_ref, double t_last,
@@ -2108,8 +2116,8 @@ k_fold_slots(const Node4<float>* __restrict__ rec, const float* __restrict__ lgm
              double* __restrict__ lnp_out) {
     const int64_t p = blockIdx.x;
     if (p >= n_P) return;
-    fold_slots_one<KC, MAXT>(rec, lgm, n_slots, n_D, dt, t_ref, t_last, periods[p], p, Q_out,
-                             T0_out, Didx_out, dep_out, sig_out, lnp_out);
+    fold_slots_one<KC, MAXT, CASC>(rec, lgm, n_slots, n_D, dt, t_ref, t_last, periods[p], p,
+                                   Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
 // ------------------------------------------------------------ batch path
@@ -2127,7 +2135,7 @@ template <int KIND, int MAXT>
 struct BatchBlocks {
     static constexpr int value =
         KIND == 0 ? (MAXT <= 64 ? 10 : (MAXT <= 128 ? 5 : NU_SCREEN_MIN_BLOCKS))
-                  : (KIND == 2 ? NU_SLOTS_MIN_BLOCKS * 256 / MAXT : 1);
+                  : (KIND >= 2 ? NU_SLOTS_MIN_BLOCKS * 256 / MAXT : 1);
 };
 
 template <int KIND, int MAXT>
@@ -2156,10 +2164,10 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
         const int g = (int)(item / (unsigned long long)n_P);
         const int64_t p = (int64_t)(item % (unsigned long long)n_P);
         const FoldSeg fs = segs[g];
-        if ((KIND == 2) != (fs.use_slots != 0)) continue;
+        if ((KIND >= 2) != (fs.use_slots != 0)) continue;
         const int64_t o = (int64_t)g * n_P + p;
-        if (KIND == 2) {
-            fold_slots_one<8, MAXT>(rec + fs.rec_off, lgm + fs.rec_off, fs.n_slots, n_D, dt,
+        if (KIND >= 2) {
+            fold_slots_one<8, MAXT, KIND == 2>(rec + fs.rec_off, lgm + fs.rec_off, fs.n_slots, n_D, dt,
                                     fs.t_ref, fs.t_last,
                               periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                               lnp_out);
@@ -2340,6 +2348,8 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
         f.rec_off = fb.n_rec_total;
         fb.n_rec_total += f.use_slots ? f.n_slots * n_D : 0;
         fb.any_slots = fb.any_slots || f.use_slots;
+        if (f.use_slots && f.n_slots * (int64_t)n_D >= (int64_t)NU_CASCADE_ROUNDS * 128)
+            fb.slot_cascade = true;
         fb.any_exact = fb.any_exact || !f.use_slots;
     }
 }
@@ -2451,7 +2461,10 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
         ++launched;
     }
     if (fb.any_slots) {
-        NU_FB_SIZE(2, counter + 1);
+        if (fb.slot_cascade)
+            NU_FB_SIZE(2, counter + 1);
+        else
+            NU_FB_SIZE(3, counter + 1);
         ++launched;
     }
 #undef NU_FB_SIZE
@@ -2541,14 +2554,18 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             n_t0, n_D, n_slots, rec);
         float* lgm = (float*)(scratch + L.lgm);
         k_slot_gain<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec, lgm);
-        if (n_P >= NU_SLOTS_SMALL_FROM)
-            k_fold_slots<8, NU_SLOTS_SMALL><<<(unsigned)n_P, NU_SLOTS_SMALL, 0, st>>>(
-                rec, lgm, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev,
-                T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
-        else
-            k_fold_slots<8, 256><<<(unsigned)n_P, 256, 0, st>>>(
-                rec, lgm, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev,
-                T0_dev, D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+        // the cascade's instance where a period can hold enough cells for it
+        const bool casc = nrec >= (int64_t)NU_CASCADE_ROUNDS * 128;
+#define NU_FS(MAXT_, CASC_)                                                                \
+    k_fold_slots<8, MAXT_, CASC_><<<(unsigned)n_P, MAXT_, 0, st>>>(                        \
+        rec, lgm, n_slots, n_D, phase_step, t_ref, t_last, periods_dev, n_P, Q_dev, T0_dev, \
+        D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev)
+        if (n_P >= NU_SLOTS_SMALL_FROM) {
+            if (casc) NU_FS(NU_SLOTS_SMALL, true); else NU_FS(NU_SLOTS_SMALL, false);
+        } else {
+            if (casc) NU_FS(256, true); else NU_FS(256, false);
+        }
+#undef NU_FS
         launched += 4;
     } else {
         k_buckets<<<div_up(n_bucket, 256), 256, 0, st>>>(t0s_dev, n_t0, t_ref, phase_step,

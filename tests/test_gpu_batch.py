@@ -146,3 +146,69 @@ def test_batch_with_wide_tree_levels():
         for key in ("Q", "T0", "lnP", "depth", "sigma"):
             np.testing.assert_allclose(res[key][c].cpu().numpy(), one[key], rtol=1e-12, atol=0,
                                        err_msg=key)
+
+
+def test_batch_default_phase_step_is_first_curve_median(curves):
+    """phase_step = 0 (None in the binding): the library takes the median
+    sample spacing of the first curve, as the explicit value does."""
+    items = [(lc.t, lc.y, lc.diag_var, lc.terms) for lc in curves]
+    dt = float(np.median(np.diff(curves[0].t)))
+    a = api.nu_batch_search(items, DS, PERIODS, k=2, precision="fp64", phase_step=None)
+    b = api.nu_batch_search(items, DS, PERIODS, k=2, precision="fp64", phase_step=dt)
+    for key in ("Q", "T0", "D_idx", "lnP", "depth", "sigma"):
+        assert torch.equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_graph_reuse_across_calls(precision):
+    """The executable graph of a configuration is kept and updated with each
+    call's buffers: two batches of the same shape and different data, called
+    alternately (and with fresh output tensors every time), each give the
+    results of their own first call, and in FP64 those of the single-curve
+    calls."""
+    dt = synth.CADENCE_DAYS
+    sets = []
+    for base in (200, 260):
+        cs = [synth.small_curve(n=n, seed=base + c, p_rot=0.3 + 0.1 * c, sigma=6e-3,
+                                gap=(30 if c == 1 else None), inject=(3e-3, 1.0 / 24.0, 0.41))
+              for c, n in enumerate((350, 420, 380))]
+        sets.append(cs)
+    runs = []
+    for rep in range(2):
+        for cs in sets:
+            r = api.nu_batch_search([(lc.t, lc.y, lc.diag_var, lc.terms) for lc in cs], DS,
+                                    PERIODS, k=2, precision=precision, phase_step=dt)
+            runs.append({k: v.cpu().numpy() for k, v in r.items() if k != "status"})
+    for i in (0, 1):
+        for key in ("Q", "T0", "D_idx", "lnP", "depth", "sigma"):
+            assert np.array_equal(runs[i][key], runs[i + 2][key], equal_nan=True), key
+    assert not np.array_equal(runs[0]["Q"], runs[1]["Q"])
+    if precision == "fp64":
+        for i, cs in enumerate(sets):
+            for c, lc in enumerate(cs):
+                one = _single(lc, "fp64", dt)
+                np.testing.assert_allclose(runs[i]["Q"][c], one["Q"], rtol=1e-12, atol=0)
+
+
+def test_injection_workload_mixed_against_oracle():
+    """Mixed precision on the injection set-up (deep transits: many cells of
+    every warp survive the first pass in the same round, which exercises the
+    fold's queue flushing): every curve succeeds, two equal the FP64 oracle
+    within the mixed tolerances."""
+    w = synth.injection_4000(n_curves=48)
+    Ds = w.durations
+    periods = np.linspace(0.3, 3.0, 600)
+    dt = synth.CADENCE_DAYS
+    res = api.nu_batch_search([(lc.t, lc.y, lc.diag_var, lc.terms) for lc in w.curves], Ds,
+                              periods, k=2, precision="mixed", phase_step=dt)
+    assert res["status"] == [0] * len(w.curves)
+    assert torch.isfinite(res["Q"]).all()
+    for c in (5, 31):
+        lc = w.curves[c]
+        g = linear.linear_search(lc.t, lc.y, lc.diag_var, lc.terms, lc.X, lc.t, Ds)
+        ora = periodic.periodic_search(lc.t, g["depth"], g["var"], g["dlnl"], periods, dt)
+        gpu = {k: res[k][c].cpu().numpy() for k in ("Q", "T0", "D_idx", "depth", "sigma", "lnP")}
+        periodic_compare(gpu, ora, lc.t, g["depth"], g["var"], g["dlnl"], periods, dt, 1e-4,
+                         MIXED_SNR_ABS, periodic.fold_period, max_reeval=len(periods),
+                         q_abs=True)
+        print(f"injection mixed curve {c}:", periodic_compare.last)
