@@ -47,10 +47,12 @@ from paper_2402_06835_gb300 import synth  # noqa: E402
 METRIC = "linear-search (t0,D) fits/s + period trials/s, %HBM roofline, mixed vs FP64"
 MEASURED_FP64_TFLOPS = 1.197   # DFMA microbenchmark on this machine's GB300 (2 DFMA/clk/SM)
 N_SMSP = 152 * 4               # SM sub-partitions (one warp instruction issued per clock each)
-# Per launch of the FP64 fold on the headline workload, from a one-pass ncu
-# capture of the kernel as it stands (the launch list and counters are
-# summarised under profiles/): DRAM bytes read + written, warp instructions.
-FOLD_NCU = {"sector_19440": {"traffic": 27120384, "inst": 7895867159}}
+# Per launch of the fold (FP64 on the sector, mixed on the 16-duration sector),
+# from one-pass ncu captures of the kernels as they stand (the launch lists and
+# counters are summarised under profiles/): DRAM bytes read + written, warp
+# instructions.
+FOLD_NCU = {("sector_19440", "fp64"): {"traffic": 27120384, "inst": 7895867159},
+            ("sector_19440_16d", "mixed"): {"traffic": 33223680, "inst": 10819232577}}
 FLUSH_BYTES = 512 << 20        # > 129 MB L2
 ORACLE_TEMPLATES = 256         # bounded oracle sample per step (both CPU legs)
 ORACLE_PERIODS = 8
@@ -725,7 +727,7 @@ def main():
     launches = api.launch_count() - n0
     ms = max_over_ranks(float(stages.sum(axis=1).mean()), torch, dev)
     head = pipeline_entry(args.workload, pipe, stages, world,
-                          FOLD_NCU.get(args.workload) if args.precision == "fp64" else None,
+                          FOLD_NCU.get((args.workload, args.precision)),
                           clocks["sm_mhz"] if clocks else None)
     out = {"metric": METRIC, "value": weak_scaling_value(n_templates, world, ms),
            "unit": "(t0,D) fits/s", "n_gpus": world,

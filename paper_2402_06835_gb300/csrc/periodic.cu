@@ -2105,9 +2105,12 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
 #ifndef NU_SLOTS_MIN_BLOCKS
 #define NU_SLOTS_MIN_BLOCKS 4
 #endif
+#ifndef NU_SLOTS_CASC_MIN_BLOCKS
+#define NU_SLOTS_CASC_MIN_BLOCKS 4
+#endif
 
 template <int KC, int MAXT, bool CASC>
-__global__ void __launch_bounds__(MAXT, NU_SLOTS_MIN_BLOCKS * 256 / MAXT)
+__global__ void __launch_bounds__(MAXT, (CASC ? NU_SLOTS_CASC_MIN_BLOCKS : NU_SLOTS_MIN_BLOCKS) * 256 / MAXT)
 k_fold_slots(const Node4<float>* __restrict__ rec, const float* __restrict__ lgm,
              int64_t n_slots, int n_D, double dt, double t_ref, double t_last,
              const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
@@ -2135,7 +2138,8 @@ template <int KIND, int MAXT>
 struct BatchBlocks {
     static constexpr int value =
         KIND == 0 ? (MAXT <= 64 ? 10 : (MAXT <= 128 ? 5 : NU_SCREEN_MIN_BLOCKS))
-                  : (KIND >= 2 ? NU_SLOTS_MIN_BLOCKS * 256 / MAXT : 1);
+                  : (KIND == 2 ? NU_SLOTS_CASC_MIN_BLOCKS * 256 / MAXT
+                               : KIND == 3 ? NU_SLOTS_MIN_BLOCKS * 256 / MAXT : 1);
 };
 
 template <int KIND, int MAXT>
