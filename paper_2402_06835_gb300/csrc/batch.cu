@@ -269,12 +269,12 @@ extern "C" nu_status nu_batch_search(int n_lc, const int64_t* offsets_host,
     const size_t f_nodes = foff; foff += fbat.any_exact ? exact_layout(N, n_D, fp64).total : 0;
     const size_t f_buck = foff;  foff += al((size_t)(fbat.n_bucket_total + 1) * 4);
     const size_t f_rec = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(Node4<float>));
-    const size_t f_lgm = foff;   foff += al((size_t)(fbat.n_rec_total + 1) * sizeof(float));
+    const size_t f_lgm = foff;   foff += al((size_t)((fp64 ? 0 : fbat.n_gain_total) + 1) * sizeof(float));
     const size_t f_srec = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(ScreenRec));
     const size_t f_slot = foff;  foff += fp64 ? al((size_t)N * sizeof(int)) : 0;
     const size_t f_reg = foff;   foff += al((size_t)n_lc * 2 * sizeof(unsigned));
     const size_t f_lint = foff;  foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
-    const size_t f_lm3 = foff;   foff += al((size_t)(fbat.n_srec_total + 1) * sizeof(float));
+    const size_t f_lm3 = foff;   foff += al((size_t)((fp64 ? fbat.n_gain_total : 0) + 1) * sizeof(float));
     const size_t f_peak = foff;  foff += al((size_t)n_lc * sizeof(unsigned long long));
     const size_t f_ptab = foff;  foff += al((size_t)n_P * period_const_bytes());
     e = cudaMallocAsync((void**)&fold_mem, foff, st);

@@ -61,7 +61,23 @@ struct FoldSeg {
     int use_slots;
     int screen;         // FP64 path: FP32 screening allowed for this curve
     int64_t srec_off;   // FP64 path: first slot-indexed screening record
+    int64_t gain_off;   // first entry of the curve's grouped gain table (either path)
 };
+
+// Gain tables are grouped by duration: the gains of W consecutive durations
+// at one slot are adjacent, so that one vector load serves W cells of one
+// phase (their epochs are the same).  Per curve the table is [n_D / W groups
+// (rounded up)][n_slots][W] floats; columns past n_D hold 0.
+#ifndef NU_GAIN_W_MAX
+#define NU_GAIN_W_MAX 4
+#endif
+__host__ __device__ inline int gain_width(int n_D) {
+    return n_D >= 4 && NU_GAIN_W_MAX >= 4 ? 4 : (n_D >= 2 && NU_GAIN_W_MAX >= 2 ? 2 : 1);
+}
+__host__ __device__ inline int gain_cols(int n_D) {
+    const int W = gain_width(n_D);
+    return (n_D + W - 1) / W * W;
+}
 
 struct PeriodConst;
 size_t period_const_bytes();
@@ -71,12 +87,13 @@ struct FoldScratch {
     void* nodes;            // exact-path records (exact_layout of all samples)
     int* bucket;            // bucket tables
     Node4<float>* rec;      // mixed slot records
-    float* lgm;             // mixed: the larger gain of each slot and the next
+    float* lgm;             // mixed: the larger gain of each slot and the next (grouped)
     ScreenRec* srec;        // FP64 slot-indexed screening records
     int* slot_of;           // FP64: slot of every sample
     unsigned* reg;          // FP64: two words per curve (zeroed by the prep)
     float* lint;            // FP64: largest gain of the interval at each slot
-    float* lm3;             //       and its maximum over the slot and both neighbours
+    float* lm3;             //       and its maximum over the slot and both
+                            //       neighbours (grouped)
     unsigned long long* peak;  // FP64: per curve, the key of its largest gain
     PeriodConst* ptab;      // FP64: per period, its curve-independent constants
 };
@@ -85,6 +102,7 @@ struct FoldScratch {
 struct FoldBatch {
     std::vector<FoldSeg> segs;
     int64_t n_bucket_total = 0, n_rec_total = 0, n_srec_total = 0;
+    int64_t n_gain_total = 0;    // entries of the grouped gain tables (either path)
     bool any_slots = false, any_exact = false;
     bool slot_cascade = false;   // some curve's grid is large enough for the mixed cascade
 };

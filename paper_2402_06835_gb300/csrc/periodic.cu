@@ -740,7 +740,7 @@ struct ScreenGeom {
     int on;                            // screening allowed for this curve
     const unsigned long long* peak;    // key of the largest finite gain (k_gain_peak);
                                        // 0: none
-    const float* lm3;                  // rows of n_slots: k_lmax3 of the interval gains
+    const float* lm3;                  // grouped gain table (k_lmax3 of the interval gains)
 };
 
 // Node sigma of one (duration, epoch) in FP64 (NaN when invalid).
@@ -873,17 +873,64 @@ __global__ void k_screen(const T* __restrict__ depth, const T* __restrict__ var,
                    slot_of, vpair);
 }
 
-// lm3[x] = max(lint[x - 1], lint[x], lint[x + 1]) over the flat array: the
-// largest gain of an event whose walk position lies in slot x (its interval
-// starts at the epoch of slot x - 1, x or x + 1, see the gain bound).  A
-// neighbour in the next row only raises the bound.
-__global__ void k_lmax3(const float* __restrict__ lint, int64_t n, float* __restrict__ lm3) {
-    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (x >= n) return;
-    float m = lint[x];
-    if (x > 0) m = fmaxf(m, lint[x - 1]);
-    if (x + 1 < n) m = fmaxf(m, lint[x + 1]);
-    lm3[x] = m;
+// Entry o of a grouped gain table: the curve (segs: the batch's, else one
+// curve of n_slots1 slots), the source row's duration d and slot s.  Per
+// curve the table holds [groups][n_slots][W] entries from gain_off on; the
+// source rows are duration-major rows of n_slots from srec_off (FP64) or
+// rec_off (mixed).  Returns false for entries of no curve.
+struct GainSlot {
+    int64_t src_off, n_slots;
+    int d, s;
+};
+__device__ __forceinline__ bool gain_slot(const FoldSeg* __restrict__ segs, int n_seg,
+                                          int64_t n_slots1, int n_D, bool fp64, int64_t o,
+                                          GainSlot& gs) {
+    int64_t out_off = 0;
+    gs.src_off = 0;
+    gs.n_slots = n_slots1;
+    if (segs) {
+        // the last curve whose table starts at or before o (curves without a
+        // table take no entries and share their successor's offset)
+        int lo = 0, hi = n_seg;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (segs[mid].gain_off <= o) lo = mid; else hi = mid;
+        }
+        const FoldSeg& f = segs[lo];
+        if (!(fp64 ? f.screen : f.use_slots)) return false;
+        out_off = f.gain_off;
+        gs.src_off = fp64 ? f.srec_off : f.rec_off;
+        gs.n_slots = f.n_slots;
+    }
+    const int W = gain_width(n_D);
+    const int64_t local = o - out_off;
+    if (local < 0 || local >= gs.n_slots * gain_cols(n_D)) return false;
+    const int64_t g = local / (gs.n_slots * W);
+    const int64_t rem = local - g * gs.n_slots * W;
+    gs.s = (int)(rem / W);
+    gs.d = (int)(g * W + (rem - (int64_t)gs.s * W));
+    return true;
+}
+
+// Grouped gain table of the FP64 screen: the maximum of lint over slots
+// s - 1, s and s + 1 of the row: the largest gain of an event whose walk
+// position lies in slot s (its interval starts at the epoch of slot s - 1, s
+// or s + 1, see the gain bound).
+__global__ void k_lmax3(const float* __restrict__ lint, const FoldSeg* __restrict__ segs,
+                        int n_seg, int64_t n_slots1, int n_D, int64_t n_out,
+                        float* __restrict__ lm3) {
+    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= n_out) return;
+    GainSlot gs;
+    if (!gain_slot(segs, n_seg, n_slots1, n_D, true, o, gs)) return;
+    float m = 0.f;
+    if (gs.d < n_D) {
+        const float* r = lint + gs.src_off + (int64_t)gs.d * gs.n_slots;
+        m = r[gs.s];
+        if (gs.s > 0) m = fmaxf(m, r[gs.s - 1]);
+        if (gs.s + 1 < gs.n_slots) m = fmaxf(m, r[gs.s + 1]);
+    }
+    lm3[o] = m;
 }
 
 // Per-period constants of the screen.
@@ -916,9 +963,13 @@ __device__ __forceinline__ ScreenPeriod screen_period_curve(const FoldGeom& g,
     sp.on = delta < 1.6e10;                                  // below 2^-6 slot
     sp.delta = (unsigned long long)delta;
     sp.uend = sp.ulast + sp.delta;
-    // regular grid: every epoch within 2^-26 slot of its own slot
+    // regular grid: every epoch within 2^-10 slot of its own slot.  The error
+    // terms below grow with the largest offset; a phase step taken as the
+    // median spacing of FP64 times carries a relative rounding of about
+    // 1e-11, so on long curves (seven sectors: 1.2e-7 slot) the offsets are
+    // well above the rounding of one sector's times.
     const float off = sg.srec ? __uint_as_float(sg.reg[1]) : 1.f;
-    sp.slots = sg.srec && sg.reg[0] == 0u && off <= 1.4901161193847656e-08f;
+    sp.slots = sg.srec && sg.reg[0] == 0u && off <= 9.765625e-04f;
     double e_w;
     if (sp.slots) {
         // the weight is the fraction of the slot: position error, the
@@ -1147,87 +1198,26 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
 // The gain bound of a cell on a regular grid, from 4 bytes per epoch.  By the
 // bound above, ln P <= S_L + 1/2, and every event's gain is at most the
 // larger gain of its interval's two nodes.  The walk's position u of epoch k
-// lies within e_pos << 1 slot of the exact epoch, and on a regular grid every
-// epoch is within 2^-26 slot of its slot, so the exact interval starts at
+// lies within half a slot of the exact epoch, and on a regular grid every
+// epoch is within 2^-10 slot of its slot, so the exact interval starts at
 // the epoch of slot floor(u) - 1, floor(u) or floor(u) + 1: lm3 at floor(u)
 // bounds the event's gain (0 for a dropped epoch, +inf on an interval outside
 // the screen's error model).  Extra walk positions past t_last (u < uend)
 // only add terms >= 0.  The FP32 sum of K terms >= 0 is rounded up by
 // (K + 16) 2^-23 of itself, and 1e-6 covers the exact path's own rounding.
-// The walk is bound by the latency of its gathers, so its terms are loaded
-// four at a time before they are added (gain_ahead loads the first four; a
-// position past uend loads a clamped slot and is not added; ustep < 2^60
-// keeps u + 3 ustep from wrapping).  gain_sum returns the sum of the terms
-// and their number.  (Loading the next round's terms a round ahead was
-// slower: the registers it holds cost more than the latency it hides.)
-struct GainAhead {
-    float a, b, c, e;
-};
-__device__ __forceinline__ GainAhead gain_ahead(const float* __restrict__ lm, unsigned ns1,
-                                                unsigned long long u, unsigned long long ustep) {
-    const unsigned long long ua = u + ustep, ub = ua + ustep, uc = ub + ustep;
-    return GainAhead{lm[min((unsigned)(u >> 40), ns1)], lm[min((unsigned)(ua >> 40), ns1)],
-                     lm[min((unsigned)(ub >> 40), ns1)], lm[min((unsigned)(uc >> 40), ns1)]};
-}
-__device__ __forceinline__ float2 gain_sum(const GainAhead& ga, const float* __restrict__ lm,
-                                           unsigned ns1, unsigned long long u,
-                                           unsigned long long ustep, unsigned long long uend) {
-    float s0 = 0.f, s1 = 0.f, K = 0.f;
-    const unsigned long long u4 = 4ull * ustep;
-    if (u < uend) {
-        const unsigned long long ua = u + ustep, ub = ua + ustep, uc = ub + ustep;
-        s0 = ga.a;
-        K = 1.f;
-        if (ua < uend) {
-            s1 = ga.b;
-            K += 1.f;
-        }
-        if (ub < uend) {
-            s0 += ga.c;
-            K += 1.f;
-        }
-        if (uc < uend) {
-            s1 += ga.e;
-            K += 1.f;
-        }
-        u += u4;
-    }
-    for (; u < uend; u += u4) {
-        const unsigned long long ua = u + ustep, ub = ua + ustep, uc = ub + ustep;
-        const float a = lm[min((unsigned)(u >> 40), ns1)];
-        const float b = lm[min((unsigned)(ua >> 40), ns1)];
-        const float c = lm[min((unsigned)(ub >> 40), ns1)];
-        const float d = lm[min((unsigned)(uc >> 40), ns1)];
-        s0 += a;
-        K += 1.f;
-        if (ua < uend) {
-            s1 += b;
-            K += 1.f;
-        }
-        if (ub < uend) {
-            s0 += c;
-            K += 1.f;
-        }
-        if (uc < uend) {
-            s1 += d;
-            K += 1.f;
-        }
-    }
-    return make_float2(s0 + s1, K);
-}
-
-// 32-bit form of the gain walk (fewer instructions per epoch): positions in
-// units of 2^-F slot, started from the 64-bit position of a cell's first
-// epoch (truncated) and advanced by the rounded step, so that epoch k is at
-// most 1 + k/2 units from the 64-bit walk.  F is chosen per period so that
-// no position the walk loads (up to end + 11 steps: two cells walked
-// together, four epochs a round, one cell a round longer) exceeds 2^31, and the
-// walk is used only when that error stays below half a slot for every epoch
-// (the gain bound tolerates the exact interval starting one slot either side
-// of the walk's slot).  The end is widened by the same error, so every epoch
-// of the 64-bit walk is counted; positions past it add terms >= 0 (the walk
-// adds four terms at a time; a position past the row is clamped to the
-// padding slot zs, whose term is 0).
+//
+// The walk runs in 32-bit fixed point (few instructions per epoch):
+// positions in units of 2^-F slot, started from the 64-bit position of a
+// cell's first epoch (truncated) and advanced by the rounded step, so that
+// epoch k is at most 1 + k/2 units from the 64-bit walk.  F is chosen per
+// period so that no position the walk loads (up to end + 3 steps: four epochs
+// a round) exceeds 2^31 (the margin below allows twelve), and the walk is
+// used only when that error stays below half a slot for every epoch (the gain
+// bound tolerates the exact interval starting one slot either side of the
+// walk's slot).  The end is widened by the same error, so every epoch of the
+// 64-bit walk is counted; positions past it add terms >= 0 (the walk adds
+// four terms at a time; a position past the row is clamped to the padding
+// slot zs, whose term is 0).
 struct GainWalk32 {
     unsigned step, end;
     int shift;            // 40 - F
@@ -1253,62 +1243,83 @@ __device__ __forceinline__ GainWalk32 gain_walk32(unsigned long long ustep,
     w.ok = w.step > 0u;
     return w;
 }
-// Two cells of one period walked together (eight loads in flight): their
-// sums and counts.  A cell that is not valid (v = false) walks the other's
-// row and positions and adds nothing (its own row pointer may lie past the
-// table), so no position exceeds the other cell's last round by more than
-// one (the cells' epoch counts differ by at most one).
-__device__ __forceinline__ float4 gain_sum32x2(const float* __restrict__ l1,
-                                               const float* __restrict__ l2, unsigned zs,
-                                               unsigned u1, unsigned u2, bool v1, bool v2,
-                                               const GainWalk32& w) {
-    float a = 0.f, ka = 0.f, b = 0.f, kb = 0.f;
-    const unsigned st = w.step;
-    if (!v1) {
-        u1 = u2;
-        l1 = l2;
-    }
-    if (!v2) {
-        u2 = u1;
-        l2 = l1;
-    }
-    while ((v1 && u1 < w.end) || (v2 && u2 < w.end)) {
-        const float x0 = l1[min(u1 >> w.F, zs)];
-        const float x1 = l1[min((u1 + st) >> w.F, zs)];
-        const float x2 = l1[min((u1 + 2u * st) >> w.F, zs)];
-        const float x3 = l1[min((u1 + 3u * st) >> w.F, zs)];
-        const float y0 = l2[min(u2 >> w.F, zs)];
-        const float y1 = l2[min((u2 + st) >> w.F, zs)];
-        const float y2 = l2[min((u2 + 2u * st) >> w.F, zs)];
-        const float y3 = l2[min((u2 + 3u * st) >> w.F, zs)];
-        if (v1 && u1 < w.end) {
-            a += (x0 + x2) + (x1 + x3);
-            ka += 4.f;
-        }
-        if (v2 && u2 < w.end) {
-            b += (y0 + y2) + (y1 + y3);
-            kb += 4.f;
-        }
-        u1 += 4u * st;
-        u2 += 4u * st;
-    }
-    return make_float4(a, ka, b, kb);
-}
 
-__device__ __forceinline__ float2 gain_sum32(const float* __restrict__ lm, unsigned zs,
-                                             unsigned u, const GainWalk32& w) {
-    float s0 = 0.f, s1 = 0.f, K = 0.f;
+// The gain tables are grouped by duration (gain_width): the W cells of one
+// phase and W consecutive durations share their epochs, so a lane walks them
+// together with one W-wide load per epoch.  row points at the group's first
+// slot; the sums of the W columns go to s (the unused ones stay 0) and the
+// number of terms, the same for every column, is returned.
+template <int W>
+struct GainVec;
+template <>
+struct GainVec<1> {
+    typedef float T;
+    __device__ static __forceinline__ T zero() { return 0.f; }
+    __device__ static __forceinline__ void add(float4& s, T a, T b, T c, T e) {
+        s.x += (a + c) + (b + e);
+    }
+};
+template <>
+struct GainVec<2> {
+    typedef float2 T;
+    __device__ static __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    __device__ static __forceinline__ void add(float4& s, T a, T b, T c, T e) {
+        s.x += (a.x + c.x) + (b.x + e.x);
+        s.y += (a.y + c.y) + (b.y + e.y);
+    }
+};
+template <>
+struct GainVec<4> {
+    typedef float4 T;
+    __device__ static __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static __forceinline__ void add(float4& s, T a, T b, T c, T e) {
+        s.x += (a.x + c.x) + (b.x + e.x);
+        s.y += (a.y + c.y) + (b.y + e.y);
+        s.z += (a.z + c.z) + (b.z + e.z);
+        s.w += (a.w + c.w) + (b.w + e.w);
+    }
+};
+// (NU_GAIN_UNROLL4 epochs a round for 4-wide groups, four for the others)
+#ifndef NU_GAIN_UNROLL4
+#define NU_GAIN_UNROLL4 4
+#endif
+template <int W>
+__device__ __forceinline__ float gain_walk_w(const float* __restrict__ row, unsigned zs,
+                                             unsigned u, const GainWalk32& w, float4& s) {
+    typedef typename GainVec<W>::T V;
+    const V* __restrict__ r = reinterpret_cast<const V*>(row);
     const unsigned st = w.step;
+    float K = 0.f;
+    if (W == 4 && NU_GAIN_UNROLL4 == 2) {
+        // two epochs a round, the second clamped past the end (a zero term)
+        for (; u < w.end; u += 2u * st) {
+            const V a = r[min(u >> w.F, zs)];
+            const V b = r[min((u + st) >> w.F, zs)];
+            const V z = GainVec<W>::zero();
+            GainVec<W>::add(s, a, b, z, z);
+            K += 2.f;
+        }
+        return K;
+    }
     for (; u < w.end; u += 4u * st) {
-        const float a = lm[min(u >> w.F, zs)];
-        const float b = lm[min((u + st) >> w.F, zs)];
-        const float c = lm[min((u + 2u * st) >> w.F, zs)];
-        const float e = lm[min((u + 3u * st) >> w.F, zs)];
-        s0 += a + c;
-        s1 += b + e;
+        const V a = r[min(u >> w.F, zs)];
+        const V b = r[min((u + st) >> w.F, zs)];
+        const V c = r[min((u + 2u * st) >> w.F, zs)];
+        const V e = r[min((u + 3u * st) >> w.F, zs)];
+        GainVec<W>::add(s, a, b, c, e);
         K += 4.f;
     }
-    return make_float2(s0 + s1, K);
+    return K;
+}
+__device__ __forceinline__ float gain_walk(const float* __restrict__ row, int W, unsigned zs,
+                                           unsigned u, const GainWalk32& w, float4& s) {
+    s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (W == 4) return gain_walk_w<4>(row, zs, u, w, s);
+    if (W == 2) return gain_walk_w<2>(row, zs, u, w, s);
+    return gain_walk_w<1>(row, zs, u, w, s);
+}
+__device__ __forceinline__ float gain_col(const float4& s, int i) {
+    return i == 0 ? s.x : (i == 1 ? s.y : (i == 2 ? s.z : s.w));
 }
 
 // The mixed fold's cascade runs on periods with at least NU_CASCADE_ROUNDS
@@ -1486,7 +1497,7 @@ __device__ __forceinline__ void evaluate_queued_warp(const FoldGeom& g,
 // lower bound) are shared by the block through atomic maxima.
 // With TAB the period's curve-independent constants come from the table
 // entry pc (k_period_consts), else they are computed here.
-template <int MAXT = 256, bool TAB = false>
+template <int MAXT = 256, bool TAB = false, bool GROUP = true>
 __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const ScreenGeom& sg,
                                                   const Node8<double>* __restrict__ nodes,
                                                   int n_D, double P, int64_t p,
@@ -1499,8 +1510,8 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                                                   const PeriodConst* __restrict__ pc = nullptr) {
     __shared__ long long sh_qc[MAXT / 32][64];      // per-warp survivor queues
     __shared__ int sh_qd[MAXT / 32][64];
-    __shared__ long long sh_qa[MAXT / 32][64];      // per-warp cells for the full screen
-    __shared__ int sh_qad[MAXT / 32][64];
+    __shared__ long long sh_qa[MAXT / 32][160];     // per-warp cells for the full screen
+    __shared__ int sh_qad[MAXT / 32][160];
     __shared__ unsigned long long sh_sbest; // best ln P evaluated (max key)
     __shared__ unsigned sh_bfk;             // its FP32 lower bound (float key)
     __shared__ Best sh_tb[MAXT];            // each thread's best evaluated cell (kept
@@ -1522,7 +1533,6 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
                                   sig_out, lnp_out);
         return;
     }
-    const int64_t n_cells = n_phi * n_D;
     sh_tb[threadIdx.x] = Best{-INFINITY, LLONG_MAX, NAN, NAN};
     if (threadIdx.x == 0) {
         sh_gw = gain_walk32(sh_sp.ustep, sh_sp.uend);
@@ -1573,7 +1583,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
     // bounded from its gains alone (the gain bound, 4 bytes per epoch); the
     // cells that bound does not rule out are queued and screened in full 32
     // at a time, and the full screen's survivors are evaluated exactly.
-    const bool cascade = sp.slots && sg.lm3 != nullptr && sp.ustep < (1ull << 60);
+    const bool cascade = sp.slots && sg.lm3 != nullptr && sp.ustep < (1ull << 60) && sh_gw.ok;
     const unsigned ns1 = (unsigned)(sg.n_slots - 1);
     // append this lane's cell to a queue when keep (positions by ballot)
     auto push = [&](long long* qx, int* qy, int& n, bool keep, long long cl, int dl) {
@@ -1615,105 +1625,133 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
         __syncwarp();
         pop32(qc, qd, nq);
     };
-    // full screen of the first cnt entries of queue A (one per lane); the
-    // survivors join the survivor queue
-    auto screen_queued = [&](int cnt) {
+    // First-round seed: the warp evaluates its lane with the largest finite
+    // bound (all lanes over its epochs), unless that bound is already below
+    // the threshold (the cell cannot raise it).  A 1e-9 margin keeps the
+    // seeding cell itself above the threshold: it is evaluated again by the
+    // thread code.
+    auto seed_warp = [&](float ub, int dl, int64_t jl) {
+        float v = (ub < INFINITY) ? ub : -INFINITY;
+        int src = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float v2 = __shfl_xor_sync(FULL, v, o);
+            const int s2 = __shfl_xor_sync(FULL, src, o);
+            if (v2 > v || (v2 == v && s2 < src)) {
+                v = v2;
+                src = s2;
+            }
+        }
+        // (the threshold is broadcast so that the branch is warp-uniform)
+        const float thr = __shfl_sync(FULL, from_fkey(sh_bfk), 0);
+        if (v > -INFINITY && !(v < thr)) {
+            const int pd = __shfl_sync(FULL, dl, src);
+            const long long pj = __shfl_sync(FULL, (long long)jl, src);
+            const double lnp = exact_cell_warp(g, nodes + (int64_t)pd * g.n_t0, c, pj);
+            if (lane == 0 && lnp == lnp && lnp > -INFINITY) {
+                const double seed = lnp - 1e-9 * (1.0 + fabs(lnp));
+                atomicMax(&sh_sbest, max_key(seed));
+                atomicMax(&sh_bfk, fkey(__double2float_rd(seed)));
+            }
+            __syncwarp();
+        }
+    };
+    // Cells are taken W durations at a time (one gain group, one phase per
+    // lane; W = 1 without the cascade).  Without the cascade, the warp's
+    // first round and its direct rounds every cell goes on; otherwise those
+    // whose gain bound reaches the threshold.  Cells that go on are screened
+    // in full from queue A, 32 at a time (the warp's first such screen seeds
+    // the threshold), and the screen's survivors are evaluated exactly from
+    // the survivor queue.
+    bool seed = true;
+    // full screen of queue A's entries h .. h + cnt - 1 (one per lane)
+    auto screen_queued = [&](int h, int cnt) {
         float ub = -INFINITY;
         long long cl = 0;
         int dl = 0;
+        int64_t jl = 0;
         if (lane < cnt) {
-            cl = qa[lane];
-            dl = qad[lane];
-            const int64_t jl = cl - (int64_t)dl * n_phi;
+            cl = qa[h + lane];
+            dl = qad[h + lane];
+            jl = cl - (int64_t)dl * n_phi;
             ub = screen_cell(g, sg, nodes + (int64_t)dl * g.n_t0, sg.rec + (int64_t)dl * g.n_t0,
-                             sg.srec + (int64_t)dl * sg.n_slots, sp, c, jl,
+                             sg.srec ? sg.srec + (int64_t)dl * sg.n_slots : nullptr, sp, c, jl,
                              (unsigned long long)jl * sp.uph, from_fkey(sh_bfk));
         }
+        if (seed) {
+            seed = false;
+            seed_warp(ub, dl, jl);
+        }
+        // a cell without events (bound -inf) is never the argmax; NaN
+        // survives.  The FP32 threshold is at most every evaluated ln P.
         push(qc, qd, nq, lane < cnt && !(ub == -INFINITY) && !(ub < from_fkey(sh_bfk)), cl,
              dl);
     };
-    int d = (int)(threadIdx.x / n_phi);
-    int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
+    // (GROUP = false compiles the one-duration walk alone: the wider walks'
+    // registers would otherwise weigh on the grids of one duration)
+    const int W = cascade && GROUP ? gain_width(n_D) : 1;
+    const int64_t n_gc = (int64_t)((n_D + W - 1) / W) * n_phi;
+    const int dr = NU_GAIN_DIRECT_ROUNDS / W > 0 ? NU_GAIN_DIRECT_ROUNDS / W : 1;
+    const unsigned zs = ns1 - 1u;
+    int gi = (int)(threadIdx.x / n_phi);
+    int64_t j = (int64_t)threadIdx.x - (int64_t)gi * n_phi;
     bool first = true;
-    int direct = 0;                          // rounds left to screen in full directly
-    for (int64_t base = (int64_t)wid * 32; base < n_cells; base += blockDim.x,
-                 j += blockDim.x) {
+    int direct = 0;                          // rounds left without the gain bound
+    for (int64_t base = (int64_t)wid * 32; base < n_gc; base += blockDim.x, j += blockDim.x) {
         while (j >= n_phi) {
             j -= n_phi;
-            ++d;
+            ++gi;
         }
-        const int64_t cell = base + lane;
-        float ub = -INFINITY;
-        if (!first && cascade && direct == 0) {
-            float gb = -INFINITY;
-            if (cell < n_cells) {
-                // ln P <= S_L + 1/2, with the gain bound's margins (one cell
-                // per lane: walking two at once spills in this kernel)
-                const float* lr = sg.lm3 + (int64_t)d * sg.n_slots;
-                const unsigned long long u0 = (unsigned long long)j * sp.uph;
-                const float2 sk =
-                    sh_gw.ok ? gain_sum32(lr, ns1 - 1u, (unsigned)(u0 >> sh_gw.shift), sh_gw)
-                             : gain_sum(gain_ahead(lr, ns1, u0, sp.ustep), lr, ns1, u0,
-                                        sp.ustep, sp.uend);
-                gb = sk.x * fmaf(sk.y + 16.f, 1.1920929e-7f, 1.f) + 0.5f + 1e-6f;
-            }
-            const bool pass = cell < n_cells && !(gb < from_fkey(sh_bfk));
-            // where the gain bound rules out almost nothing (cells of many
-            // epochs, whose bound needs the depth terms) the warp screens
-            // its next rounds in full directly
-            if (__popc(__ballot_sync(FULL, pass)) >= NU_GAIN_PASS_MAX) direct = NU_GAIN_DIRECT_ROUNDS;
-            push(qa, qad, na, pass, cell, d);
-            if (na >= 32) {
-                screen_queued(32);
-                pop32(qa, qad, na);
-            }
+        const int d0 = gi * W;
+        const int nv = base + lane < n_gc ? min(W, n_D - d0) : 0;   // this lane's cells
+        unsigned pass = 0u;
+        if (!cascade || first || direct > 0) {
+            if (cascade && !first) --direct;
+            first = false;
+            pass = (1u << nv) - 1u;
         } else {
-            if (direct > 0) --direct;
-            if (cell < n_cells)
-                ub = screen_cell(g, sg, nodes + (int64_t)d * g.n_t0,
-                                 sg.rec + (int64_t)d * g.n_t0,
-                                 sg.srec ? sg.srec + (int64_t)d * sg.n_slots : nullptr, sp, c,
-                                 j, (unsigned long long)j * sp.uph, from_fkey(sh_bfk));
-            if (first) {
-                // seed: the warp evaluates its lane with the largest finite
-                // bound, unless that bound is already below the threshold
-                // (the cell cannot raise it)
-                first = false;
-                float v = (ub < INFINITY) ? ub : -INFINITY;
-                int src = lane;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float v2 = __shfl_xor_sync(FULL, v, o);
-                    const int s2 = __shfl_xor_sync(FULL, src, o);
-                    if (v2 > v || (v2 == v && s2 < src)) {
-                        v = v2;
-                        src = s2;
-                    }
-                }
-                // (the threshold is broadcast so that the branch is warp-uniform)
-                const float thr = __shfl_sync(FULL, from_fkey(sh_bfk), 0);
-                if (v > -INFINITY && !(v < thr)) {
-                    const int pd = __shfl_sync(FULL, d, src);
-                    const long long pj = __shfl_sync(FULL, (long long)j, src);
-                    const double lnp = exact_cell_warp(g, nodes + (int64_t)pd * g.n_t0, c, pj);
-                    if (lane == 0 && lnp == lnp && lnp > -INFINITY) {
-                        // a 1e-9 margin: the seeding cell itself stays above
-                        // the threshold and is evaluated again by the thread
-                        // code
-                        const double seed = lnp - 1e-9 * (1.0 + fabs(lnp));
-                        atomicMax(&sh_sbest, max_key(seed));
-                        atomicMax(&sh_bfk, fkey(__double2float_rd(seed)));
-                    }
-                    __syncwarp();
-                }
+            if (nv > 0) {
+                float4 sk;
+                const float K = gain_walk(sg.lm3 + (int64_t)gi * sg.n_slots * W, W, zs,
+                                          (unsigned)(((unsigned long long)j * sp.uph) >>
+                                                     sh_gw.shift),
+                                          sh_gw, sk);
+                const float f = fmaf(K + 16.f, 1.1920929e-7f, 1.f);
+                const float thr = from_fkey(sh_bfk);
+                for (int i = 0; i < nv; ++i)
+                    if (!(gain_col(sk, i) * f + 0.5f + 1e-6f < thr)) pass |= 1u << i;
             }
-            // a cell without events (bound -inf) is never the argmax; NaN
-            // survives.  The FP32 threshold is at most every evaluated ln P.
-            push(qc, qd, nq, cell < n_cells && !(ub == -INFINITY) && !(ub < from_fkey(sh_bfk)),
-                 cell, d);
+            // where the gain bound rules out almost nothing (cells of many
+            // epochs, whose bound needs the depth terms) the warp screens its
+            // next rounds in full directly
+            const int np = __reduce_add_sync(FULL, (unsigned)__popc(pass));
+            const int nt = __reduce_add_sync(FULL, (unsigned)nv);
+            if (nt > 0 && np * 32 >= NU_GAIN_PASS_MAX * nt) direct = dr;
         }
-        if (nq >= 32) evaluate32();
+        for (int i = 0; i < W; ++i)
+            push(qa, qad, na, (pass >> i) & 1u, (long long)(d0 + i) * n_phi + j, d0 + i);
+        // queue A holds at most 31 + 32 W entries here
+        int h = 0;
+        for (; na - h >= 32; h += 32) {
+            screen_queued(h, 32);
+            if (nq >= 32) evaluate32();
+        }
+        if (h > 0) {
+            na -= h;
+            long long c2 = 0;
+            int d2 = 0;
+            if (lane < na) {
+                c2 = qa[h + lane];
+                d2 = qad[h + lane];
+            }
+            __syncwarp();
+            if (lane < na) {
+                qa[lane] = c2;
+                qad[lane] = d2;
+            }
+            __syncwarp();
+        }
     }
-    if (na > 0) screen_queued(na);
+    if (na > 0) screen_queued(0, na);
     if (nq >= 32) evaluate32();
     if (coop) {
         for (int q = 0; q < nq; ++q)
@@ -1737,12 +1775,19 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
 #endif
 
 // 256-thread blocks: 3 per SM (about 80 registers); 64-thread blocks:
-// NU_SCREEN_SMALL_BLOCKS per SM (the shared arrays are sized for 2 warps).
+// NU_SCREEN_SMALL_BLOCKS per SM (the shared arrays are sized for 2 warps),
+// NU_SCREEN_GROUP_BLOCKS with the grouped gain walk, whose registers need 80
+// (C2 fold 8.52 ms at 12 blocks, 8.74 ms at 14 with 72 registers).
 #ifndef NU_SCREEN_SMALL_BLOCKS
 #define NU_SCREEN_SMALL_BLOCKS 14
 #endif
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT, MAXT <= 64 ? NU_SCREEN_SMALL_BLOCKS : NU_SCREEN_MIN_BLOCKS)
+#ifndef NU_SCREEN_GROUP_BLOCKS
+#define NU_SCREEN_GROUP_BLOCKS 12
+#endif
+template <int MAXT, bool GROUP>
+__global__ void __launch_bounds__(MAXT, MAXT <= 64 ? (GROUP ? NU_SCREEN_GROUP_BLOCKS
+                                                            : NU_SCREEN_SMALL_BLOCKS)
+                                                   : NU_SCREEN_MIN_BLOCKS)
 k_fold_screened(FoldGeom g, ScreenGeom sg, const Node8<double>* __restrict__ nodes, int n_D,
                 const double* __restrict__ periods, int64_t n_P, double* __restrict__ Q_out,
                 double* __restrict__ T0_out, int* __restrict__ Didx_out,
@@ -1750,8 +1795,8 @@ k_fold_screened(FoldGeom g, ScreenGeom sg, const Node8<double>* __restrict__ nod
                 double* __restrict__ lnp_out) {
     const int64_t p = blockIdx.x;
     if (p >= n_P) return;
-    fold_screened_one<MAXT>(g, sg, nodes, n_D, periods[p], p, Q_out, T0_out, Didx_out,
-                            dep_out, sig_out, lnp_out);
+    fold_screened_one<MAXT, false, GROUP>(g, sg, nodes, n_D, periods[p], p, Q_out, T0_out,
+                                          Didx_out, dep_out, sig_out, lnp_out);
 }
 
 // ---------------------------------------- slot path (mixed, regular grids)
@@ -1828,21 +1873,24 @@ struct SCell {
     int d, kmax, pad;
 };
 
-// Gain table of the slot path: lgm[x] = the larger gain of slots x and x + 1
-// of a duration row when both records are valid (0 otherwise, a dropped
-// event), rounded up: the interpolated gain of an event in slot x is at most
-// that (to the FP32 rounding of the interpolation).  Every row ends with
-// padding slots (NaN), so a pair never reaches into the next row.
-__global__ void k_slot_gain(const Node4<float>* __restrict__ rec, int64_t n,
-                            float* __restrict__ lgm) {
-    const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (x >= n) return;
+// Gain table of the slot path: the larger gain of slots s and s + 1 of a
+// duration row when both records are valid (0 otherwise, a dropped event),
+// rounded up: the interpolated gain of an event in slot s is at most that (to
+// the FP32 rounding of the interpolation).  Grouped by duration (gain_slot).
+__global__ void k_slot_gain(const Node4<float>* __restrict__ rec,
+                            const FoldSeg* __restrict__ segs, int n_seg, int64_t n_slots1,
+                            int n_D, int64_t n_out, float* __restrict__ lgm) {
+    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= n_out) return;
+    GainSlot gs;
+    if (!gain_slot(segs, n_seg, n_slots1, n_D, false, o, gs)) return;
     float m = 0.f;
-    if (x + 1 < n) {
-        const Node4<float> a = rec[x], b = rec[x + 1];
+    if (gs.d < n_D && gs.s + 1 < gs.n_slots) {
+        const Node4<float>* r = rec + gs.src_off + (int64_t)gs.d * gs.n_slots;
+        const Node4<float> a = r[gs.s], b = r[gs.s + 1];
         if (!isnan(a.s) && !isnan(b.s)) m = __fmul_ru(fmaxf(0.f, fmaxf(a.l, b.l)), 1.0000005f);
     }
-    lgm[x] = m;
+    lgm[o] = m;
 }
 
 // Epochs walk the slot grid in 24.40 fixed point: u = (T - t_ref)/dt =
@@ -1854,14 +1902,17 @@ __global__ void k_slot_gain(const Node4<float>* __restrict__ rec, int64_t n,
 // Cascade per warp (no block barriers until the final argmax):
 //   1. gain bound of each cell from lgm (4 bytes per epoch): with the bound
 //      of cannot_win, ln P <= S_L + 1/2, and S_L is at most the sum of the
-//      epochs' lgm; cells below the threshold stop here;
+//      epochs' lgm; cells below the threshold stop here.  A lane bounds the
+//      cells of one phase and one group of durations (gain_width) in one
+//      walk;
 //   2. queued, 32 at a time: the first pass (FP32 sums) and the bound of
 //      cannot_win_f;
 //   3. queued, 32 at a time: the second pass, whose ln P raises the threshold.
-// A warp's first round runs the first pass directly.  Warps whose gain
-// bounds pass almost every cell (cells of many epochs) skip step 1 for their
-// next rounds, and periods with few cells per warp (short curves) skip it
-// throughout: their threshold does not rise in time for the bound to pay.
+// A warp's first round skips step 1.  Warps whose gain bounds pass almost
+// every cell (cells of many epochs) skip it for their next rounds, and
+// periods with few cells per warp (short curves) skip the cascade
+// throughout, running the first pass directly: their threshold does not rise
+// in time for the bound to pay.
 // CASC = false compiles the fold without the cascade (its registers spill
 // the plain path's), for grids too small for it (the host decides).
 // (Evaluating the best-bounded cell of the first round at once, as a seed
@@ -1878,8 +1929,8 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                                                double* __restrict__ sig_out,
                                                double* __restrict__ lnp_out) {
     __shared__ SCell sh_q[MAXT / 32][64];
-    __shared__ long long sh_qa[MAXT / 32][64];     // cells for the first pass
-    __shared__ int sh_qad[MAXT / 32][64];
+    __shared__ long long sh_qa[MAXT / 32][CASC ? 160 : 1];   // cells for the first pass
+    __shared__ int sh_qad[MAXT / 32][CASC ? 160 : 1];
     __shared__ unsigned int sh_best;
     FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
     if (bad_period(P, gg)) {
@@ -1912,9 +1963,9 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     // them from wrapping (ulast < 2^62).  The cascade needs the threshold to
     // rise before it pays: periods of fewer than NU_CASCADE_ROUNDS rounds of
     // cells per warp (short light curves) run the first pass on every cell.
-    const bool cascade = CASC && lgm != nullptr && ustep < (1ull << 60) &&
-                         n_cells >= (int64_t)NU_CASCADE_ROUNDS * blockDim.x;
     const GainWalk32 gw = gain_walk32(ustep, ulast + 1);
+    const bool cascade = CASC && lgm != nullptr && ustep < (1ull << 60) && gw.ok &&
+                         n_cells >= (int64_t)NU_CASCADE_ROUNDS * blockDim.x;
     auto best_now = [&]() {
         const unsigned int kb = sh_best;
         return fmaxf(bl, kb ? __uint_as_float((kb >> 31) ? (kb & 0x7fffffffu) : ~kb)
@@ -1980,113 +2031,113 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
         __syncwarp();
     };
     // first passes of the first cnt entries of queue A, one per lane; the
-    // survivors join queue B, which is flushed at once when it holds 32
-    // (queue B never holds more than 63 entries: a round can flush queue A
-    // twice)
-    auto flush_a = [&](int cnt) {
+    // survivors join queue B, which is flushed at once when it holds 32 (so
+    // it never holds more than 63 entries)
+    auto flush_a = [&](int h, int cnt) {
         SCell e;
         float ub;
         bool keep = false;
         if (lane < cnt) {
-            const long long cl = qa[lane];
-            const int dl = qad[lane];
+            const long long cl = qa[h + lane];
+            const int dl = qad[h + lane];
             keep = pass1(dl, cl - (int64_t)dl * n_phi, cl, e, &ub);
         }
         push_b(keep, e);
         if (nq >= 32) flush_b();
-        __syncwarp();
-        na -= cnt;
-        long long c2 = 0;
-        int d2 = 0;
-        if (lane < na) {
-            c2 = qa[cnt + lane];
-            d2 = qad[cnt + lane];
-        }
-        __syncwarp();
-        if (lane < na) {
-            qa[lane] = c2;
-            qad[lane] = d2;
-        }
-        __syncwarp();
     };
-    int d = (int)(threadIdx.x / n_phi);
-    int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
-    bool first = true;
-    int direct = 0;                          // rounds left without the gain bound
-    for (int64_t base = (int64_t)wid * 32; base < n_cells; base += blockDim.x,
-                 j += blockDim.x) {
-        while (j >= n_phi) {
-            j -= n_phi;
-            ++d;
-        }
-        const int64_t cell = base + lane;
-        if (!first && cascade && direct == 0) {
-            // two rounds at once where the 32-bit walk applies (epochs with
-            // u <= ulast): this round's cells and the next round's
-            const bool pair = gw.ok != 0;
-            int64_t j2 = j + (pair ? (int64_t)blockDim.x : 0);
-            int d2 = d;
-            while (j2 >= n_phi) {
-                j2 -= n_phi;
-                ++d2;
+    if (cascade) {
+        // cells W durations at a time (one gain group, one phase per lane),
+        // as in the FP64 fold: the first and the direct rounds pass every
+        // cell to queue A, the others those whose gain bound reaches the
+        // threshold (with the margins of cannot_win_f on top of the rounding
+        // of the sum)
+        const int W = gain_width(n_D);
+        const int64_t n_gc = (int64_t)((n_D + W - 1) / W) * n_phi;
+        const int dr = NU_GAIN_DIRECT_ROUNDS / W > 0 ? NU_GAIN_DIRECT_ROUNDS / W : 1;
+        const unsigned zs = ns1 - 1u;
+        int gi = (int)(threadIdx.x / n_phi);
+        int64_t j = (int64_t)threadIdx.x - (int64_t)gi * n_phi;
+        bool first = true;
+        int direct = 0;                      // rounds left without the gain bound
+        for (int64_t base = (int64_t)wid * 32; base < n_gc; base += blockDim.x,
+                     j += blockDim.x) {
+            while (j >= n_phi) {
+                j -= n_phi;
+                ++gi;
             }
-            const int64_t cell2 = cell + blockDim.x;
-            float2 sk = make_float2(0.f, 0.f), sk2 = make_float2(0.f, 0.f);
-            if (pair) {
-                const bool v1 = cell < n_cells, v2 = cell2 < n_cells;
-                if (v1 || v2) {
-                    const float4 s4 = gain_sum32x2(
-                        lgm + (int64_t)d * n_slots, lgm + (int64_t)d2 * n_slots, ns1 - 1u,
-                        (unsigned)(((unsigned long long)j * uph) >> gw.shift),
-                        (unsigned)(((unsigned long long)j2 * uph) >> gw.shift), v1, v2, gw);
-                    sk = make_float2(s4.x, s4.y);
-                    sk2 = make_float2(s4.z, s4.w);
+            const int d0 = gi * W;
+            const int nv = base + lane < n_gc ? min(W, n_D - d0) : 0;   // this lane's cells
+            unsigned pass = 0u;
+            if (first || direct > 0) {
+                if (!first) --direct;
+                first = false;
+                pass = (1u << nv) - 1u;
+            } else {
+                if (nv > 0) {
+                    float4 sk;
+                    const float K = gain_walk(lgm + (int64_t)gi * n_slots * W, W, zs,
+                                              (unsigned)(((unsigned long long)j * uph) >> gw.shift),
+                                              gw, sk);
+                    const float f = fmaf(K + 16.f, 1.1920929e-7f, 1.f);
+                    const float thr = best_now();
+                    if (K > 0.f)
+                        for (int i = 0; i < nv; ++i) {
+                            const float gb = gain_col(sk, i) * f + 0.5f;
+                            if (!(gb + 1e-4f * fmaxf(1.f, fabsf(gb)) < thr)) pass |= 1u << i;
+                        }
                 }
-            } else if (cell < n_cells) {
-                const float* lr = lgm + (int64_t)d * n_slots;
-                const unsigned long long u0 = (unsigned long long)j * uph;
-                sk = gain_sum(gain_ahead(lr, ns1, u0, ustep), lr, ns1, u0, ustep, ulast + 1);
+                const int np = __reduce_add_sync(FULL, (unsigned)__popc(pass));
+                const int nt = __reduce_add_sync(FULL, (unsigned)nv);
+                if (nt > 0 && np * 32 >= NU_GAIN_PASS_MAX * nt) direct = dr;
             }
-            // the margins of cannot_win_f on top of the rounding of the sum
-            const float thr = best_now();
-            auto passes = [&](const float2& v) {
-                const float gb = v.x * fmaf(v.y + 16.f, 1.1920929e-7f, 1.f) + 0.5f;
-                return v.y > 0.f && !(gb + 1e-4f * fmaxf(1.f, fabsf(gb)) < thr);
-            };
-            const bool pass = cell < n_cells && passes(sk);
-            const bool pass2 = pair && cell2 < n_cells && passes(sk2);
-            if (__popc(__ballot_sync(FULL, pass)) >= NU_GAIN_PASS_MAX)
-                direct = NU_GAIN_DIRECT_ROUNDS;
-            auto push_a = [&](bool keep, long long cl, int dl) {
+            for (int i = 0; i < W; ++i) {
+                const bool keep = (pass >> i) & 1u;
                 const unsigned m = __ballot_sync(FULL, keep);
                 if (keep) {
                     const int pos = na + __popc(m & ((1u << lane) - 1u));
-                    qa[pos] = cl;
-                    qad[pos] = dl;
+                    qa[pos] = (long long)(d0 + i) * n_phi + j;
+                    qad[pos] = d0 + i;
                 }
                 na += __popc(m);
                 __syncwarp();
-                if (na >= 32) flush_a(32);
-            };
-            push_a(pass, cell, d);
-            if (pair) {
-                push_a(pass2, cell2, d2);
-                // the loop's increment moves past the second round
-                base += blockDim.x;
-                j = j2;
-                d = d2;
             }
-        } else {
-            if (direct > 0) --direct;
+            // queue A holds at most 31 + 32 W entries here
+            int h = 0;
+            for (; na - h >= 32; h += 32) flush_a(h, 32);
+            if (h > 0) {
+                na -= h;
+                long long c2 = 0;
+                int d2 = 0;
+                if (lane < na) {
+                    c2 = qa[h + lane];
+                    d2 = qad[h + lane];
+                }
+                __syncwarp();
+                if (lane < na) {
+                    qa[lane] = c2;
+                    qad[lane] = d2;
+                }
+                __syncwarp();
+            }
+        }
+        if (na > 0) flush_a(0, na);
+    } else {
+        int d = (int)(threadIdx.x / n_phi);
+        int64_t j = (int64_t)threadIdx.x - (int64_t)d * n_phi;
+        for (int64_t base = (int64_t)wid * 32; base < n_cells; base += blockDim.x,
+                     j += blockDim.x) {
+            while (j >= n_phi) {
+                j -= n_phi;
+                ++d;
+            }
+            const int64_t cell = base + lane;
             SCell e;
             float ub = -INFINITY;
             const bool keep = cell < n_cells && pass1(d, j, cell, e, &ub);
-            first = false;
             push_b(keep, e);
+            if (nq >= 32) flush_b();
         }
-        if (nq >= 32) flush_b();
     }
-    if (na > 0) flush_a(na);
     if (nq >= 32) flush_b();
     if (lane < nq) pass2(q[lane]);
     Best best{-INFINITY, LLONG_MAX, NAN, NAN};
@@ -2137,7 +2188,7 @@ k_fold_slots(const Node4<float>* __restrict__ rec, const float* __restrict__ lgm
 template <int KIND, int MAXT>
 struct BatchBlocks {
     static constexpr int value =
-        KIND == 0 ? (MAXT <= 64 ? 10 : (MAXT <= 128 ? 5 : NU_SCREEN_MIN_BLOCKS))
+        KIND == 0 || KIND == 4 ? (MAXT <= 64 ? 10 : (MAXT <= 128 ? 5 : NU_SCREEN_MIN_BLOCKS))
                   : (KIND == 2 ? NU_SLOTS_CASC_MIN_BLOCKS * 256 / MAXT
                                : KIND == 3 ? NU_SLOTS_MIN_BLOCKS * 256 / MAXT : 1);
 };
@@ -2168,21 +2219,21 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
         const int g = (int)(item / (unsigned long long)n_P);
         const int64_t p = (int64_t)(item % (unsigned long long)n_P);
         const FoldSeg fs = segs[g];
-        if ((KIND >= 2) != (fs.use_slots != 0)) continue;
+        if ((KIND == 2 || KIND == 3) != (fs.use_slots != 0)) continue;
         const int64_t o = (int64_t)g * n_P + p;
-        if (KIND >= 2) {
-            fold_slots_one<8, MAXT, KIND == 2>(rec + fs.rec_off, lgm + fs.rec_off, fs.n_slots, n_D, dt,
+        if (KIND == 2 || KIND == 3) {
+            fold_slots_one<8, MAXT, KIND == 2>(rec + fs.rec_off, lgm + fs.gain_off, fs.n_slots, n_D, dt,
                                     fs.t_ref, fs.t_last,
                               periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
                               lnp_out);
         } else {
             FoldGeom gg{t + fs.s_off, fs.n_t0, fs.t_ref, fs.t_last, dt, 1.0 / dt,
                         gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
-            if (KIND == 0) {
+            if (KIND == 0 || KIND == 4) {
                 const ScreenGeom sg{screen + fs.s_off * n_D, vpair + fs.s_off,
                                     srec + fs.srec_off, fs.n_slots,
-                                    reg + 2 * g, fs.screen, peak + g, lm3 + fs.srec_off};
-                fold_screened_one<MAXT, true>(gg, sg,
+                                    reg + 2 * g, fs.screen, peak + g, lm3 + fs.gain_off};
+                fold_screened_one<MAXT, true, KIND == 4>(gg, sg,
                                               (const Node8<double>*)nodes + fs.s_off * n_D, n_D,
                                               periods[p], o, Q_out, T0_out, Didx_out, dep_out,
                                               sig_out, lnp_out, ptab + p);
@@ -2347,6 +2398,8 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
         f.screen = (fp64 && gap_factor < 2.0 && span < 8.0e6) ? 1 : 0;
         f.srec_off = fb.n_srec_total;
         fb.n_srec_total += f.screen ? f.n_slots * n_D : 0;
+        f.gain_off = fb.n_gain_total;
+        fb.n_gain_total += (fp64 ? f.screen : f.use_slots) ? f.n_slots * gain_cols(n_D) : 0;
         f.bucket_off = fb.n_bucket_total;
         fb.n_bucket_total += f.use_slots ? 0 : f.n_bucket;
         f.rec_off = fb.n_rec_total;
@@ -2394,8 +2447,8 @@ cudaError_t launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev,
                 n_seg, s_off_dev, n_D, gap_factor * dt, dt,
                 (ScreenRec*)((char*)fs.nodes + L.off_screen),
                 (ulonglong2*)((char*)fs.nodes + L.off_vpos), fs.srec, fs.lint, fs.slot_of);
-            k_lmax3<<<div_up(fb.n_srec_total + 1, 256), 256, 0, st>>>(fs.lint, fb.n_srec_total,
-                                                                     fs.lm3);
+            k_lmax3<<<div_up(fb.n_gain_total + 1, 256), 256, 0, st>>>(
+                fs.lint, segs_dev, n_seg, 0, n_D, fb.n_gain_total, fs.lm3);
             launched += 2;
             e = cudaMemsetAsync(fs.peak, 0, (size_t)n_seg * sizeof(unsigned long long), st);
             if (e != cudaSuccess) {
@@ -2420,8 +2473,8 @@ cudaError_t launch_fold_prep(const FoldBatch& fb, const FoldSeg* segs_dev,
         k_slot_fill_batch<<<div_up(ngrid, 256), 256, 0, st>>>(
             (const float*)depth, (const float*)var, (const float*)gain, t, segs_dev, n_seg,
             s_off_dev, n_D, 1.0 / dt, fs.rec);
-        k_slot_gain<<<div_up(fb.n_rec_total + 1, 256), 256, 0, st>>>(fs.rec, fb.n_rec_total,
-                                                                     fs.lgm);
+        k_slot_gain<<<div_up(fb.n_gain_total + 1, 256), 256, 0, st>>>(
+            fs.rec, segs_dev, n_seg, 0, n_D, fb.n_gain_total, fs.lgm);
         launched += 3;
     }
     *n_launched = launched;
@@ -2459,7 +2512,10 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
         if (fp64) {
             k_period_consts<<<div_up(n_P, 256), 256, 0, st>>>(periods, n_P, dt, fs.ptab);
             ++launched;
-            NU_FB_SIZE(0, counter);
+            if (gain_width(n_D) > 1)
+                NU_FB_SIZE(4, counter);
+            else
+                NU_FB_SIZE(0, counter);
         } else
             NU_FB_SIZE(1, counter);
         ++launched;
@@ -2507,8 +2563,8 @@ static SingleLayout single_layout(int64_t n_t0, int n_D, int64_t n_bucket, bool 
     L.srec = L.rec + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(Node4<float>)));
     L.lint = L.srec + (fp64 ? al((size_t)n_slots * n_D * sizeof(ScreenRec)) : 0);
     L.lm3 = L.lint + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
-    L.lgm = L.lm3 + (fp64 ? al((size_t)n_slots * n_D * sizeof(float)) : 0);
-    L.total = L.lgm + (fp64 ? 0 : al((size_t)n_slots * n_D * sizeof(float)));
+    L.lgm = L.lm3 + (fp64 ? al((size_t)n_slots * gain_cols(n_D) * sizeof(float)) : 0);
+    L.total = L.lgm + (fp64 ? 0 : al((size_t)n_slots * gain_cols(n_D) * sizeof(float)));
     return L;
 }
 
@@ -2557,7 +2613,8 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
             (const float*)depth_dev, (const float*)var_dev, (const float*)dlnl_dev, slot_of,
             n_t0, n_D, n_slots, rec);
         float* lgm = (float*)(scratch + L.lgm);
-        k_slot_gain<<<div_up(nrec, 256), 256, 0, st>>>(rec, nrec, lgm);
+        const int64_t nlg = n_slots * gain_cols(n_D);
+        k_slot_gain<<<div_up(nlg, 256), 256, 0, st>>>(rec, nullptr, 0, n_slots, n_D, nlg, lgm);
         // the cascade's instance where a period can hold enough cells for it
         const bool casc = nrec >= (int64_t)NU_CASCADE_ROUNDS * 128;
 #define NU_FS(MAXT_, CASC_)                                                                \
@@ -2606,21 +2663,31 @@ static nu_status single_fold(const char* who, char* scratch, const SingleLayout&
                 (const double*)depth_dev, (const double*)var_dev, (const double*)dlnl_dev,
                 t0s_dev, n_t0, n_D, g.gap_max, phase_step, nrec, srec, lint, n_slots, slot_of,
                 vpair);
-            k_lmax3<<<div_up(n_slots * n_D, 256), 256, 0, st>>>(lint, n_slots * n_D, lm3);
+            const int64_t nlm = n_slots * gain_cols(n_D);
+            k_lmax3<<<div_up(nlm, 256), 256, 0, st>>>(lint, nullptr, 0, n_slots, n_D, nlm, lm3);
             k_gain_peak<<<dim3(1, (unsigned)std::min<int64_t>(div_up(ngrid, 2048), 608)), 256, 0,
                           st>>>((const double*)dlnl_dev, nullptr, n_t0, n_D, peak);
             // One block per period.  With many periods, 2-warp blocks: 14 fit
             // on an SM (28 warps) and each period has 2 warps to seed; with
             // few, 8-warp blocks keep the GPU full (C2, 20 000 periods: 16.5 ms
             // at 256 threads, 14.0 at 128 (7 per SM), 13.6 at 64).
+            // (the grouped gain walk where the durations form groups)
+#define NU_FSC(MAXT_)                                                                      \
+    do {                                                                                   \
+        if (gain_width(n_D) > 1)                                                           \
+            k_fold_screened<MAXT_, true><<<(unsigned)n_P, MAXT_, 0, st>>>(                 \
+                g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,  \
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);                         \
+        else                                                                               \
+            k_fold_screened<MAXT_, false><<<(unsigned)n_P, MAXT_, 0, st>>>(                \
+                g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,  \
+                D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);                         \
+    } while (0)
             if (n_P >= 8192)
-                k_fold_screened<64><<<(unsigned)n_P, 64, 0, st>>>(
-                    g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
-                    D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+                NU_FSC(64);
             else
-                k_fold_screened<256><<<(unsigned)n_P, 256, 0, st>>>(
-                    g, sg, (const Node8<double>*)nodes, n_D, periods_dev, n_P, Q_dev, T0_dev,
-                    D_idx_dev, depth_out_dev, sigma_out_dev, lnP_dev);
+                NU_FSC(256);
+#undef NU_FSC
             launched += 8;
         } else {
             k_nodes<float><<<div_up(ngrid, 256), 256, 0, st>>>(
