@@ -725,7 +725,9 @@ k_fold_exact(FoldGeom g, const Node8<T>* __restrict__ nodes, int n_D,
 //
 // Error term.  An FP32 event value x (depth, sigma, gain) differs from the
 // FP64 one by at most cv (|x_i| + |x_{i+1}|) (node and slope rounding,
-// weight rounding and position error, the FMA), with |x_i| + |x_{i+1}| <=
+// weight rounding and position error, the FMA; an event in the band of an
+// epoch takes its exact interval and an FP32 weight within 5u of the exact
+// one), with |x_i| + |x_{i+1}| <=
 // 2|x| + |x_{i+1} - x_i| accumulated per cell.  Intervals whose end sigmas
 // differ by more than a factor 3 (or outside the other limits of the
 // screening record) are not screened, so |ds|/s <= 2 and the
@@ -948,6 +950,7 @@ struct ScreenPeriod {
     unsigned long long uph, ustep, ulast, delta;
     unsigned long long uend;   // epochs walk while u < uend = ulast + delta
     float inv_ustep32;
+    float wscale;   // 2^22 / dt (FP32): weight of an event in the band of an epoch
     float cv;       // error coefficient of an FP32 event value
     float dw;       // half-width of the band around an epoch, as an interval weight
     float hw;       // 1/2 - dw: an event is in a band when |w - 1/2| > hw
@@ -991,8 +994,18 @@ __device__ __forceinline__ ScreenPeriod screen_period_curve(const FoldGeom& g,
         sp.dw = (float)(4.04 * delta / SCALE + 2.0e-6);
         e_w = 4.0 * e_pos / SCALE + 9.5367431640625e-07;
     }
-    sp.cv = (float)(8.0 * 5.9604644775390625e-08 + 2.0 * e_w);
+    // (the weight of an event in the band of an epoch, computed in FP32 by
+    // screen_exact_event, is within 5u of the exact one: 3u more than the
+    // smallest e_w)
+    sp.cv = (float)(8.0 * 5.9604644775390625e-08 + 2.0 * (e_w + 3.0 * 5.9604644775390625e-08));
+    // on a regular grid an event within one fraction unit of an epoch's slot
+    // may take the epoch's values: off by at most ws times a slope, and for
+    // sigma ws times 2 sigma (adjacent sigmas within a factor 3)
+    if (sp.slots)
+        sp.cv = fmaxf(sp.cv, (float)(2.02 * (1.1920928955078125e-07 + e_pos / SCALE + (double)off) +
+                                     8.0 * 5.9604644775390625e-08));
     sp.hw = 0.5f - sp.dw;
+    sp.wscale = (float)(4194304.0 * g.inv_dt);
     return sp;
 }
 
@@ -1006,6 +1019,7 @@ __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const S
     sp.slots = false;
     sp.uph = sp.ustep = sp.ulast = sp.delta = sp.uend = 0;
     sp.inv_ustep32 = 0.f;
+    sp.wscale = 0.f;
     sp.cv = 0.f;
     sp.dw = 0.f;
     sp.hw = 0.5f;
@@ -1027,6 +1041,7 @@ __device__ __forceinline__ ScreenPeriod screen_period(const FoldGeom& g, const S
     sp.slots = false;
     sp.uph = sp.ustep = sp.ulast = sp.delta = sp.uend = 0;
     sp.inv_ustep32 = 0.f;
+    sp.wscale = 0.f;
     sp.cv = 0.f;
     sp.dw = 0.f;
     sp.hw = 0.5f;
@@ -1092,34 +1107,37 @@ struct ScreenAcc {
     }
 };
 
-// The event at epoch k computed as the exact path does (FP64 epoch, interval
-// and values), rounded to FP32 for the screen.  Returns 0 when the epoch is
-// dropped, 1 for an event, 2 when its interval is outside the error model.
+// The event of epoch k whose walk position lies in the band of an epoch
+// (or of t_last): T and its interval exactly as the exact path computes
+// them (FP64 epoch, comparisons of the doubles' integer keys), then the
+// weight (T - t_i)/gap in FP32 from the interval's screening record (within
+// 5u of the exact path's weight, which the error coefficient covers) and the
+// FP32 values as for any other event.  Returns 0 when there is no event, 1
+// when the event was added, 2 when its interval is outside the error model.
 __device__ __forceinline__ int screen_exact_event(const FoldGeom& g,
-                                                  const Node8<double>* __restrict__ nd,
                                                   const ScreenRec* __restrict__ rd,
                                                   const CellCtx& c, double phi, int64_t k,
-                                                  unsigned long long u, ScreenAcc& acc) {
+                                                  unsigned long long u, float wscale,
+                                                  ScreenAcc& acc) {
     const double Tk = epoch_time(g, c, phi, (double)k);
     const long long kT = okey(Tk);
     if (kT > c.klast) return 0;                 // after the last epoch
     const int64_t i = bracket_from(g, kT, guess_at(g, u));
-    const Node8<double> a = nd[i];
-    const double w = (Tk - g.t0s[i]) * a.ig;
-    const double s = fma(w, a.ds, a.s);
-    if (nan64(s)) return 0;
-    if (rd[i].flags) return 2;
-    acc.add((float)fma(w, a.dd, a.d), (float)s, (float)fma(w, a.dl, a.l), (float)a.dd,
-            (float)a.dl);
+    const ScreenRec r = rd[i];
+    if (r.flags) return 2;
+    // wsc = 2^-22 dt/gap: (T - t_i) 2^22/dt wsc = (T - t_i)/gap
+    const float w = (float)(Tk - g.t0s[i]) * wscale * r.wsc;
+    const float s = fmaf(w, r.ds, r.s);
+    if (isnan(s)) return 0;                     // the interval has no event
+    acc.add(fmaf(w, r.dd, r.d), s, fmaf(w, r.dl, r.l), r.dd, r.dl);
     return 1;
 }
 
-// Upper bound on ln P of cell (j, duration rows nd / rd / rs) whose first
+// Upper bound on ln P of cell (j, duration rows rd / rs) whose first
 // epoch is at u0 (see above): -inf when the cell has no event, +inf when an
 // event falls on an interval outside the screen's error model; any value
 // below bf when the cell is already known not to reach bf.
 __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom& sg,
-                                             const Node8<double>* __restrict__ nd,
                                              const ScreenRec* __restrict__ rd,
                                              const ScreenRec* __restrict__ rs,
                                              const ScreenPeriod& sp, const CellCtx& c,
@@ -1140,7 +1158,7 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
             have_phi = true;
         }
         const int64_t k = (int64_t)((u - u0) / sp.ustep);
-        return screen_exact_event(g, nd, rd, c, phi, k, u, acc) != 2;
+        return screen_exact_event(g, rd, c, phi, k, u, sp.wscale, acc) != 2;
     };
     if (sp.slots) {
         // regular grid: the interval is the slot's, the weight its fraction
@@ -1150,7 +1168,26 @@ __device__ __forceinline__ float screen_cell(const FoldGeom& g, const ScreenGeom
             // fraction of the slot: its top 23 bits as the mantissa of a float in [1, 2)
             const float w =
                 __uint_as_float(0x3f800000u | (unsigned)((u >> 17) & 0x7fffffu)) - 1.0f;
-            if (fabsf(w - 0.5f) > sp.hw) return exact();
+            if (fabsf(w - 0.5f) > sp.hw) {
+                // in the band of an epoch.  A position within one unit of the
+                // fraction of the epoch's slot m (every event of a period of
+                // whole slots) takes the epoch's values when both intervals
+                // at m are screened: the event lies on one of them, within
+                // ws = 2^-23 + e_pos + off of m, so its values are the epoch's
+                // within ws times either slope (the error coefficient covers
+                // it, with the larger slope as the event's).  Otherwise the
+                // exact event.
+                if (w != 0.f && w < 0.99999988f) return exact();
+                const unsigned sl = slot(u);
+                const unsigned m = w < 0.5f ? sl : sl + 1u;
+                if (m == 0u || m >= ns1) return exact();
+                const ScreenRec L = m == sl ? rs[m - 1u] : r;
+                const ScreenRec R = m == sl ? r : rs[m];
+                if (!(L.s < INFINITY) || !(R.s < INFINITY)) return exact();
+                acc.add(R.d, R.s, R.l, fmaxf(fabsf(L.dd), fabsf(R.dd)),
+                        fmaxf(fabsf(L.dl), fabsf(R.dl)));
+                return true;
+            }
             const float s = fmaf(w, r.ds, r.s);
             if (!(s < INFINITY)) return s != s;   // NaN: no event; +inf: not screened
             acc.add(fmaf(w, r.dd, r.d), s, fmaf(w, r.dl, r.l), r.dd, r.dl);
@@ -1683,7 +1720,7 @@ __device__ __forceinline__ void fold_screened_one(const FoldGeom& g, const Scree
             cl = qa[h + lane];
             dl = qad[h + lane];
             jl = cl - (int64_t)dl * n_phi;
-            ub = screen_cell(g, sg, nodes + (int64_t)dl * g.n_t0, sg.rec + (int64_t)dl * g.n_t0,
+            ub = screen_cell(g, sg, sg.rec + (int64_t)dl * g.n_t0,
                              sg.srec ? sg.srec + (int64_t)dl * sg.n_slots : nullptr, sp, c, jl,
                              (unsigned long long)jl * sp.uph, from_fkey(sh_bfk));
         }

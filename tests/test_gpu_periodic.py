@@ -161,16 +161,20 @@ def test_fold_invalid_periods_are_nan():
         assert np.isfinite(gpu["Q"][[0, 4]]).all()
 
 
+@pytest.mark.parametrize("drift", [0.0, 3e-10])
 @pytest.mark.parametrize("offset", [0.0, 2000.0])
 @pytest.mark.parametrize("regular", [True, False])
-def test_fold_fp64_screen_hard_cases(offset, regular):
+def test_fold_fp64_screen_hard_cases(offset, regular, drift):
     """FP64 fold on grids built to stress the FP32 screen of the exact path:
     periods that are whole multiples of the step (epochs land on samples and
     on the edges of gaps and NaN holes), epochs far from zero, regular
     epochs (slot-indexed screen) or irregular ones with near-coincident pairs
     (position search), neighbours whose variances differ by orders of
     magnitude, and gains consistent with the depths (strong pruning) next to
-    unrelated ones.  Every period is compared."""
+    unrelated ones.  With drift the phase step differs from the cadence by
+    that fraction, so the samples sit up to 5e-7 step off the phase grid (as
+    a median spacing of FP64 times puts them on long curves).  Every period
+    is compared."""
     rng = np.random.default_rng(41)
     dt = synth.CADENCE_DAYS
     base = np.concatenate([np.arange(600), np.arange(640, 1300), np.arange(1302, 1500)])
@@ -190,12 +194,13 @@ def test_fold_fp64_screen_hard_cases(offset, regular):
     g = dict(depth=depth, var=var, dlnl=dlnl)
     periods = np.concatenate([np.arange(37, 400, 3) * dt,
                               np.linspace(0.05, 1.2, 150), [1.9, 2.05]])
-    ora = periodic.periodic_search(t0s, depth, var, dlnl, periods, dt)
-    gpu = _gpu_fold(t0s, np.ones(4), g, periods, "fp64", phase_step=dt)
-    wl, wq, differ = periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, dt,
+    step = dt * (1.0 + drift)
+    ora = periodic.periodic_search(t0s, depth, var, dlnl, periods, step)
+    gpu = _gpu_fold(t0s, np.ones(4), g, periods, "fp64", phase_step=step)
+    wl, wq, differ = periodic_compare(gpu, ora, t0s, depth, var, dlnl, periods, step,
                                       FP64_TOL, FP64_TOL, periodic.fold_period)
-    print(f"fp64 screen hard cases offset={offset} regular={regular}: lnP err {wl:.2e}, "
-          f"Q err {wq:.2e}, ties {differ}")
+    print(f"fp64 screen hard cases offset={offset} regular={regular} drift={drift}: "
+          f"lnP err {wl:.2e}, Q err {wq:.2e}, ties {differ}")
 
 
 def test_fold_fp64_peak_seed_edges():
