@@ -1365,6 +1365,35 @@ __device__ __forceinline__ float gain_walk(const float* __restrict__ row, int W,
     if (W == 2) return gain_walk_w<2>(row, zs, u, w, s);
     return gain_walk_w<1>(row, zs, u, w, s);
 }
+// The same walk on the 64-bit positions (2^-40 slot) that define the mixed
+// fold's events: each epoch's slot is exactly its event's, so the table needs
+// no neighbours.  Positions past uend add terms >= 0 (clamped to zs);
+// ustep < 2^60 and u < 2^62 keep u + 3 ustep from wrapping.
+template <int W>
+__device__ __forceinline__ float gain_walk64_w(const float* __restrict__ row, unsigned zs,
+                                               unsigned long long u, unsigned long long ustep,
+                                               unsigned long long uend, float4& s) {
+    typedef typename GainVec<W>::T V;
+    const V* __restrict__ r = reinterpret_cast<const V*>(row);
+    float K = 0.f;
+    for (; u < uend; u += 4ull * ustep) {
+        const V a = r[min((unsigned)(u >> 40), zs)];
+        const V b = r[min((unsigned)((u + ustep) >> 40), zs)];
+        const V c = r[min((unsigned)((u + 2ull * ustep) >> 40), zs)];
+        const V e = r[min((unsigned)((u + 3ull * ustep) >> 40), zs)];
+        GainVec<W>::add(s, a, b, c, e);
+        K += 4.f;
+    }
+    return K;
+}
+__device__ __forceinline__ float gain_walk64(const float* __restrict__ row, int W, unsigned zs,
+                                             unsigned long long u, unsigned long long ustep,
+                                             unsigned long long uend, float4& s) {
+    s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (W == 4) return gain_walk64_w<4>(row, zs, u, ustep, uend, s);
+    if (W == 2) return gain_walk64_w<2>(row, zs, u, ustep, uend, s);
+    return gain_walk64_w<1>(row, zs, u, ustep, uend, s);
+}
 __device__ __forceinline__ float gain_col(const float4& s, int i) {
     return i == 0 ? s.x : (i == 1 ? s.y : (i == 2 ? s.z : s.w));
 }
@@ -1920,10 +1949,13 @@ struct SCell {
     int d, kmax, pad;
 };
 
-// Gain table of the slot path: the larger gain of slots s and s + 1 of a
-// duration row when both records are valid (0 otherwise, a dropped event),
-// rounded up: the interpolated gain of an event in slot s is at most that (to
-// the FP32 rounding of the interpolation).  Grouped by duration (gain_slot).
+// Gain table of the slot path.  An event at walk position u interpolates the
+// records of slots floor(u) and floor(u) + 1, so its gain is at most the
+// pair gain of floor(u): the larger gain of the two records when both are
+// valid (0 otherwise, a dropped event), rounded up (to cover the FP32
+// rounding of the interpolation).  The gain walk reads it at the 64-bit
+// positions that define the events (gain_walk64).  Grouped by duration
+// (gain_slot).
 __global__ void k_slot_gain(const Node4<float>* __restrict__ rec,
                             const FoldSeg* __restrict__ segs, int n_seg, int64_t n_slots1,
                             int n_D, int64_t n_out, float* __restrict__ lgm) {
@@ -2010,8 +2042,7 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     // them from wrapping (ulast < 2^62).  The cascade needs the threshold to
     // rise before it pays: periods of fewer than NU_CASCADE_ROUNDS rounds of
     // cells per warp (short light curves) run the first pass on every cell.
-    const GainWalk32 gw = gain_walk32(ustep, ulast + 1);
-    const bool cascade = CASC && lgm != nullptr && ustep < (1ull << 60) && gw.ok &&
+    const bool cascade = CASC && lgm != nullptr && ustep < (1ull << 60) &&
                          n_cells >= (int64_t)NU_CASCADE_ROUNDS * blockDim.x;
     auto best_now = [&]() {
         const unsigned int kb = sh_best;
@@ -2122,9 +2153,9 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
             } else {
                 if (nv > 0) {
                     float4 sk;
-                    const float K = gain_walk(lgm + (int64_t)gi * n_slots * W, W, zs,
-                                              (unsigned)(((unsigned long long)j * uph) >> gw.shift),
-                                              gw, sk);
+                    const float K = gain_walk64(lgm + (int64_t)gi * n_slots * W, W, zs,
+                                                (unsigned long long)j * uph, ustep, ulast + 1,
+                                                sk);
                     const float f = fmaf(K + 16.f, 1.1920929e-7f, 1.f);
                     const float thr = best_now();
                     if (K > 0.f)
