@@ -62,6 +62,7 @@ struct FoldSeg {
     int screen;         // FP64 path: FP32 screening allowed for this curve
     int64_t srec_off;   // FP64 path: first slot-indexed screening record
     int64_t gain_off;   // first entry of the curve's grouped gain table (either path)
+    unsigned long long ulast;   // slot path: the last epoch's position, 24.40 slots
 };
 
 // Gain tables are grouped by duration: the gains of W consecutive durations

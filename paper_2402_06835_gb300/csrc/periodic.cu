@@ -267,7 +267,7 @@ __device__ __forceinline__ bool cannot_win_f(float s_l, float s_inv, float s_d, 
 
 __device__ __forceinline__ bool bad_period(double P, const FoldGeom& g) {
     // a period must be finite, > 0 and give at most 1e9 epochs and phases
-    return !(P > 0.0) || !isfinite(P) || (g.t_last - g.t_ref) / P > 1.0e9 ||
+    return !(P > 0.0) || !isfinite(P) || g.t_last - g.t_ref > 1.0e9 * P ||
            P / g.dt > 1.0e9;
 }
 
@@ -531,7 +531,43 @@ __global__ void k_period_consts(const double* __restrict__ periods, int64_t n_P,
     out[i] = period_const(P, dt, 1.0 / dt);
 }
 
-size_t period_const_bytes() { return sizeof(PeriodConst); }
+// Per-period constants of the slot path: phases, and the epoch and phase
+// steps in 24.40 fixed point.  The single-curve fold computes them per block;
+// the batch reads them from a table filled by the same function
+// (k_slot_periods), so both fold a curve identically.  bad marks a period
+// that is not folded for any curve (the curve's own limit, a span of more
+// than 1e9 periods, is tested per curve).
+struct SlotPeriod {
+    int64_t n_phi;
+    unsigned long long ustep, uph;
+    int bad;
+};
+// The position of a curve's last epoch (< 2^62 by the host's span check).
+__host__ __device__ inline unsigned long long slot_ulast(double t_ref, double t_last, double dt) {
+    return (unsigned long long)llrint((t_last - t_ref) / dt * 1099511627776.0);
+}
+__device__ __forceinline__ SlotPeriod slot_period(double P, double dt) {
+    SlotPeriod sp{1, 0ull, 0ull, 1};
+    if (!(P > 0.0) || !isfinite(P) || P / dt > 1.0e9) return sp;
+    const double SCALE = 1099511627776.0;                      // 2^40
+    const double R = P / dt;                                   // slots per period
+    sp.n_phi = (int64_t)ceil(R);
+    sp.ustep = R * SCALE < 4.0e18 ? (unsigned long long)llrint(R * SCALE)
+                                  : 4000000000000000000ull;
+    // phase j starts at j * (R / n_phi) slots; per-cell work stays integer
+    sp.uph = (unsigned long long)llrint(R / (double)sp.n_phi * SCALE);
+    sp.bad = 0;
+    return sp;
+}
+__global__ void k_slot_periods(const double* __restrict__ periods, int64_t n_P, double dt,
+                               SlotPeriod* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_P) out[i] = slot_period(periods[i], dt);
+}
+
+size_t period_const_bytes() {
+    return sizeof(PeriodConst) > sizeof(SlotPeriod) ? sizeof(PeriodConst) : sizeof(SlotPeriod);
+}
 
 __device__ __forceinline__ double cell_phi(const CellCtx& c, int64_t j) {
     const double jd = (double)j;
@@ -2001,6 +2037,8 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
                                                const float* __restrict__ lgm,
                                                int64_t n_slots, int n_D, double dt,
                                                double t_ref, double t_last, double P, int64_t p,
+                                               const SlotPeriod* __restrict__ spp,
+                                               unsigned long long ulast_in,
                                                double* __restrict__ Q_out,
                                                double* __restrict__ T0_out,
                                                int* __restrict__ Didx_out,
@@ -2011,22 +2049,18 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     __shared__ long long sh_qa[MAXT / 32][CASC ? 160 : 1];   // cells for the first pass
     __shared__ int sh_qad[MAXT / 32][CASC ? 160 : 1];
     __shared__ unsigned int sh_best;
-    FoldGeom gg{nullptr, 0, t_ref, t_last, dt, 1.0 / dt, 0.0, nullptr, 0};
-    if (bad_period(P, gg)) {
+    // the period's constants from the batch's table (spp) or computed here;
+    // the curve's last epoch position from the batch (ulast_in) or here
+    const SlotPeriod spc = spp ? *spp : slot_period(P, dt);
+    if (spc.bad || t_last - t_ref > 1.0e9 * P) {
         if (threadIdx.x == 0) write_bad(p, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
         return;
     }
     const unsigned FULL = 0xffffffffu;
-    const int64_t n_phi = (int64_t)ceil(P / dt);
+    const int64_t n_phi = spc.n_phi;
     const int64_t n_cells = n_phi * n_D;
-    const double R = P / dt;                                   // slots per period
-    const double SCALE = 1099511627776.0;                      // 2^40
-    const double ulast_d = (t_last - t_ref) / dt * SCALE;       // < 2^62 (host check)
-    const unsigned long long ulast = (unsigned long long)llrint(ulast_d);
-    const unsigned long long ustep =
-        R * SCALE < 4.0e18 ? (unsigned long long)llrint(R * SCALE) : 4000000000000000000ull;
-    // phase j starts at j * (R / n_phi) slots; per-cell work stays integer
-    const unsigned long long uph = (unsigned long long)llrint(R / (double)n_phi * SCALE);
+    const unsigned long long ulast = spp ? ulast_in : slot_ulast(t_ref, t_last, dt);
+    const unsigned long long ustep = spc.ustep, uph = spc.uph;
     float bl = -INFINITY, bD = NAN, bs2 = NAN;
     long long bc = LLONG_MAX;
     if (threadIdx.x == 0) sh_best = 0u;     // key below every finite float
@@ -2218,11 +2252,42 @@ __device__ __forceinline__ void fold_slots_one(const Node4<float>* __restrict__ 
     }
     if (nq >= 32) flush_b();
     if (lane < nq) pass2(q[lane]);
-    Best best{-INFINITY, LLONG_MAX, NAN, NAN};
-    if (bc != LLONG_MAX) best = Best{(double)bl, bc, (double)bD, sqrt((double)bs2)};
-    const Best b = block_argmax<MAXT>(best);
-    if (threadIdx.x == 0)
+    // block argmax in FP32 (larger ln P, ties to the smaller cell): warp
+    // shuffles, then the warps' winners through shared memory; FP64 only for
+    // the one result (the FP64 pipe is 1/64 of the FP32 one on this part)
+    for (int o = 16; o > 0; o >>= 1) {
+        const float l2 = __shfl_xor_sync(FULL, bl, o);
+        const long long c2 = __shfl_xor_sync(FULL, bc, o);
+        const float D2 = __shfl_xor_sync(FULL, bD, o);
+        const float s2 = __shfl_xor_sync(FULL, bs2, o);
+        if (l2 > bl || (l2 == bl && c2 < bc)) {
+            bl = l2;
+            bc = c2;
+            bD = D2;
+            bs2 = s2;
+        }
+    }
+    __shared__ float sh_bl[MAXT / 32], sh_bD[MAXT / 32], sh_bs2[MAXT / 32];
+    __shared__ long long sh_bc[MAXT / 32];
+    if (lane == 0) {
+        sh_bl[wid] = bl;
+        sh_bc[wid] = bc;
+        sh_bD[wid] = bD;
+        sh_bs2[wid] = bs2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sh_bl[w] > bl || (sh_bl[w] == bl && sh_bc[w] < bc)) {
+                bl = sh_bl[w];
+                bc = sh_bc[w];
+                bD = sh_bD[w];
+                bs2 = sh_bs2[w];
+            }
+        Best b{-INFINITY, LLONG_MAX, NAN, NAN};
+        if (bc != LLONG_MAX) b = Best{(double)bl, bc, (double)bD, sqrt((double)bs2)};
         write_best(b, p, n_phi, t_ref, P, Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
+    }
 }
 
 #ifndef NU_SLOTS_SMALL
@@ -2249,6 +2314,7 @@ k_fold_slots(const Node4<float>* __restrict__ rec, const float* __restrict__ lgm
     if ((int64_t)blockIdx.x >= n_P) return;
     const int64_t p = period_slot(blockIdx.x, periods, n_P);
     fold_slots_one<KC, MAXT, CASC>(rec, lgm, n_slots, n_D, dt, t_ref, t_last, periods[p], p,
+                                   nullptr, 0ull,
                                    Q_out, T0_out, Didx_out, dep_out, sig_out, lnp_out);
 }
 
@@ -2300,10 +2366,11 @@ k_fold_batch(const FoldSeg* __restrict__ segs, int n_seg, const double* __restri
         if ((KIND == 2 || KIND == 3) != (fs.use_slots != 0)) continue;
         const int64_t o = (int64_t)g * n_P + p;
         if (KIND == 2 || KIND == 3) {
-            fold_slots_one<8, MAXT, KIND == 2>(rec + fs.rec_off, lgm + fs.gain_off, fs.n_slots, n_D, dt,
-                                    fs.t_ref, fs.t_last,
-                              periods[p], o, Q_out, T0_out, Didx_out, dep_out, sig_out,
-                              lnp_out);
+            // (the slot path's period table shares the FP64 path's buffer)
+            fold_slots_one<8, MAXT, KIND == 2>(
+                rec + fs.rec_off, lgm + fs.gain_off, fs.n_slots, n_D, dt, fs.t_ref, fs.t_last,
+                periods[p], o, reinterpret_cast<const SlotPeriod*>(ptab) + p, fs.ulast, Q_out,
+                T0_out, Didx_out, dep_out, sig_out, lnp_out);
         } else {
             FoldGeom gg{t + fs.s_off, fs.n_t0, fs.t_ref, fs.t_last, dt, 1.0 / dt,
                         gap_factor * dt, bucket + fs.bucket_off, fs.n_bucket};
@@ -2468,6 +2535,7 @@ void plan_fold_batch(const std::vector<int64_t>& s_off, const std::vector<double
         f.n_t0 = s_off[g + 1] - s_off[g];
         f.t_ref = t_first[g];
         f.t_last = t_last[g];
+        f.ulast = slot_ulast(f.t_ref, f.t_last, dt);
         const double span = (t_last[g] - t_first[g]) / dt;
         f.n_bucket = (int64_t)span + 2;
         f.n_slots = f.n_bucket + 2;
@@ -2599,6 +2667,9 @@ int launch_fold_batch(const FoldBatch& fb, const FoldSeg* segs_dev, int n_seg,
         ++launched;
     }
     if (fb.any_slots) {
+        k_slot_periods<<<div_up(n_P, 256), 256, 0, st>>>(periods, n_P, dt,
+                                                         reinterpret_cast<SlotPeriod*>(fs.ptab));
+        ++launched;
         if (fb.slot_cascade)
             NU_FB_SIZE(2, counter + 1);
         else
