@@ -51,8 +51,8 @@ N_SMSP = 152 * 4               # SM sub-partitions (one warp instruction issued 
 # from one-pass ncu captures of the kernels as they stand (the launch lists and
 # counters are summarised under profiles/): DRAM bytes read + written, warp
 # instructions.
-FOLD_NCU = {("sector_19440", "fp64"): {"traffic": 20871936, "inst": 6202021918},
-            ("sector_19440_16d", "mixed"): {"traffic": 7300736, "inst": 7650747144}}
+FOLD_NCU = {("sector_19440", "fp64"): {"traffic": 20915456, "inst": 6200356940},
+            ("sector_19440_16d", "mixed"): {"traffic": 7206912, "inst": 7679427940}}
 FLUSH_BYTES = 512 << 20        # > 129 MB L2
 ORACLE_TEMPLATES = 256         # bounded oracle sample per step (both CPU legs)
 ORACLE_PERIODS = 8
