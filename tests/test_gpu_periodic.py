@@ -161,6 +161,35 @@ def test_fold_invalid_periods_are_nan():
         assert np.isfinite(gpu["Q"][[0, 4]]).all()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fold_period_order_does_not_change_results(precision):
+    """The folds take a descending period grid from its far end (short periods
+    first); every period's outputs are the same in any order of the grid:
+    ascending, descending, shuffled, and with NaN entries at either end."""
+    rng = np.random.default_rng(5)
+    dt = synth.CADENCE_DAYS
+    t0s = np.concatenate([np.arange(900), np.arange(960, 1700)]) * dt
+    n = len(t0s)
+    var = rng.uniform(1e-8, 5e-8, (3, n))
+    depth = rng.normal(0, 1.5e-4, (3, n))
+    depth[:, 400:406] += 1.5e-3
+    g = dict(depth=depth, var=var, dlnl=depth ** 2 / (2 * var))
+    if precision == "mixed":
+        g = {k: a.astype(np.float32).astype(np.float64) for k, a in g.items()}
+    P = np.linspace(0.04, 1.5, 700)
+    ref = _gpu_fold(t0s, np.ones(3), g, P, precision, phase_step=dt)
+    perm = rng.permutation(len(P))
+    for order in (np.arange(len(P))[::-1], perm):
+        out = _gpu_fold(t0s, np.ones(3), g, P[order], precision, phase_step=dt)
+        for k in ref:
+            np.testing.assert_array_equal(out[k], ref[k][order], err_msg=k)
+    Pn = np.concatenate([[np.nan], P[::-1], [np.nan]])
+    out = _gpu_fold(t0s, np.ones(3), g, Pn, precision, phase_step=dt)
+    assert np.isnan(out["Q"][[0, -1]]).all()
+    for k in ref:
+        np.testing.assert_array_equal(out[k][1:-1], ref[k][::-1], err_msg=k)
+
+
 @pytest.mark.parametrize("drift", [0.0, 3e-10])
 @pytest.mark.parametrize("offset", [0.0, 2000.0])
 @pytest.mark.parametrize("regular", [True, False])
