@@ -458,7 +458,8 @@ def cpu_legs(lc, w, n_templates, gpu_mixed16):
     """The oracle on the host cores (bench.py's CPU baseline leg): the headline
     workload on a bounded sample, extrapolated; the 2048-sample light curve in
     full (the anchor of the extrapolations); the seven-sector curve through the
-    sequential celerite reference (bounded sample, extrapolated); and the mixed
+    sequential celerite reference (bounded sample, extrapolated); the survey
+    from its shortest curve (bounded sample, extrapolated); and the mixed
     path's per-output error against the oracle's whole grid of the 16-duration
     sector (gpu_mixed16: the GPU's mixed linear search and fold of that
     workload)."""
@@ -522,6 +523,30 @@ def cpu_legs(lc, w, n_templates, gpu_mixed16):
         "period_trials_per_s": len(w5.periods) / tot5, "kind": "celerite reference "
         "(oracle/semisep.py, the stand-in where the dense oracle does not fit)",
         "extrapolated": True, "sample": f"factor once ({ts5:.1f} s), 16 templates, 3 periods"}
+    # survey (438 curves in one batched call on the GPU): the oracle on its
+    # shortest curve (dense factor and a bounded sample), extrapolated to every
+    # curve: the factor by (n / n0)^3, templates by count, folds by span
+    w4 = synth.survey_438()
+    lens = np.array([len(c.t) for c in w4.curves])
+    l4 = w4.curves[int(np.argmin(lens))]
+    t0 = time.perf_counter()
+    m4 = linear.DenseModel(l4.t, l4.y, l4.diag_var, l4.terms, l4.X)
+    ts4 = time.perf_counter() - t0
+    s4 = oracle_sample(l4, w4.durations, w4.periods, m4, ts4, n_templates=64, n_periods=4,
+                       seed=4)
+    del m4
+    n0, span0 = len(l4.t), float(l4.t[-1] - l4.t[0])
+    tot4 = sum(ts4 * (len(c.t) / n0) ** 3 + s4["t_template"] * len(c.t) * len(w4.durations) +
+               s4["t_period"] * len(w4.periods) * float(c.t[-1] - c.t[0]) / span0
+               for c in w4.curves)
+    out["cpu_survey"] = {
+        "value": float(lens.sum()) * len(w4.durations) / tot4, "unit": "(t0,D) fits/s",
+        "period_trials_per_s": len(w4.curves) * len(w4.periods) / tot4,
+        "cores": blas_threads(), "kind": "oracle", "extrapolated": True,
+        "sample": f"the shortest of {len(w4.curves)} curves (N={n0}): dense Sigma factor "
+                  f"({ts4:.1f} s), 64 random templates, 4 random periods; extrapolated to "
+                  f"every curve (factor x (N/N0)^3, templates by count, folds by span)",
+        "wall_s": ts4 + s4["wall_s"]}
     # mixed precision: per-output error against the FP64 oracle's whole grid
     if gpu_mixed16 is not None:
         out["mixed_error"] = mixed_error(gpu_mixed16)
@@ -813,6 +838,11 @@ def main():
             if "cpu_multisector" in legs and isinstance(out.get("multisector"), dict):
                 out["multisector"]["cpu_baseline"] = legs.pop("cpu_multisector")
                 out.pop("cpu_multisector", None)
+            if "cpu_survey" in legs:
+                for key in ("batch_mixed", "batch_fp64"):
+                    if isinstance(out.get(key), dict) and "error" not in out[key]:
+                        out[key]["cpu_baseline"] = legs["cpu_survey"]
+                out.pop("cpu_survey", None)
         except Exception as exc:
             out["cpu_baseline"] = {"error": repr(exc)}
     if rank == 0:
